@@ -1,0 +1,205 @@
+"""CPU oracle for the Vecchia / VIF space-time likelihood (arXiv 2602.03609).
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+with the CUDA path (``paper_2602_03609_gb300``) and never imports it.
+
+The arithmetic lives in ``vecchia_oracle.cpp`` (plain FP64 C++, every
+function citing the passage of the paper it writes out); this module only
+marshals numpy arrays through ctypes.  ``vif.py`` holds the VIF oracle in
+numpy.  Parity status per function is listed in the C++ source.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+_D = ctypes.POINTER(ctypes.c_double)
+_I32 = ctypes.POINTER(ctypes.c_int32)
+_I64 = ctypes.POINTER(ctypes.c_int64)
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        L.orc_matern.restype = ctypes.c_double
+        L.orc_matern.argtypes = [ctypes.c_double, ctypes.c_double]
+        L.orc_cov.restype = ctypes.c_double
+        L.orc_cov.argtypes = [_D, ctypes.c_double, ctypes.c_double]
+        L.orc_cov_grad.restype = None
+        L.orc_cov_grad.argtypes = [_D, ctypes.c_double, ctypes.c_double, _D]
+        L.orc_theta_from_ranges.restype = ctypes.c_int
+        L.orc_theta_from_ranges.argtypes = [ctypes.c_double] * 8 + [_D]
+        L.orc_knn_rows.restype = None
+        L.orc_knn_rows.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int, ctypes.c_int64, _I64,
+                                   _I32, _I32, _D, _D, ctypes.c_int]
+        L.orc_factor.restype = ctypes.c_int64
+        L.orc_factor.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int, _I32, _I32, _D, _D, ctypes.c_int]
+        L.orc_nll.restype = ctypes.c_double
+        L.orc_nll.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int, _I32, _I32, _D, _D, ctypes.c_int]
+        L.orc_nll_grad.restype = ctypes.c_double
+        L.orc_nll_grad.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int, _I32, _I32, _D, _D, _D,
+                                   ctypes.c_int]
+        L.orc_vecchia_sample.restype = None
+        L.orc_vecchia_sample.argtypes = [ctypes.c_int64, ctypes.c_int, _I32, _I32, _D, _D, _D, _D]
+        L.orc_dense_nll.restype = ctypes.c_double
+        L.orc_dense_nll.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D]
+        L.orc_dense_sample.restype = ctypes.c_int
+        L.orc_dense_sample.argtypes = [ctypes.c_int64, _D, _D, _D, _D, _D]
+        L.orc_cov_matrix.restype = None
+        L.orc_cov_matrix.argtypes = [ctypes.c_int64, _D, _D, ctypes.c_int64, _D, _D, _D, _D]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_D)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+def theta_from_ranges(sigma2, range_s, range_t, gamma, nugget, alpha=0.4, delta=0.2, nu=1.5) -> np.ndarray:
+    """Native parameters (sigma1^2, c, a, gamma, nugget, alpha, delta, nu)."""
+    out = np.zeros(8)
+    rc = lib().orc_theta_from_ranges(sigma2, range_s, range_t, gamma, nugget, alpha, delta, nu, _d(out))
+    if rc != 0:
+        raise ValueError("invalid ranges")
+    return out
+
+
+def theta_native(rt) -> np.ndarray:
+    """From a ``synthetic_inputs.RangeTheta``."""
+    return theta_from_ranges(*rt.astuple())
+
+
+def matern(nu: float, x: float) -> float:
+    return lib().orc_matern(float(nu), float(x))
+
+
+def cov(theta, h: float, u: float) -> float:
+    th = _f64(theta)
+    return lib().orc_cov(_d(th), float(h), float(u))
+
+
+def cov_grad(theta, h: float, u: float) -> np.ndarray:
+    th = _f64(theta)
+    out = np.zeros(4)
+    lib().orc_cov_grad(_d(th), float(h), float(u), _d(out))
+    return out
+
+
+def cov_matrix(xy1, t1, xy2, t2, theta) -> np.ndarray:
+    xy1, t1, xy2, t2, th = _f64(xy1), _f64(t1), _f64(xy2), _f64(t2), _f64(theta)
+    out = np.zeros((t1.shape[0], t2.shape[0]))
+    lib().orc_cov_matrix(t1.shape[0], _d(xy1), _d(t1), t2.shape[0], _d(xy2), _d(t2), _d(th), _d(out))
+    return out
+
+
+def knn(xy, t, theta, m, rows=None, threads=None):
+    """Brute-force correlation neighbours.  Returns (nn int32 [r,m] (-1 pad),
+    nn_cnt int32 [r], rho_m [r], rho_m1 [r]) for the requested rows (all by default)."""
+    xy, t, th = _f64(xy), _f64(t), _f64(theta)
+    n = t.shape[0]
+    rows = np.arange(n, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    R = rows.shape[0]
+    nn = np.full((R, m), -1, dtype=np.int32)
+    cnt = np.zeros(R, dtype=np.int32)
+    rm = np.zeros(R)
+    rm1 = np.zeros(R)
+    lib().orc_knn_rows(n, _d(xy), _d(t), _d(th), int(m), R, rows.ctypes.data_as(_I64),
+                       nn.ctypes.data_as(_I32), cnt.ctypes.data_as(_I32), _d(rm), _d(rm1),
+                       int(threads or default_threads()))
+    return nn, cnt, rm, rm1
+
+
+def tie_rows(rho_m, rho_m1, rel: float = 1e-12) -> np.ndarray:
+    """Rows whose m-th and (m+1)-th correlations differ by less than rel (relative)."""
+    with np.errstate(invalid="ignore"):
+        tie = np.isfinite(rho_m) & np.isfinite(rho_m1) & ((rho_m - rho_m1) <= rel * np.abs(rho_m))
+    return np.nonzero(tie)[0]
+
+
+def factor(xy, t, theta, m, nn, nn_cnt, threads=None):
+    xy, t, th = _f64(xy), _f64(t), _f64(theta)
+    nn, nn_cnt = _i32(nn), _i32(nn_cnt)
+    n = t.shape[0]
+    A = np.zeros((n, m))
+    D = np.zeros(n)
+    bad = lib().orc_factor(n, _d(xy), _d(t), _d(th), int(m), nn.ctypes.data_as(_I32),
+                           nn_cnt.ctypes.data_as(_I32), _d(A), _d(D), int(threads or default_threads()))
+    if bad >= 0:
+        raise np.linalg.LinAlgError(f"local block not SPD at row {bad}")
+    return A, D
+
+
+def nll(xy, t, theta, m, nn, nn_cnt, y, terms=False, threads=None):
+    xy, t, th, y = _f64(xy), _f64(t), _f64(theta), _f64(y)
+    nn, nn_cnt = _i32(nn), _i32(nn_cnt)
+    n = t.shape[0]
+    term = np.zeros(n) if terms else None
+    v = lib().orc_nll(n, _d(xy), _d(t), _d(th), int(m), nn.ctypes.data_as(_I32), nn_cnt.ctypes.data_as(_I32),
+                      _d(y), _d(term) if terms else None, int(threads or default_threads()))
+    return (v, term) if terms else v
+
+
+def nll_grad(xy, t, theta, m, nn, nn_cnt, y, terms=False, threads=None):
+    xy, t, th, y = _f64(xy), _f64(t), _f64(theta), _f64(y)
+    nn, nn_cnt = _i32(nn), _i32(nn_cnt)
+    n = t.shape[0]
+    g = np.zeros(5)
+    gt = np.zeros((n, 5)) if terms else None
+    v = lib().orc_nll_grad(n, _d(xy), _d(t), _d(th), int(m), nn.ctypes.data_as(_I32),
+                           nn_cnt.ctypes.data_as(_I32), _d(y), _d(g), _d(gt) if terms else None,
+                           int(threads or default_threads()))
+    return (v, g, gt) if terms else (v, g)
+
+
+def vecchia_sample(m, nn, nn_cnt, A, D, z):
+    nn, nn_cnt, A, D, z = _i32(nn), _i32(nn_cnt), _f64(A), _f64(D), _f64(z)
+    y = np.zeros(z.shape[0])
+    lib().orc_vecchia_sample(z.shape[0], int(m), nn.ctypes.data_as(_I32), nn_cnt.ctypes.data_as(_I32),
+                             _d(A), _d(D), _d(z), _d(y))
+    return y
+
+
+def dense_nll(xy, t, theta, y, grad=False):
+    xy, t, th, y = _f64(xy), _f64(t), _f64(theta), _f64(y)
+    g = np.zeros(5)
+    v = lib().orc_dense_nll(t.shape[0], _d(xy), _d(t), _d(th), _d(y), _d(g) if grad else None)
+    return (v, g) if grad else v
+
+
+def dense_sample(xy, t, theta, z):
+    xy, t, th, z = _f64(xy), _f64(t), _f64(theta), _f64(z)
+    y = np.zeros(z.shape[0])
+    if lib().orc_dense_sample(t.shape[0], _d(xy), _d(t), _d(th), _d(z), _d(y)) != 0:
+        raise np.linalg.LinAlgError("covariance not SPD")
+    return y
+
+
+def all_predecessors(n: int):
+    """Neighbour sets N(i) = {0..i-1} (m = n-1): the exact factorisation."""
+    m = max(n - 1, 1)
+    nn = np.full((n, m), -1, dtype=np.int32)
+    for i in range(1, n):
+        nn[i, :i] = np.arange(i, dtype=np.int32)
+    cnt = np.minimum(np.arange(n), m).astype(np.int32)
+    return m, nn, cnt
