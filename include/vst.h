@@ -1,0 +1,204 @@
+/*
+ * vst.h -- C ABI of the GB300 (sm_103a) Vecchia / VIF space-time likelihood
+ * library (libvst.so).
+ *
+ * Method: Gyger, Furrer & Sigrist, "Scalable non-separable spatio-temporal
+ * Gaussian process models for large-scale short-term weather prediction"
+ * (arXiv 2602.03609).  The library evaluates, on one GPU, the hot path of
+ * fitting the Gaussian model Y = b + eps of Eq. (1) with the non-separable
+ * Gneiting covariance of Eq. (2) under a Vecchia approximation (Sect. 4.1):
+ *
+ *   1. correlation-based neighbour selection (Sect. 4.4.1),
+ *   2. the per-row Vecchia factor A_i, D_i (Sect. 4.1),
+ *   3. the negative log-likelihood (Sect. 3.1) and its gradient with respect
+ *      to the covariance parameters.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All array arguments are DEVICE pointers (cudaMalloc'd memory, or the
+ *    storage of a CUDA tensor) on the current device, unless stated otherwise.
+ *    The caller owns every buffer; the library allocates nothing and keeps no
+ *    state between calls.  Scratch memory is the caller's `workspace`
+ *    (`ws_bytes` >= vst_workspace_size(...), 256-byte aligned).  A workspace
+ *    may not be shared by calls that can overlap on the GPU.
+ *  - Points are already in Vecchia order: row i may condition only on rows
+ *    j < i.  Layouts: xy[n][2] (x, y interleaved, FP64), t[n] (FP64, time in
+ *    the unit of the temporal range), y[n] (FP64 responses with the mean
+ *    removed), nn[n][m] (int32 neighbour indices, -1 padded), nn_cnt[n]
+ *    (int32, number of valid entries of row i of nn), A[n][m] (FP64, A[i][q]
+ *    multiplies neighbour nn[i][q]; B_{i, nn[i][q]} = -A[i][q]), D[n] (FP64).
+ *  - Calls are asynchronous on `stream` (a cudaStream_t; NULL = legacy default
+ *    stream) unless stated otherwise.  The returned status covers argument
+ *    validation and launch errors.  Errors found on the device (a local
+ *    covariance block that is not positive definite, a neighbour index that is
+ *    not a predecessor, a bounded wait that ran out) are recorded in the
+ *    workspace header and returned by vst_workspace_status(), which
+ *    synchronises the stream.
+ *  - Sizes: 0 <= n < 2^31, 0 <= m <= VST_MAX_M.  n == 0 is valid (the NLL is 0).
+ *  - Covariance parameters (vst_theta) must satisfy sigma1sq > 0, c > 0,
+ *    a > 0, 0 <= gamma <= 1, nugget >= 0, 0 < alpha <= 1, delta >= 0,
+ *    delta + gamma > 0 and nu in {0.5, 1.5, 2.5} (the closed-form Matern
+ *    orders, Sect. 4.5); otherwise VST_EINVAL.
+ */
+#ifndef VST_H
+#define VST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VST_MAX_M 31
+
+typedef enum {
+  VST_OK = 0,
+  VST_EINVAL = 1,     /* bad argument (message in vst_last_error) */
+  VST_ENOMEM = 2,     /* workspace too small */
+  VST_ENOTSPD = 3,    /* a local covariance block is not positive definite */
+  VST_ETIMEOUT = 4,   /* a bounded device-side wait ran out */
+  VST_ECUDA = 5,      /* a CUDA runtime call failed */
+  VST_EINTERNAL = 6   /* an internal consistency check failed on the device */
+} vst_status;
+
+typedef enum {
+  VST_FP64 = 0,   /* every step in FP64 */
+  VST_MIXED = 1   /* FP32 covariance + Cholesky, one refinement step of the
+                     solve with FP64 residuals, FP64 log-determinant and
+                     accumulation; rows whose local condition estimate exceeds
+                     the threshold, or whose FP32 Cholesky fails, are redone in
+                     FP64 */
+} vst_precision;
+
+/* Native parameters of Eq. (2) plus the nugget of Eq. (1):
+ *   c((s,t),(s',t')) = sigma1sq * psi^{-(delta+gamma)} * M_nu(c h psi^{-gamma/2}),
+ *   psi = a |t-t'|^{2 alpha} + 1,  h = ||s - s'||,
+ *   M_nu(x) = 2^{1-nu}/Gamma(nu) x^nu K_nu(x)   (d = 2),
+ * response covariance Sigma~ = Sigma + nugget * I. */
+typedef struct {
+  double sigma1sq, c, a, gamma, nugget, alpha, delta, nu;
+} vst_theta;
+
+/* n space-time points in Vecchia order (device pointers). */
+typedef struct {
+  const double* xy;
+  const double* t;
+  int64_t n;
+} vst_points;
+
+/* k inducing points of the VIF model (Sect. 4.3), device pointers.  A NULL
+ * pointer to this struct, or k == 0, selects the plain Vecchia model. */
+typedef struct {
+  const double* xy;
+  const double* t;
+  int64_t k;
+} vst_inducing;
+
+/* Device-side counters kept in the workspace header (see vst_workspace_status). */
+typedef struct {
+  int32_t status;        /* vst_status of the last call that used the workspace */
+  int32_t reserved;
+  int64_t bad_row;       /* first offending row, or -1 */
+  int64_t n_fallback;    /* VST_MIXED: rows redone in FP64 */
+  int64_t n_tie;         /* vif_build_neighbors: rows with a cut-off tie */
+} vst_ws_info;
+
+/* Host-only.  Map effective ranges to native parameters.  The effective
+ * ranges are the distance (range_s) and lag (range_t) at which the
+ * correlation decays to 0.05 (the convention of the paper's parameter tables,
+ * Sect. 6 and Table A3):  M_nu(c range_s) = 0.05  and
+ * (a range_t^{2 alpha} + 1)^{-(delta+gamma)} = 0.05.
+ * Returns VST_EINVAL on non-positive ranges or an unsupported nu. */
+vst_status vst_theta_from_ranges(double sigma1sq, double range_s, double range_t, double gamma,
+                                 double nugget, double alpha, double delta, double nu,
+                                 vst_theta* out);
+
+/* Host-only.  Workspace bytes needed by any entry point below for n points,
+ * m neighbours and k inducing points (k = 0: plain Vecchia). */
+size_t vst_workspace_size(int64_t n, int m, int64_t k);
+
+/* Correlation-based Vecchia neighbour selection (Sect. 4.4.1).
+ * For every row i: the min(i, m) predecessors j < i with the largest
+ * |rho_ij| = |Sigma_ij| / sqrt(Sigma_ii Sigma_jj) (latent covariance, no
+ * nugget; equivalently the smallest d_c = sqrt(1 - |rho_ij|)), ranked in
+ * FP64, ties broken by the smaller index, written to nn[i][0..] in decreasing
+ * order of |rho|; nn_cnt[i] = min(i, m).
+ * tie_rows (may be NULL): up to tie_cap rows (unordered) whose m-th and
+ * (m+1)-th correlations differ by less than 1e-12 relative; their number is
+ * vst_ws_info.n_tie.
+ * The search is exact: a space-time bucket grid is pruned only by a rigorous
+ * upper bound of the correlation over each bucket.
+ * Synchronises `stream` once (to size the bucket grid from the point cloud's
+ * bounding box).  ind != NULL with k > 0 (VIF residual correlation) is not
+ * available in this version and returns VST_EINVAL. */
+vst_status vif_build_neighbors(const vst_points* pts, const vst_theta* theta, int m,
+                               const vst_inducing* ind, int32_t* nn, int32_t* nn_cnt,
+                               int64_t* tie_rows, int64_t tie_cap, void* workspace,
+                               size_t ws_bytes, void* stream);
+
+/* Vecchia factor of the response covariance Sigma~ (Sect. 4.1 with the nugget
+ * of Sect. 3.1 on the diagonal): A_i = Sigma~_{i,N(i)} Sigma~_{N(i)}^{-1},
+ * D_i = Sigma~_ii - A_i Sigma~_{i,N(i)}^T, N(i) = nn[i][0..nn_cnt[i]).
+ * Entries q >= nn_cnt[i] of A[i] are set to 0.  Requires nn[i][q] < i. */
+vst_status vecchia_factor(const vst_points* pts, const vst_theta* theta, int m,
+                          const vst_inducing* ind, const int32_t* nn, const int32_t* nn_cnt,
+                          int precision, double* A, double* D, void* workspace,
+                          size_t ws_bytes, void* stream);
+
+/* Vecchia negative log-likelihood (Sect. 3.1 likelihood under the Vecchia
+ * approximation of Sect. 4.1):
+ *   nll = n/2 log(2 pi) + 1/2 sum_i log D_i + 1/2 sum_i (y_i - A_i y_N(i))^2 / D_i.
+ * nll: one FP64 device scalar.  The sum is taken in a fixed order, so repeated
+ * calls give the same bits. */
+vst_status vecchia_nll(const vst_points* pts, const vst_theta* theta, int m,
+                       const vst_inducing* ind, const int32_t* nn, const int32_t* nn_cnt,
+                       const double* y, int precision, double* nll, void* workspace,
+                       size_t ws_bytes, void* stream);
+
+/* NLL and its gradient with respect to the native parameters in the order
+ * (sigma1sq, c, a, gamma, nugget); alpha, delta and nu are held fixed and the
+ * neighbour sets are held fixed.  grad: 5 FP64 device values.  The factor is
+ * recomputed, not stored. */
+vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m,
+                            const vst_inducing* ind, const int32_t* nn, const int32_t* nn_cnt,
+                            const double* y, int precision, double* nll, double* grad,
+                            void* workspace, size_t ws_bytes, void* stream);
+
+/* Draw y = B^{-1} D^{1/2} z, a sample of the Vecchia-approximated response
+ * (y_i = A_i y_N(i) + sqrt(D_i) z_i in row order), with the FP64 factor of
+ * (pts, theta, nn).  z: n FP64 device values; y: n FP64 device outputs. */
+vst_status vecchia_sample(const vst_points* pts, const vst_theta* theta, int m,
+                          const int32_t* nn, const int32_t* nn_cnt, const double* z, double* y,
+                          void* workspace, size_t ws_bytes, void* stream);
+
+/* Measurement hooks (not part of the method).  While enabled, the library
+ * records a CUDA event pair on the launching stream around every launch of
+ * its main kernels, by class: 0 = fused row kernel (NLL / gradient / factor),
+ * 1 = FP64 fallback row kernel of the mixed form, 2 = neighbour query kernel,
+ * 3 = Vecchia sampling kernel.  vst_profile_read() synchronises on the
+ * recorded events and returns the number of launches of that class and their
+ * summed device time (ms) since the last vst_profile_enable(1).  At most 4096
+ * launches are recorded; later ones are counted but not timed (returns 1 if
+ * any launch of the class was dropped, 0 otherwise, -1 on a bad class).
+ * Not for use while a stream is being captured into a graph.  Host-only
+ * bookkeeping, not thread-safe. */
+void vst_profile_enable(int on);
+int vst_profile_read(int kernel_class, int64_t* launches, double* total_ms);
+
+/* Synchronise `stream` and copy the workspace header (device-side status and
+ * counters of the last call on this workspace) into *info (may be NULL).
+ * Returns info->status. */
+vst_status vst_workspace_status(const void* workspace, void* stream, vst_ws_info* info);
+
+/* Thread-local text of the last host-side error (empty if none). */
+const char* vst_last_error(void);
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int vst_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VST_H */

@@ -43,6 +43,12 @@ def lib():
                                    _I32, _I32, _D, _D, ctypes.c_int]
         L.orc_factor.restype = ctypes.c_int64
         L.orc_factor.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int, _I32, _I32, _D, _D, ctypes.c_int]
+        L.orc_factor_rows.restype = None
+        L.orc_factor_rows.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int, ctypes.c_int64, _I64, _I32, _I32,
+                                      _D, _D, ctypes.c_int]
+        L.orc_nll_grad_rows.restype = ctypes.c_double
+        L.orc_nll_grad_rows.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int, ctypes.c_int64, _I64, _I32, _I32,
+                                        _D, _D, ctypes.c_int]
         L.orc_nll.restype = ctypes.c_double
         L.orc_nll.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int, _I32, _I32, _D, _D, ctypes.c_int]
         L.orc_nll_grad.restype = ctypes.c_double
@@ -150,6 +156,20 @@ def factor(xy, t, theta, m, nn, nn_cnt, threads=None):
     return A, D
 
 
+def factor_rows(xy, t, theta, m, rows, nn_rows, cnt_rows, threads=None):
+    """A, D of the given rows with the given neighbour lists (spot checks)."""
+    xy, t, th = _f64(xy), _f64(t), _f64(theta)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    nn_rows, cnt_rows = _i32(nn_rows), _i32(cnt_rows)
+    R = rows.shape[0]
+    A = np.zeros((R, m))
+    D = np.zeros(R)
+    lib().orc_factor_rows(t.shape[0], _d(xy), _d(t), _d(th), int(m), R, rows.ctypes.data_as(_I64),
+                          nn_rows.ctypes.data_as(_I32), cnt_rows.ctypes.data_as(_I32), _d(A), _d(D),
+                          int(threads or default_threads()))
+    return A, D
+
+
 def nll(xy, t, theta, m, nn, nn_cnt, y, terms=False, threads=None):
     xy, t, th, y = _f64(xy), _f64(t), _f64(theta), _f64(y)
     nn, nn_cnt = _i32(nn), _i32(nn_cnt)
@@ -170,6 +190,18 @@ def nll_grad(xy, t, theta, m, nn, nn_cnt, y, terms=False, threads=None):
                            nn_cnt.ctypes.data_as(_I32), _d(y), _d(g), _d(gt) if terms else None,
                            int(threads or default_threads()))
     return (v, g, gt) if terms else (v, g)
+
+
+def nll_grad_rows(xy, t, theta, m, rows, nn_rows, cnt_rows, y, threads=None):
+    """Sum of the NLL terms and gradient terms of the given rows (no constant)."""
+    xy, t, th, y = _f64(xy), _f64(t), _f64(theta), _f64(y)
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    nn_rows, cnt_rows = _i32(nn_rows), _i32(cnt_rows)
+    g = np.zeros(5)
+    v = lib().orc_nll_grad_rows(t.shape[0], _d(xy), _d(t), _d(th), int(m), rows.shape[0],
+                                rows.ctypes.data_as(_I64), nn_rows.ctypes.data_as(_I32),
+                                cnt_rows.ctypes.data_as(_I32), _d(y), _d(g), int(threads or default_threads()))
+    return v, g
 
 
 def vecchia_sample(m, nn, nn_cnt, A, D, z):

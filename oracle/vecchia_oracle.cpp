@@ -281,6 +281,26 @@ int64_t orc_factor(int64_t n, const double* xy, const double* t, const double* t
   return first_bad;
 }
 
+// The factor of selected rows only (for spot checks at large n): for each r,
+// row rows[r] with neighbour list nn_rows[r][0..cnt[r]).  Same definition as
+// orc_factor.  A_rows [R][m], D_rows [R] (NaN if the block is not SPD).
+void orc_factor_rows(int64_t n, const double* xy, const double* t, const double* th8, int m, int64_t n_rows,
+                     const int64_t* rows, const int32_t* nn_rows, const int32_t* cnt_rows, double* A_rows,
+                     double* D_rows, int threads) {
+  const Theta th = mk(th8);
+  (void)n;
+  parallel_rows(n_rows, threads, [&](int64_t r) {
+    RowFactor rf;
+    const int cnt = cnt_rows[r];
+    if (!factor_row(th, xy, t, rows[r], nn_rows + r * m, cnt, rf)) {
+      D_rows[r] = NAN;
+      return;
+    }
+    for (int q = 0; q < m; ++q) A_rows[r * m + q] = q < cnt ? rf.a[q] : 0.0;
+    D_rows[r] = rf.D;
+  });
+}
+
 // Vecchia negative log-likelihood (Sect. 3.1 likelihood with Sigma~ replaced by
 // its Vecchia approximation (B^T D^{-1} B)^{-1}):
 //   n/2 log(2 pi) + 1/2 sum_i log D_i + 1/2 sum_i (y_i - A_i y_N(i))^2 / D_i.
@@ -370,6 +390,59 @@ double orc_nll_grad(int64_t n, const double* xy, const double* t, const double* 
     for (int p = 0; p < 5; ++p) grad[p] += rowg[(size_t)i * 5 + p];
   }
   if (gterm) std::memcpy(gterm, rowg.data(), sizeof(double) * 5 * (size_t)n);
+  return s;
+}
+
+// NLL and gradient terms of selected rows only, each with its own neighbour
+// list (same definitions as orc_nll_grad, without the n/2 log 2pi constant):
+// returns sum_r NLL_rows[r], grad = sum_r dNLL_rows[r].  Used to time the
+// oracle on a bounded sample of a large problem.
+double orc_nll_grad_rows(int64_t n, const double* xy, const double* t, const double* th8, int m,
+                         int64_t n_rows, const int64_t* rows, const int32_t* nn_rows, const int32_t* cnt_rows,
+                         const double* y, double* grad, int threads) {
+  const Theta th = mk(th8);
+  (void)n;
+  std::vector<double> out((size_t)n_rows * 6, 0.0);
+  parallel_rows(n_rows, threads, [&](int64_t q) {
+    const int64_t i = rows[q];
+    const int cnt = cnt_rows[q];
+    const int32_t* N = nn_rows + q * m;
+    RowFactor rf;
+    if (!factor_row(th, xy, t, i, N, cnt, rf)) { out[q * 6] = NAN; return; }
+    double r = y[i];
+    for (int u = 0; u < cnt; ++u) r -= rf.a[u] * y[N[u]];
+    const double D = rf.D;
+    out[q * 6] = 0.5 * std::log(D) + 0.5 * r * r / D;
+    std::vector<double> dK((size_t)cnt * cnt), dk(cnt), w(cnt);
+    double g5[5];
+    for (int p = 0; p < 5; ++p) {
+      for (int u = 0; u < cnt; ++u) {
+        for (int v = 0; v < cnt; ++v) { cov_resp_grad(th, xy, t, N[u], N[v], g5); dK[u * cnt + v] = g5[p]; }
+        cov_resp_grad(th, xy, t, N[u], i, g5);
+        dk[u] = g5[p];
+      }
+      cov_resp_grad(th, xy, t, i, i, g5);
+      double dD = g5[p];
+      for (int u = 0; u < cnt; ++u) dD -= 2.0 * dk[u] * rf.a[u];
+      for (int u = 0; u < cnt; ++u)
+        for (int v = 0; v < cnt; ++v) dD += rf.a[u] * dK[u * cnt + v] * rf.a[v];
+      for (int u = 0; u < cnt; ++u) {
+        double s = dk[u];
+        for (int v = 0; v < cnt; ++v) s -= dK[u * cnt + v] * rf.a[v];
+        w[u] = s;
+      }
+      if (cnt > 0) chol_solve(rf.L, cnt, w.data());
+      double dAy = 0.0;
+      for (int u = 0; u < cnt; ++u) dAy += w[u] * y[N[u]];
+      out[q * 6 + 1 + p] = 0.5 * dD / D - r * dAy / D - 0.5 * r * r * dD / (D * D);
+    }
+  });
+  double s = 0.0;
+  for (int p = 0; p < 5; ++p) grad[p] = 0.0;
+  for (int64_t q = 0; q < n_rows; ++q) {
+    s += out[q * 6];
+    for (int p = 0; p < 5; ++p) grad[p] += out[q * 6 + 1 + p];
+  }
   return s;
 }
 

@@ -1,0 +1,300 @@
+"""GB300 (sm_103a) Vecchia / VIF space-time likelihood engine.
+
+Python binding of ``libvst.so`` (C ABI in ``include/vst.h``).  The functions
+here carry the C entry points' names and only marshal arguments: every step
+of the computation runs in the library's CUDA kernels.  PyTorch supplies
+device memory (CUDA tensors), streams, and the autograd wrapper.
+
+There is no CPU path: loading fails loudly if ``libvst.so`` is missing (run
+``python -m paper_2602_03609_gb300.build`` or ``__graft_entry__.build()``).
+
+Layouts (row i of every array is point i in Vecchia order):
+    xy  float64 [n, 2]     t  float64 [n]     y  float64 [n]
+    nn  int32 [n, m] (-1 padded)              nn_cnt  int32 [n]
+    A   float64 [n, m]  (B[i, nn[i, q]] = -A[i, q])   D  float64 [n]
+theta: native parameters of Eq. (2) as a sequence
+    (sigma1sq, c, a, gamma, nugget, alpha, delta, nu)
+gradients are with respect to (sigma1sq, c, a, gamma, nugget).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+__all__ = [
+    "FP64", "MIXED", "MAX_M", "VstError", "lib", "vst_theta_from_ranges", "vst_workspace_size",
+    "Workspace", "vif_build_neighbors", "vecchia_factor", "vecchia_nll", "vecchia_nll_grad",
+    "vecchia_sample", "vst_workspace_status", "VecchiaNLL", "theta_tuple", "vst_profile_enable",
+    "vst_profile_read",
+]
+
+FP64 = 0
+MIXED = 1
+MAX_M = 31
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libvst.so")
+
+_STATUS = {0: "VST_OK", 1: "VST_EINVAL", 2: "VST_ENOMEM", 3: "VST_ENOTSPD", 4: "VST_ETIMEOUT",
+           5: "VST_ECUDA", 6: "VST_EINTERNAL"}
+
+
+class VstError(RuntimeError):
+    def __init__(self, code, msg, info=None):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.info = info
+
+
+class _Theta(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("sigma1sq", "c", "a", "gamma", "nugget", "alpha", "delta", "nu")]
+
+
+class _Points(ctypes.Structure):
+    _fields_ = [("xy", ctypes.c_void_p), ("t", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+class _Inducing(ctypes.Structure):
+    _fields_ = [("xy", ctypes.c_void_p), ("t", ctypes.c_void_p), ("k", ctypes.c_int64)]
+
+
+class WsInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("bad_row", ctypes.c_int64),
+                ("n_fallback", ctypes.c_int64), ("n_tie", ctypes.c_int64)]
+
+    def asdict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def lib():
+    """The loaded libvst.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: the CUDA library must be built "
+                              "(python -m paper_2602_03609_gb300.build); there is no CPU fallback")
+        L = ctypes.CDLL(LIB_PATH)
+        L.vst_last_error.restype = ctypes.c_char_p
+        L.vst_version.restype = ctypes.c_int
+        L.vst_theta_from_ranges.restype = ctypes.c_int
+        L.vst_theta_from_ranges.argtypes = [ctypes.c_double] * 8 + [ctypes.POINTER(_Theta)]
+        L.vst_workspace_size.restype = ctypes.c_size_t
+        L.vst_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int64]
+        PT, TH, IN = ctypes.POINTER(_Points), ctypes.POINTER(_Theta), ctypes.POINTER(_Inducing)
+        L.vif_build_neighbors.restype = ctypes.c_int
+        L.vif_build_neighbors.argtypes = [PT, TH, ctypes.c_int, IN, _P, _P, _P, ctypes.c_int64, _P,
+                                          ctypes.c_size_t, _P]
+        L.vecchia_factor.restype = ctypes.c_int
+        L.vecchia_factor.argtypes = [PT, TH, ctypes.c_int, IN, _P, _P, ctypes.c_int, _P, _P, _P,
+                                     ctypes.c_size_t, _P]
+        L.vecchia_nll.restype = ctypes.c_int
+        L.vecchia_nll.argtypes = [PT, TH, ctypes.c_int, IN, _P, _P, _P, ctypes.c_int, _P, _P, ctypes.c_size_t, _P]
+        L.vecchia_nll_grad.restype = ctypes.c_int
+        L.vecchia_nll_grad.argtypes = [PT, TH, ctypes.c_int, IN, _P, _P, _P, ctypes.c_int, _P, _P, _P,
+                                       ctypes.c_size_t, _P]
+        L.vecchia_sample.restype = ctypes.c_int
+        L.vecchia_sample.argtypes = [PT, TH, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]
+        L.vst_profile_enable.restype = None
+        L.vst_profile_enable.argtypes = [ctypes.c_int]
+        L.vst_profile_read.restype = ctypes.c_int
+        L.vst_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+        L.vst_workspace_status.restype = ctypes.c_int
+        L.vst_workspace_status.argtypes = [_P, _P, ctypes.POINTER(WsInfo)]
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise VstError(rc, lib().vst_last_error().decode())
+
+
+def theta_tuple(theta):
+    if isinstance(theta, _Theta):
+        return tuple(getattr(theta, k) for k, _ in _Theta._fields_)
+    t = tuple(float(v) for v in (theta.tolist() if hasattr(theta, "tolist") else theta))
+    if len(t) != 8:
+        raise ValueError("theta needs 8 values (sigma1sq, c, a, gamma, nugget, alpha, delta, nu)")
+    return t
+
+
+def _th(theta):
+    return _Theta(*theta_tuple(theta))
+
+
+def vst_theta_from_ranges(sigma1sq, range_s, range_t, gamma, nugget, alpha=0.4, delta=0.2, nu=1.5):
+    out = _Theta()
+    _check(lib().vst_theta_from_ranges(sigma1sq, range_s, range_t, gamma, nugget, alpha, delta, nu,
+                                       ctypes.byref(out)))
+    return theta_tuple(out)
+
+
+def vst_workspace_size(n, m, k=0) -> int:
+    return int(lib().vst_workspace_size(int(n), int(m), int(k)))
+
+
+class Workspace:
+    """Caller-owned scratch memory (a CUDA uint8 tensor, 256-byte aligned)."""
+
+    def __init__(self, n, m, k=0, device=None):
+        self.nbytes = vst_workspace_size(n, m, k)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+        self.ptr = (self.buf.data_ptr() + 255) // 256 * 256
+
+    def fits(self, n, m, k=0):
+        return self.nbytes >= vst_workspace_size(n, m, k)
+
+
+def _ptr(x, dtype, name):
+    if x is None:
+        return None
+    if not (isinstance(x, torch.Tensor) and x.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if x.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return x.data_ptr()
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def _points(xy, t):
+    n = t.shape[0]
+    if xy.shape != (n, 2):
+        raise ValueError("xy must be [n, 2]")
+    return _Points(_ptr(xy, torch.float64, "xy"), _ptr(t, torch.float64, "t"), n)
+
+
+def _ws(ws, n, m):
+    if ws is None:
+        ws = Workspace(n, m)
+    if not ws.fits(n, m):
+        raise ValueError("workspace too small")
+    return ws
+
+
+def vif_build_neighbors(xy, t, theta, m, nn=None, nn_cnt=None, tie_rows=None, ws=None, stream=None):
+    """Correlation-based neighbour sets (Sect. 4.4.1).  Returns (nn, nn_cnt)."""
+    n = t.shape[0]
+    nn = nn if nn is not None else torch.empty((n, m), dtype=torch.int32, device=t.device)
+    nn_cnt = nn_cnt if nn_cnt is not None else torch.empty(n, dtype=torch.int32, device=t.device)
+    ws = _ws(ws, n, m)
+    pts = _points(xy, t)
+    cap = 0 if tie_rows is None else tie_rows.numel()
+    _check(lib().vif_build_neighbors(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), None,
+                                     _ptr(nn, torch.int32, "nn"), _ptr(nn_cnt, torch.int32, "nn_cnt"),
+                                     _ptr(tie_rows, torch.int64, "tie_rows"), cap, ws.ptr, ws.nbytes,
+                                     _stream(stream)))
+    return nn, nn_cnt
+
+
+def vecchia_factor(xy, t, theta, m, nn, nn_cnt, precision=FP64, A=None, D=None, ws=None, stream=None):
+    """Vecchia factor (A, D) of the response covariance (Sect. 4.1)."""
+    n = t.shape[0]
+    A = A if A is not None else torch.empty((n, m), dtype=torch.float64, device=t.device)
+    D = D if D is not None else torch.empty(n, dtype=torch.float64, device=t.device)
+    ws = _ws(ws, n, m)
+    pts = _points(xy, t)
+    _check(lib().vecchia_factor(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), None,
+                                _ptr(nn, torch.int32, "nn"), _ptr(nn_cnt, torch.int32, "nn_cnt"), int(precision),
+                                _ptr(A, torch.float64, "A"), _ptr(D, torch.float64, "D"), ws.ptr, ws.nbytes,
+                                _stream(stream)))
+    return A, D
+
+
+def vecchia_nll(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, out=None, ws=None, stream=None):
+    """Vecchia negative log-likelihood; returns a 1-element CUDA float64 tensor."""
+    n = t.shape[0]
+    out = out if out is not None else torch.empty(1, dtype=torch.float64, device=t.device)
+    ws = _ws(ws, n, m)
+    pts = _points(xy, t)
+    _check(lib().vecchia_nll(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), None,
+                             _ptr(nn, torch.int32, "nn"), _ptr(nn_cnt, torch.int32, "nn_cnt"),
+                             _ptr(y, torch.float64, "y"), int(precision), _ptr(out, torch.float64, "nll"),
+                             ws.ptr, ws.nbytes, _stream(stream)))
+    return out
+
+
+def vecchia_nll_grad(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, nll=None, grad=None, ws=None, stream=None):
+    """NLL and its gradient w.r.t. (sigma1sq, c, a, gamma, nugget); CUDA tensors."""
+    n = t.shape[0]
+    nll = nll if nll is not None else torch.empty(1, dtype=torch.float64, device=t.device)
+    grad = grad if grad is not None else torch.empty(5, dtype=torch.float64, device=t.device)
+    ws = _ws(ws, n, m)
+    pts = _points(xy, t)
+    _check(lib().vecchia_nll_grad(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), None,
+                                  _ptr(nn, torch.int32, "nn"), _ptr(nn_cnt, torch.int32, "nn_cnt"),
+                                  _ptr(y, torch.float64, "y"), int(precision), _ptr(nll, torch.float64, "nll"),
+                                  _ptr(grad, torch.float64, "grad"), ws.ptr, ws.nbytes, _stream(stream)))
+    return nll, grad
+
+
+def vecchia_sample(xy, t, theta, m, nn, nn_cnt, z, y=None, ws=None, stream=None):
+    """y = B^{-1} D^{1/2} z with the FP64 Vecchia factor."""
+    n = t.shape[0]
+    y = y if y is not None else torch.empty(n, dtype=torch.float64, device=t.device)
+    ws = _ws(ws, n, m)
+    pts = _points(xy, t)
+    _check(lib().vecchia_sample(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), _ptr(nn, torch.int32, "nn"),
+                                _ptr(nn_cnt, torch.int32, "nn_cnt"), _ptr(z, torch.float64, "z"),
+                                _ptr(y, torch.float64, "y"), ws.ptr, ws.nbytes, _stream(stream)))
+    return y
+
+
+def vst_workspace_status(ws, stream=None, raise_on_error=True):
+    """Synchronise and read the device-side status/counters of the last call."""
+    info = WsInfo()
+    rc = lib().vst_workspace_status(ws.ptr, _stream(stream), ctypes.byref(info))
+    if rc != 0 and raise_on_error:
+        raise VstError(rc, lib().vst_last_error().decode(), info.asdict())
+    return info.asdict()
+
+
+PROF_ROWS, PROF_FALLBACK, PROF_KNN, PROF_SAMPLE = 0, 1, 2, 3
+
+
+def vst_profile_enable(on=True):
+    lib().vst_profile_enable(1 if on else 0)
+
+
+def vst_profile_read(kernel_class):
+    """(launches, total device ms) of one kernel class since the last enable."""
+    n = ctypes.c_int64(0)
+    ms = ctypes.c_double(0.0)
+    rc = lib().vst_profile_read(int(kernel_class), ctypes.byref(n), ctypes.byref(ms))
+    if rc < 0:
+        raise ValueError("bad kernel class")
+    return int(n.value), float(ms.value)
+
+
+class VecchiaNLL(torch.autograd.Function):
+    """NLL as a differentiable function of the 5 free native parameters.
+
+    forward(theta5, fixed3, xy, t, y, nn, nn_cnt, m, precision, ws) where
+    theta5 = (sigma1sq, c, a, gamma, nugget) is a float64 tensor (any device)
+    and fixed3 = (alpha, delta, nu).  The gradient is computed by the
+    library's adjoint kernel at forward time (the factor is recomputed, not
+    stored) and scaled by grad_output in backward.
+    """
+
+    @staticmethod
+    def forward(ctx, theta5, fixed3, xy, t, y, nn, nn_cnt, m, precision=MIXED, ws=None):
+        th = [float(v) for v in theta5.detach().cpu().tolist()] + [float(v) for v in fixed3]
+        nll, grad = vecchia_nll_grad(xy, t, th, m, nn, nn_cnt, y, precision=precision, ws=ws)
+        ctx.save_for_backward(grad)
+        ctx.theta_device = theta5.device
+        return nll.reshape(()).to(theta5.device)
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return (g * grad.to(ctx.theta_device),) + (None,) * 9

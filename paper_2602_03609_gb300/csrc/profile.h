@@ -1,0 +1,21 @@
+// RAII event pair around one kernel launch when profiling is enabled.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace vst {
+
+enum ProfileClass { kProfRows = 0, kProfFallback = 1, kProfKnn = 2, kProfSample = 3 };
+
+class ProfileScope {
+ public:
+  ProfileScope(int cls, cudaStream_t st);
+  ~ProfileScope();
+
+ private:
+  int cls_;
+  cudaStream_t st_;
+  int rec_;
+};
+
+}  // namespace vst

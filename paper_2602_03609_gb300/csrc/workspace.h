@@ -1,0 +1,63 @@
+// Layout of the caller-provided workspace.  Every region starts on a 256-byte
+// boundary; the layout depends only on (n, m, k), so vst_workspace_size() and
+// the entry points agree.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace vst {
+
+constexpr int64_t kMaxTimeBins = 1 << 16;   // neighbour search: time bins
+constexpr int kBBoxBlocks = 512;            // neighbour search: bounding-box partials
+
+inline int64_t max_buckets(int64_t n) { return 2 * n + 4096; }
+
+struct WsLayout {
+  size_t hdr, lagd, lagf, partial, flag;
+  // neighbour search
+  size_t bbox_part, bbox, binmin, offsets, cursor, blocksums, sidx, sx, sy, pbucket;
+  // Vecchia sampling
+  size_t sA, sD, ready, counter;
+  size_t total;
+};
+
+inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+inline WsLayout ws_layout(int64_t n, int m, int64_t k) {
+  (void)k;
+  WsLayout L{};
+  size_t off = 0;
+  auto take = [&off](size_t bytes) {
+    const size_t at = off;
+    off = align256(off + bytes);
+    return at;
+  };
+  const int64_t nb = max_buckets(n);
+  const int64_t nn = n > 0 ? n : 1;
+  L.hdr = take(256);
+  L.lagd = take(sizeof(LagD) * kLagTab);
+  L.lagf = take(sizeof(LagF) * kLagTab);
+  L.partial = take(sizeof(double) * 8 * (size_t)(1 << 16) * 2);
+  L.flag = take((size_t)nn);
+  L.bbox_part = take(sizeof(double) * 8 * kBBoxBlocks);
+  L.bbox = take(sizeof(double) * 8);
+  L.binmin = take(sizeof(int32_t) * kMaxTimeBins);
+  L.offsets = take(sizeof(int32_t) * (size_t)(nb + 1));
+  L.cursor = take(sizeof(int32_t) * (size_t)nb);
+  L.blocksums = take(sizeof(int32_t) * (size_t)(nb / 1024 + 2));
+  L.sidx = take(sizeof(int32_t) * (size_t)nn);
+  L.sx = take(sizeof(float) * (size_t)nn);
+  L.sy = take(sizeof(float) * (size_t)nn);
+  L.pbucket = take(sizeof(int32_t) * (size_t)nn);
+  L.sA = take(sizeof(double) * (size_t)nn * (size_t)(m > 0 ? m : 1));
+  L.sD = take(sizeof(double) * (size_t)nn);
+  L.ready = take(sizeof(int32_t) * (size_t)nn);
+  L.counter = take(sizeof(unsigned long long) * 2);
+  L.total = off;
+  return L;
+}
+
+}  // namespace vst

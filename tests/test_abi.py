@@ -1,0 +1,87 @@
+"""C-ABI library: it builds, loads, exports every symbol include/vst.h declares,
+and its host-only entry points validate arguments.  No compute call (no GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*([a-z_0-9]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def vst():
+    from paper_2602_03609_gb300 import build
+    build.build()
+    import paper_2602_03609_gb300 as p
+    return p
+
+
+def test_exports_every_declared_symbol(vst):
+    names = declared_functions()
+    assert {"vif_build_neighbors", "vecchia_factor", "vecchia_nll", "vecchia_nll_grad"} <= set(names)
+    L = ctypes.CDLL(vst.LIB_PATH)
+    for nm in names:
+        assert hasattr(L, nm), nm
+
+
+def test_theta_from_ranges_matches_oracle(vst):
+    for args in [(1, 0.1, 3, 0.5, 0.05, 0.4, 0.2, 1.5), (2, 0.08, 5, 0.9, 0.1, 0.7, 0.1, 0.5),
+                 (1, 0.3, 1, 0.1, 0.2, 0.4, 0.2, 2.5)]:
+        np.testing.assert_allclose(vst.vst_theta_from_ranges(*args), oracle.theta_from_ranges(*args), rtol=1e-13)
+    with pytest.raises(vst.VstError):
+        vst.vst_theta_from_ranges(1, -0.1, 3, 0.5, 0.05)
+    with pytest.raises(vst.VstError):
+        vst.vst_theta_from_ranges(1, 0.1, 3, 0.5, 0.05, nu=1.0)
+
+
+def test_workspace_size_monotone(vst):
+    a = vst.vst_workspace_size(1000, 10)
+    b = vst.vst_workspace_size(100000, 10)
+    c = vst.vst_workspace_size(100000, 30)
+    assert 0 < a < b < c
+    assert vst.vst_workspace_size(0, 0) > 0
+
+
+def test_host_validation_without_gpu(vst):
+    L = vst.lib()
+    th = vst._Theta(*vst.vst_theta_from_ranges(1, 0.1, 3, 0.5, 0.05))
+    pts = vst._Points(None, None, 10)
+    # m beyond the supported maximum
+    rc = L.vecchia_nll(ctypes.byref(pts), ctypes.byref(th), 40, None, None, None, None, 0, None, None, 0, None)
+    assert rc == 1 and b"m=40" in L.vst_last_error()
+    # invalid covariance parameters
+    bad = vst._Theta(1.0, -1.0, 1.0, 0.5, 0.05, 0.4, 0.2, 1.5)
+    rc = L.vecchia_nll(ctypes.byref(pts), ctypes.byref(bad), 10, None, None, None, None, 0, None, None, 0, None)
+    assert rc == 1
+    # unsupported smoothness
+    bad = vst._Theta(1.0, 1.0, 1.0, 0.5, 0.05, 0.4, 0.2, 1.0)
+    rc = L.vecchia_nll(ctypes.byref(pts), ctypes.byref(bad), 10, None, None, None, None, 0, None, None, 0, None)
+    assert rc == 1 and b"nu" in L.vst_last_error()
+    # NULL arrays
+    rc = L.vecchia_nll_grad(ctypes.byref(pts), ctypes.byref(th), 10, None, None, None, None, 0, None, None,
+                            None, 0, None)
+    assert rc == 1
+    # workspace too small (non-NULL, aligned dummy address; never dereferenced)
+    pts = vst._Points(256, 512, 10)
+    rc = L.vecchia_factor(ctypes.byref(pts), ctypes.byref(th), 5, None, 1024, 2048, 0, 4096, 8192, 256, 16,
+                          None)
+    assert rc == 2
+    # VIF is rejected by the plain entry points of this version
+    ind = vst._Inducing(256, 512, 5)
+    rc = L.vif_build_neighbors(ctypes.byref(pts), ctypes.byref(th), 5, ctypes.byref(ind), 1024, 2048, None, 0,
+                               256, 1 << 30, None)
+    assert rc == 1

@@ -1,0 +1,83 @@
+"""The bench workload at full size (continental: ~1.108M points, m = 30), in the
+launch configuration bench.py times: neighbour sets and factor rows checked
+against the oracle on sampled rows; the NLL through properties that hold at
+any size (whitening identity; mixed vs FP64)."""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic_inputs as si
+from gpu_util import cuda_or_skip, dev, load_vst
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def full():
+    torch = cuda_or_skip()
+    vst = load_vst()
+    w = si.continental()
+    th = oracle.theta_native(w.theta)
+    xy, t, z = dev(torch, w.xy, w.t, w.z)
+    ws = vst.Workspace(w.n, w.m)
+    nn, cnt = vst.vif_build_neighbors(xy, t, th, w.m, ws=ws)
+    info = vst.vst_workspace_status(ws)
+    return dict(torch=torch, vst=vst, w=w, th=th, xy=xy, t=t, z=z, ws=ws, nn=nn, cnt=cnt, info=info)
+
+
+def sample_rows(n, k=600, seed=0):
+    r = np.random.default_rng(seed)
+    rows = np.concatenate([np.arange(40), r.choice(n, k, replace=False), np.arange(n - 40, n)])
+    return np.unique(rows)
+
+
+def test_neighbours_sampled_rows(full):
+    w, th = full["w"], full["th"]
+    rows = sample_rows(w.n)
+    nn_o, cnt_o, rm, rm1 = oracle.knn(w.xy, w.t, th, w.m, rows=rows)
+    nn_g = full["nn"].cpu().numpy()[rows]
+    cnt_g = full["cnt"].cpu().numpy()[rows]
+    assert np.array_equal(cnt_g, cnt_o)
+    ties = set(oracle.tie_rows(rm, rm1).tolist())
+    for r in range(rows.shape[0]):
+        if r in ties:
+            continue
+        assert np.array_equal(np.sort(nn_g[r, :cnt_o[r]]), np.sort(nn_o[r, :cnt_o[r]])), rows[r]
+    # factor rows against the oracle with the oracle's own neighbour lists
+    A_o, D_o = oracle.factor_rows(w.xy, w.t, th, w.m, rows, nn_o, cnt_o)
+    A_g, D_g = full["vst"].vecchia_factor(full["xy"], full["t"], th, w.m, full["nn"], full["cnt"])
+    A_g, D_g = A_g.cpu().numpy()[rows], D_g.cpu().numpy()[rows]
+    for r in range(rows.shape[0]):
+        if r in ties:
+            continue
+        # A's entries are stored in each side's neighbour order: compare per index
+        og = dict(zip(nn_g[r, :cnt_o[r]], A_g[r, :cnt_o[r]]))
+        oo = dict(zip(nn_o[r, :cnt_o[r]], A_o[r, :cnt_o[r]]))
+        assert og.keys() == oo.keys()
+        for k in og:
+            assert abs(og[k] - oo[k]) <= 1e-9
+        assert D_g[r] == pytest.approx(D_o[r], rel=1e-9)
+
+
+def test_nll_properties_full_size(full):
+    torch, vst, w, th = full["torch"], full["vst"], full["w"], full["th"]
+    y = vst.vecchia_sample(full["xy"], full["t"], th, w.m, full["nn"], full["cnt"], full["z"], ws=full["ws"])
+    vst.vst_workspace_status(full["ws"])
+    A, D = vst.vecchia_factor(full["xy"], full["t"], th, w.m, full["nn"], full["cnt"], ws=full["ws"])
+    v64, g64 = vst.vecchia_nll_grad(full["xy"], full["t"], th, w.m, full["nn"], full["cnt"], y,
+                                    precision=vst.FP64, ws=full["ws"])
+    vst.vst_workspace_status(full["ws"])
+    Dn = D.cpu().numpy()
+    ref = 0.5 * w.n * np.log(2 * np.pi) + 0.5 * np.log(Dn).sum() + 0.5 * (w.z ** 2).sum()
+    assert abs(v64.item() - ref) / w.n <= 1e-10
+    assert np.all(Dn >= th[4] * (1 - 1e-12)) and np.all(Dn <= (th[0] + th[4]) * (1 + 1e-12))
+    vmx, gmx = vst.vecchia_nll_grad(full["xy"], full["t"], th, w.m, full["nn"], full["cnt"], y,
+                                    precision=vst.MIXED, ws=full["ws"])
+    info = vst.vst_workspace_status(full["ws"])
+    assert abs(vmx.item() - v64.item()) / w.n <= 1e-6
+    # variance-scaling identity (any size): s1 dNLL/ds1 + s2 dNLL/ds2 = n/2 - 1/2 sum e_i^2, e = z here
+    g = g64.cpu().numpy()
+    assert th[0] * g[0] + th[4] * g[4] == pytest.approx(w.n / 2 - 0.5 * (w.z ** 2).sum(), rel=1e-8, abs=1e-6 * w.n)
+    gm = gmx.cpu().numpy()
+    assert np.all(np.abs(gm - g) <= 1e-3 * np.maximum(np.abs(g), 1e-3 * w.n))
+    assert info["n_fallback"] == 0
