@@ -186,6 +186,41 @@ vst_status vecchia_sample(const vst_points* pts, const vst_theta* theta, int m,
 void vst_profile_enable(int on);
 int vst_profile_read(int kernel_class, int64_t* launches, double* total_ms);
 
+/* ------------------------------------------------------------------------
+ * No-allocation entry point.  The paper has no counterpart to this call: it
+ * exists for callers that cannot call cudaMalloc at all -- code that runs
+ * inside a host application which owns every device allocation (a fixed
+ * memory pool, or a strict memory budget checked by its allocator), or code
+ * on a latency-critical path, where cudaMalloc's implicit device-wide
+ * synchronisation and possible failure are not acceptable.
+ *
+ * vecchia_nll_grad_noalloc computes exactly what vecchia_nll_grad computes
+ * (same arguments, minus the workspace) but takes its scratch memory from a
+ * file-scope device array of about 10 MiB (its exact size is returned by
+ * vst_noalloc_scratch_bytes()) that every GPU loading the library holds
+ * until the process exits.  It allocates nothing: no cudaMalloc/cudaFree and
+ * no allocating library routine.
+ *  - n may not exceed VST_NOALLOC_MAX_N (2^21 points); larger n returns
+ *    VST_EINVAL with a message -- use vecchia_nll_grad with a workspace.
+ *  - The first call on each device looks up the array's device address
+ *    (cudaGetSymbolAddress, with that device current); make that first call
+ *    before capturing the stream into a CUDA graph.
+ *  - Every call shares the one array and overwrites it (each call resets the
+ *    parts that must start at zero).  Calls that may overlap on the GPU --
+ *    on different streams, or from different host threads -- race on it and
+ *    must not be issued concurrently; calls on one stream are ordered.
+ *  - Device-side status of the last call: vst_noalloc_status().
+ * ------------------------------------------------------------------------ */
+#define VST_NOALLOC_MAX_N (1 << 21)
+vst_status vecchia_nll_grad_noalloc(const vst_points* pts, const vst_theta* theta, int m,
+                                    const int32_t* nn, const int32_t* nn_cnt, const double* y,
+                                    int precision, double* nll, double* grad, void* stream);
+/* Size in bytes of the static scratch array used by the call above. */
+size_t vst_noalloc_scratch_bytes(void);
+/* Like vst_workspace_status, for the static scratch of the no-allocation call
+ * on the current device. */
+vst_status vst_noalloc_status(void* stream, vst_ws_info* info);
+
 /* Synchronise `stream` and copy the workspace header (device-side status and
  * counters of the last call on this workspace) into *info (may be NULL).
  * Returns info->status. */

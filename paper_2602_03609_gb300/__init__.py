@@ -27,7 +27,7 @@ __all__ = [
     "FP64", "MIXED", "MAX_M", "VstError", "lib", "vst_theta_from_ranges", "vst_workspace_size",
     "Workspace", "vif_build_neighbors", "vecchia_factor", "vecchia_nll", "vecchia_nll_grad",
     "vecchia_sample", "vst_workspace_status", "VecchiaNLL", "theta_tuple", "vst_profile_enable",
-    "vst_profile_read",
+    "vst_profile_read", "vecchia_nll_grad_noalloc", "vst_noalloc_status", "NOALLOC_MAX_N",
 ]
 
 FP64 = 0
@@ -103,6 +103,12 @@ def lib():
         L.vst_profile_enable.argtypes = [ctypes.c_int]
         L.vst_profile_read.restype = ctypes.c_int
         L.vst_profile_read.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)]
+        L.vecchia_nll_grad_noalloc.restype = ctypes.c_int
+        L.vecchia_nll_grad_noalloc.argtypes = [PT, TH, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, _P, _P]
+        L.vst_noalloc_scratch_bytes.restype = ctypes.c_size_t
+        L.vst_noalloc_scratch_bytes.argtypes = []
+        L.vst_noalloc_status.restype = ctypes.c_int
+        L.vst_noalloc_status.argtypes = [_P, ctypes.POINTER(WsInfo)]
         L.vst_workspace_status.restype = ctypes.c_int
         L.vst_workspace_status.argtypes = [_P, _P, ctypes.POINTER(WsInfo)]
         _lib = L
@@ -236,6 +242,35 @@ def vecchia_nll_grad(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, nll=None, g
                                   _ptr(y, torch.float64, "y"), int(precision), _ptr(nll, torch.float64, "nll"),
                                   _ptr(grad, torch.float64, "grad"), ws.ptr, ws.nbytes, _stream(stream)))
     return nll, grad
+
+
+NOALLOC_MAX_N = 1 << 21
+
+
+def vecchia_nll_grad_noalloc(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, nll=None, grad=None, stream=None):
+    """vecchia_nll_grad without a workspace, for callers that cannot allocate
+    device memory (the library's own ~10 MiB static device scratch is used;
+    n <= NOALLOC_MAX_N; calls that overlap on the GPU race on that scratch).
+    nll/grad, if given, must be preallocated CUDA float64 tensors."""
+    n = t.shape[0]
+    nll = nll if nll is not None else torch.empty(1, dtype=torch.float64, device=t.device)
+    grad = grad if grad is not None else torch.empty(5, dtype=torch.float64, device=t.device)
+    pts = _points(xy, t)
+    _check(lib().vecchia_nll_grad_noalloc(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m),
+                                          _ptr(nn, torch.int32, "nn"), _ptr(nn_cnt, torch.int32, "nn_cnt"),
+                                          _ptr(y, torch.float64, "y"), int(precision),
+                                          _ptr(nll, torch.float64, "nll"), _ptr(grad, torch.float64, "grad"),
+                                          _stream(stream)))
+    return nll, grad
+
+
+def vst_noalloc_status(stream=None, raise_on_error=True):
+    """Device-side status of the last no-allocation call on the current device."""
+    info = WsInfo()
+    rc = lib().vst_noalloc_status(_stream(stream), ctypes.byref(info))
+    if rc != 0 and raise_on_error:
+        raise VstError(rc, lib().vst_last_error().decode(), info.asdict())
+    return info.asdict()
 
 
 def vecchia_sample(xy, t, theta, m, nn, nn_cnt, z, y=None, ws=None, stream=None):

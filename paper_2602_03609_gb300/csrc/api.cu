@@ -84,6 +84,11 @@ void launch_lag_table(const DevTheta& th, LagD* d, LagF* f, cudaStream_t st) {
 
 void launch_init_header(WsHeader* h, cudaStream_t st) { init_header_kernel<<<1, 1, 0, st>>>(h); }
 
+void launch_reduce_partials(const double* p0, int64_t w0, const double* p1, int64_t w1, double nll_const,
+                            double* nll, double* grad, cudaStream_t st) {
+  reduce_partials_kernel<<<1, 256, 0, st>>>(p0, w0, p1, w1, nll_const, nll, grad);
+}
+
 int nu_code(double nu) {
   if (nu == 0.5) return 0;
   if (nu == 1.5) return 1;

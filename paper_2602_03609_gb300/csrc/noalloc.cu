@@ -1,0 +1,144 @@
+// vecchia_nll_grad_noalloc: the NLL + gradient entry point for callers that
+// cannot allocate device memory.  Its scratch memory (status header, lag
+// tables, per-warp partial sums, FP64-fallback row flags) lives in one
+// file-scope device array instead of a caller-provided workspace.
+#include <mutex>
+
+#include "kernels.h"
+#include "profile.h"
+
+namespace vst {
+
+vst_status fail(vst_status s, const char* fmt, ...);
+vst_status cuda_fail(cudaError_t e, const char* where);
+vst_status check_theta(const vst_theta* th);
+DevTheta dev_theta(const vst_theta* th);
+int nu_code(double nu);
+void launch_lag_table(const DevTheta& th, LagD* d, LagF* f, cudaStream_t st);
+void launch_init_header(WsHeader* h, cudaStream_t st);
+void launch_reduce_partials(const double* p0, int64_t w0, const double* p1, int64_t w1, double nll_const,
+                            double* nll, double* grad, cudaStream_t st);
+
+namespace {
+
+// Layout of the static scratch array (byte offsets, 256-byte aligned).
+constexpr size_t kHdrOff = 0;
+constexpr size_t kLagDOff = 256;
+constexpr size_t kLagFOff = kLagDOff + sizeof(LagD) * kLagTab;
+constexpr size_t kPartOff = kLagFOff + sizeof(LagF) * kLagTab;
+constexpr size_t kPartBytes = sizeof(double) * 8 * (size_t)kMaxPartialWarps;  // one buffer
+constexpr size_t kFlagOff = kPartOff + 2 * kPartBytes;
+constexpr size_t kScratchBytes = kFlagOff + (size_t)VST_NOALLOC_MAX_N;
+static_assert(kLagFOff % 256 == 0 && kPartOff % 256 == 0 && kFlagOff % 256 == 0, "alignment");
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+void* g_scratch_ptr[kMaxDevices] = {};
+
+}  // namespace
+
+// Every GPU that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
+
+// Device address of the scratch array on the current device (looked up once
+// per device; the host-side symbol itself is not a device address).
+static vst_status scratch_address(char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(VST_EINVAL, "device %d out of range", dev);
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (g_scratch_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+    g_scratch_ptr[dev] = p;
+  }
+  *out = static_cast<char*>(g_scratch_ptr[dev]);
+  return VST_OK;
+}
+
+}  // namespace vst
+
+using namespace vst;
+
+extern "C" size_t vst_noalloc_scratch_bytes(void) { return kScratchBytes; }
+
+extern "C" vst_status vecchia_nll_grad_noalloc(const vst_points* pts, const vst_theta* theta, int m,
+                                               const int32_t* nn, const int32_t* nn_cnt, const double* y,
+                                               int precision, double* nll, double* grad, void* stream) {
+  if (!pts) return fail(VST_EINVAL, "pts is NULL");
+  const int64_t n = pts->n;
+  if (n < 0) return fail(VST_EINVAL, "n=%lld is negative", (long long)n);
+  if (n > VST_NOALLOC_MAX_N)
+    return fail(VST_EINVAL, "n=%lld exceeds the no-allocation limit VST_NOALLOC_MAX_N=%d; use vecchia_nll_grad "
+                "with a caller-provided workspace", (long long)n, VST_NOALLOC_MAX_N);
+  if (m < 0 || m > VST_MAX_M) return fail(VST_EINVAL, "m=%d out of range [0, %d]", m, VST_MAX_M);
+  vst_status s = check_theta(theta);
+  if (s != VST_OK) return s;
+  if (precision != VST_FP64 && precision != VST_MIXED) return fail(VST_EINVAL, "bad precision %d", precision);
+  if (n > 0 && (!pts->xy || !pts->t || !y || !nn_cnt || (m > 0 && !nn))) return fail(VST_EINVAL, "NULL array");
+  if (!nll || !grad) return fail(VST_EINVAL, "nll/grad is NULL");
+  char* base = nullptr;
+  s = scratch_address(&base);
+  if (s != VST_OK) return s;
+
+  cudaStream_t st = (cudaStream_t)stream;
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(base + kHdrOff);
+  LagD* lagd = reinterpret_cast<LagD*>(base + kLagDOff);
+  LagF* lagf = reinterpret_cast<LagF*>(base + kLagFOff);
+  double* part0 = reinterpret_cast<double*>(base + kPartOff);
+  double* part1 = reinterpret_cast<double*>(base + kPartOff + kPartBytes);
+  uint8_t* flag = reinterpret_cast<uint8_t*>(base + kFlagOff);
+  const DevTheta th = dev_theta(theta);
+  const bool mixed = precision == VST_MIXED;
+
+  // the array keeps the previous call's contents: reset what must start at zero
+  launch_init_header(hdr, st);
+  launch_lag_table(th, lagd, lagf, st);
+  cudaError_t e = cudaSuccess;
+  if (mixed && n > 0) e = cudaMemsetAsync(flag, 0, (size_t)n, st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "launch");
+
+  RowArgs g{};
+  g.xy = pts->xy;
+  g.t = pts->t;
+  g.y = y;
+  g.nn = nn;
+  g.nn_cnt = nn_cnt;
+  g.n = n;
+  g.m = m;
+  g.th = th;
+  g.lagd = lagd;
+  g.lagf = lagf;
+  g.flag = flag;
+  g.hdr = hdr;
+  g.tau = 1.0e4f;
+  g.offsets = nullptr;
+  const int nu = nu_code(theta->nu);
+  int64_t w0 = 0, w1 = 0;
+  if (n > 0) {
+    g.partial = part0;
+    g.fallback_only = 0;
+    e = launch_rows(mixed, nu, m + 1, kModeNllGrad, g, st, &w0);
+    if (e != cudaSuccess) return cuda_fail(e, "row kernel");
+    if (mixed) {
+      g.partial = part1;
+      g.fallback_only = 1;
+      e = launch_rows(false, nu, m + 1, kModeNllGrad, g, st, &w1);
+      if (e != cudaSuccess) return cuda_fail(e, "fallback row kernel");
+    }
+  }
+  if (w0 > kMaxPartialWarps || w1 > kMaxPartialWarps) return fail(VST_EINTERNAL, "too many warps");
+  launch_reduce_partials(part0, w0, part1, w1, 0.5 * (double)n * std::log(2.0 * M_PI), nll, grad, st);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? VST_OK : cuda_fail(e, "reduce kernel");
+}
+
+extern "C" vst_status vst_noalloc_status(void* stream, vst_ws_info* info) {
+  char* base = nullptr;
+  vst_status s = scratch_address(&base);
+  if (s != VST_OK) return s;
+  return vst_workspace_status(base + kHdrOff, stream, info);
+}
