@@ -121,6 +121,9 @@ DevTheta dev_theta(const vst_theta* th) {
   d.delta = th->delta;
   d.nu = th->nu;
   d.p = th->delta + th->gamma;  // delta + gamma d/2, d = 2
+  const double dg = th->sigma1sq + th->nugget;
+  d.dg_hi = (float)dg;
+  d.dg_lo = (float)(dg - (double)d.dg_hi);
   return d;
 }
 

@@ -12,7 +12,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
-#include "../../include/vst.h"
+#include "vst.h"
 
 namespace vst {
 
@@ -22,7 +22,8 @@ constexpr unsigned kFull = 0xffffffffu;
 // Parameters as the kernels see them (by value in the kernel arguments).
 struct DevTheta {
   double sigma1sq, c, a, gamma, nugget, alpha, delta, nu;
-  double p;  // delta + gamma * d / 2 with d = 2
+  double p;            // delta + gamma * d / 2 with d = 2
+  float dg_hi, dg_lo;  // sigma1^2 + nugget as a double-float (mixed form's diagonal)
 };
 
 // Per-lag factors of Eq. (2) and of its parameter derivatives:

@@ -6,7 +6,7 @@
 //   4. solve for A_i = Sigma~_{i,N} Sigma~_N^{-1} and D_i (Sect. 4.1) and the
 //      whitened residual, giving the NLL term 1/2 log D_i + 1/2 r_i^2 / D_i,
 //   5. (gradient) contract the adjoint weights dNLL_i/dSigma~ with the
-//      covariance derivatives dSigma~/dtheta, recomputed pair by pair.
+//      covariance derivatives dSigma~/dtheta, pair by pair.
 //
 // The factor of the (m+1)-block with row i last contains everything:
 // its last row is [w^T, sqrt(D_i)] with w = L_N^{-1} k, and A_i = L_N^{-T} w.
@@ -26,10 +26,14 @@
 //
 // Mixed precision (T = float): covariance and Cholesky in FP32; one step of
 // iterative refinement of A_i whose residual k - K_N A_i is accumulated in
-// double-float arithmetic; D_i and r_i are formed in double-float; every sum
-// over rows is FP64.  Rows whose Cholesky fails in FP32, or whose condition
-// estimate (max_j L_jj / min_j L_jj)^2 exceeds tau, are flagged and redone by
-// the FP64 instantiation.
+// double-float arithmetic; D_i and r_i are formed in double-float; per-warp
+// sums over rows are double-float, combined in FP64 at the end.  The FP64
+// pipe of this part runs at 1/64 of the FP32 rate, so the mixed form keeps
+// FP64 out of the per-pair and per-row work except for forming the
+// coordinate offsets and splitting y.  Rows whose Cholesky fails in FP32,
+// whose D_i is not positive, or whose condition estimate
+// (max_j L_jj / min_j L_jj)^2 exceeds tau are flagged and redone by the FP64
+// instantiation.
 #pragma once
 
 #include <type_traits>
@@ -67,25 +71,76 @@ struct RowArgs {
   double* row_out;            // batched: per-row [6] (nll term, grad[5])
 };
 
+// Per-position record of the local block: offsets from row i, integer day
+// (valid when all times of the block are integers), used flag.
+template <typename T> struct alignas(16) Pos { T ox, oy; int td, valid; };
+
 template <typename T, int PM>
 struct WarpSm {
-  T K[PM][PM + 1];                       // local covariance (FP64: reused for L)
-  T Ls[std::is_same<T, float>::value ? PM : 1][PM + 1];  // mixed: factor L
-  alignas(16) T col[PM];                 // column broadcast during Cholesky
-  alignas(16) T v0[PM];                  // a (and a~)
-  alignas(16) T v1[PM];                  // b~
-  T ox[PM], oy[PM];                      // offsets from row i
-  double tt[PM];                         // times (non-integer lag fallback)
-  int td[PM];                            // integer days
-  int valid[PM];
+  static constexpr int KS = PM + 16 / (int)sizeof(T);   // row stride: rows 16-byte aligned
+  static constexpr int NPAIR = PM * (PM + 1) / 2;
+  static constexpr bool MIXED = std::is_same<T, float>::value;
+  alignas(16) T K[PM][KS];                          // local covariance (FP64: reused for L)
+  alignas(16) T Ls[MIXED ? PM : 1][KS];             // mixed: factor L
+  alignas(16) T col[PM];                            // column broadcast during Cholesky
+  alignas(16) T v0[PM];                             // a (refinement)
+  alignas(16) T ab[PM][2];                          // (a~, b~) per position (adjoint)
+  alignas(16) Pos<T> pos[PM];
+  alignas(16) float q1[MIXED ? NPAIR : 1];          // mixed: P x M'(x) per pair
+  alignas(16) double xe[MIXED ? 1 : NPAIR][2];      // FP64: (x, e^-x) per pair
+  double tt[PM];                                    // times (non-integer lag path)
 };
 
-template <typename T>
-__device__ __forceinline__ void lag_lookup(const RowArgs& g, const DevTheta& th, const LagD* lagd,
-                                           const LagF* lagf, bool allint, int tdr, int tdc,
-                                           double ttr, double ttc, T& P, T& G, T& Qa, T& L) {
+// Block-wide tables shared by the warps: the (r, c) position pair of each
+// packed lower-triangle index, and the first kLagSmem lags of the lag table.
+constexpr int kLagSmem = 128;
+template <typename T, int PM>
+struct BlockSm {
+  uint16_t pairs[PM * (PM + 1) / 2];
+  alignas(16) typename std::conditional<std::is_same<T, float>::value, LagF, LagD>::type lag[kLagSmem];
+};
+
+// Per-lane accumulators of the NLL and gradient sums over the rows a warp
+// processes: FP64 for the FP64 form, double-float for the mixed form.
+template <typename T> struct RowAcc;
+template <> struct RowAcc<double> {
+  double v[6];
+  __device__ void zero() {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) v[q] = 0.0;
+  }
+  __device__ void add(int q, double x) { v[q] += x; }
+  __device__ double get(int q) const { return v[q]; }
+};
+template <> struct RowAcc<float> {
+  df v[6];
+  __device__ void zero() {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) v[q] = df{0.f, 0.f};
+  }
+  __device__ void add(int q, float x) {
+    const df t = df_two_sum(v[q].hi, x);
+    v[q].hi = t.hi;
+    v[q].lo += t.lo;
+  }
+  __device__ double get(int q) const { return df_to_double(v[q]); }
+};
+
+template <typename T, typename LagS>
+__device__ __forceinline__ void lag_lookup(const DevTheta& th, const LagD* lagd, const LagF* lagf,
+                                           const LagS* lags, bool allint, int tdr, int tdc, double ttr,
+                                           double ttc, T& P, T& G, T& Qa, T& L) {
   const int lag = abs(tdr - tdc);
-  if (allint && lag < kLagTab) {
+  if (allint && lag < kLagSmem && lags != nullptr) {
+    if constexpr (std::is_same<T, float>::value) {
+      const float4 f = *reinterpret_cast<const float4*>(&lags[lag]);
+      P = f.x; G = f.y; Qa = f.z; L = f.w;
+    } else {
+      const double2 a = reinterpret_cast<const double2*>(&lags[lag])[0];
+      const double2 b = reinterpret_cast<const double2*>(&lags[lag])[1];
+      P = a.x; G = a.y; Qa = b.x; L = b.y;
+    }
+  } else if (allint && lag < kLagTab) {
     if constexpr (std::is_same<T, float>::value) {
       const float4 f = __ldg(reinterpret_cast<const float4*>(lagf) + lag);
       P = f.x; G = f.y; Qa = f.z; L = f.w;
@@ -100,14 +155,42 @@ __device__ __forceinline__ void lag_lookup(const RowArgs& g, const DevTheta& th,
   }
 }
 
-// Process one row; all 32 lanes call it together.  Returns false if the row
-// was skipped (error, or flagged for the FP64 fallback).
+template <int PM>
+__device__ __forceinline__ void pair_of(int e, int& r, int& c) {
+  const int pr = e / (PM + 1), off = e - pr * (PM + 1);
+  if (off <= pr) { r = pr; c = off; } else { r = PM - 1 - pr; c = off - pr - 1; }
+}
+
+// 16-byte vector load / store of 16 / sizeof(T) consecutive shared elements
+template <typename T, int VEC>
+__device__ __forceinline__ void ld16(T (&v)[VEC], const T* p) {
+  if constexpr (std::is_same<T, float>::value) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+  } else {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x; v[1] = q.y;
+  }
+}
+template <typename T, int VEC>
+__device__ __forceinline__ void st16(T* p, const T (&v)[VEC]) {
+  if constexpr (std::is_same<T, float>::value) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+}
+
+// Process one row; all 32 lanes call it together.
 template <typename T, int NU, int PM, int MODE>
 __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, const LagD* lagd,
-                                         const LagF* lagf, WarpSm<T, PM>& s, int64_t i, int64_t row0,
-                                         int lane, double& acc_nll, double (&acc_g)[5]) {
+                                         const LagF* lagf, const BlockSm<T, PM>* bs, bool lag_smem,
+                                         WarpSm<T, PM>& s, int64_t i, int64_t row0, int lane,
+                                         RowAcc<T>& acc) {
   constexpr bool MIXED = std::is_same<T, float>::value;
   constexpr int LAST = PM - 1;
+  constexpr int VEC = 16 / (int)sizeof(T);
+  constexpr int NPAIR = WarpSm<T, PM>::NPAIR;
   const int m = g.m;
   const int64_t gi = row0 + i;  // global row (batched form); nn indices are local
   const int cnt = g.nn_cnt[gi];
@@ -140,45 +223,73 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   const bool tint = (tj == floor(tj)) && fabs(tj) < 1.0e9;
   const bool allint = __all_sync(kFull, tint);
   if (lane < PM) {
-    s.ox[lane] = (T)(xj - xi);
-    s.oy[lane] = (T)(yj - yi);
+    Pos<T> p;
+    p.ox = (T)(xj - xi);
+    p.oy = (T)(yj - yi);
+    p.td = allint ? (int)tj : 0;
+    p.valid = valid;
+    s.pos[lane] = p;
     s.tt[lane] = tj;
-    s.td[lane] = allint ? (int)tj : 0;
-    s.valid[lane] = valid;
   }
   __syncwarp();
 
   // ---- 2. local covariance, lower triangle distributed over the lanes
-  constexpr int NPAIR = PM * (PM + 1) / 2;
-  const T diag = (T)(th.sigma1sq + th.nugget);
+  const T diag = MIXED ? (T)th.dg_hi : (T)(th.sigma1sq + th.nugget);
+  const auto* lags = lag_smem ? bs->lag : nullptr;
+#pragma unroll 2
   for (int e = lane; e < NPAIR; e += 32) {
-    const int pr = e / (PM + 1), off = e - pr * (PM + 1);
-    int r, c;
-    if (off <= pr) { r = pr; c = off; } else { r = PM - 1 - pr; c = off - pr - 1; }
+    const int rc = bs->pairs[e];
+    const int r = rc & 0xff, c = rc >> 8;
     T v;
-    const bool vr = s.valid[r], vc = s.valid[c];
+    float q1 = 0.f;
+    T xv = T(0), ev = T(1);
+    const Pos<T> pr = s.pos[r], pc = s.pos[c];
     if (r == c) {
-      v = vr ? diag : T(1);
-    } else if (!vr || !vc) {
+      v = pr.valid ? diag : T(1);
+    } else if (!pr.valid || !pc.valid) {
       v = T(0);
     } else {
-      const T dx = s.ox[r] - s.ox[c], dy = s.oy[r] - s.oy[c];
-      const T h = dsqrt<T>(dx * dx + dy * dy);
+      const T dx = pr.ox - pc.ox, dy = pr.oy - pc.oy;
+      const T d2 = dx * dx + dy * dy;
       T P, G, Qa, L;
-      lag_lookup<T>(g, th, lagd, lagf, allint, s.td[r], s.td[c], s.tt[r], s.tt[c], P, G, Qa, L);
-      const T x = G * h;
-      v = P * matern_M<NU, T>(x, dexp<T>(-x));
+      lag_lookup<T>(th, lagd, lagf, lags, allint, pr.td, pc.td, s.tt[r], s.tt[c], P, G, Qa, L);
+      if constexpr (MIXED) {
+        // FP32: h = d2 * rsqrt(d2), e^-x via the exp2 unit (relative errors
+        // of a few 1e-7, inside the mixed form's covariance error budget)
+        const float h = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
+        const float x = G * h;
+        const float E = __expf(-x);
+        v = P * matern_M<NU, float>(x, E);
+        q1 = P * matern_xdM<NU, float>(x, E);
+      } else {
+        xv = G * sqrt(d2);
+        ev = exp(-xv);
+        v = P * matern_M<NU, T>(xv, ev);
+      }
     }
     s.K[r][c] = v;
     s.K[c][r] = v;
+    if (MODE == kModeNllGrad) {
+      if constexpr (MIXED) {
+        s.q1[e] = q1;
+      } else {
+        s.xe[e][0] = xv;
+        s.xe[e][1] = ev;
+      }
+    }
   }
   __syncwarp();
 
-  // ---- 3. Cholesky, row `lane` in registers
+  // ---- 3. Cholesky, row `lane` in registers (row reads are 16-byte vectors)
   const int lj = lane < PM ? lane : PM - 1;
   T a[PM];
 #pragma unroll
-  for (int l = 0; l < PM; ++l) a[l] = s.K[l][lj];
+  for (int q = 0; q < PM; q += VEC) {
+    T tmp[VEC];
+    ld16<T, VEC>(tmp, &s.K[lj][q]);
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) a[q + u] = tmp[u];
+  }
   bool ok = true;
   T dinv = T(1);
 #pragma unroll
@@ -193,11 +304,16 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     if (lane < PM) s.col[lane] = v;
     __syncwarp();
 #pragma unroll
-    for (int l = k + 1; l < PM; ++l) a[l] = fma(-v, s.col[l], a[l]);
+    for (int q = ((k + 1) / VEC) * VEC; q < PM; q += VEC) {
+      T cv[VEC];
+      ld16<T, VEC>(cv, &s.col[q]);
+#pragma unroll
+      for (int u = 0; u < VEC; ++u)
+        if (q + u > k) a[q + u] = fma(-v, cv[u], a[q + u]);
+    }
     __syncwarp();
   }
 
-  bool fallback = false;
   if constexpr (MIXED) {
     // condition estimate from the pivots of the used positions
     const float Ljj = (lane < PM && valid) ? 1.0f / dinv : 1.0f;
@@ -209,8 +325,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       mn = fminf(mn, __shfl_xor_sync(kFull, mn, o));
     }
     const float ratio = mx / mn;
-    fallback = !ok || !(ratio * ratio <= g.tau);
-    if (fallback) {
+    if (!ok || !(ratio * ratio <= g.tau)) {
       if (lane == 0) {
         g.flag[gi] = 1;
         atomicAdd(&g.hdr->n_fallback, 1ull);
@@ -225,25 +340,30 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   }
 
   // ---- factor rows to shared memory (row-major) for the transposed solves
-  T(*Lsm)[PM + 1] = MIXED ? reinterpret_cast<T(*)[PM + 1]>(&s.Ls[0][0]) : s.K;
+  T(*Lsm)[WarpSm<T, PM>::KS] = MIXED ? reinterpret_cast<T(*)[WarpSm<T, PM>::KS]>(&s.Ls[0][0]) : s.K;
   __syncwarp();
   if (lane < PM) {
 #pragma unroll
-    for (int l = 0; l < PM; ++l) Lsm[lane][l] = a[l];
+    for (int q = 0; q < PM; q += VEC) {
+      T tmp[VEC];
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) tmp[u] = a[q + u];
+      st16<T, VEC>(&Lsm[lane][q], tmp);
+    }
   }
   __syncwarp();
   const T Llast = (T)1 / __shfl_sync(kFull, dinv, LAST);
   const T wj = (lane < LAST) ? Lsm[LAST][lane] : T(0);  // last row: L_N^{-1} k
 
-  // forward solve z = L^{-1} y_local (needed for the NLL of the FP64 form and for b)
+  // forward solve z = L^{-1} y_local (NLL of the FP64 form; b for the gradient)
   T zj = T(0);
   if ((!MIXED && MODE != kModeFactor) || MODE == kModeNllGrad) {
-    T acc = (lane < PM) ? (T)rj : T(0);
+    T accz = (lane < PM) ? (T)rj : T(0);
 #pragma unroll
     for (int k = 0; k < PM; ++k) {
-      const T zk = __shfl_sync(kFull, acc * dinv, k);
+      const T zk = __shfl_sync(kFull, accz * dinv, k);
       if (lane == k) zj = zk;
-      if (lane > k) acc = fma(-a[k], zk, acc);
+      if (lane > k) accz = fma(-a[k], zk, accz);
     }
   }
 
@@ -268,30 +388,37 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   }
 
   // ---- 4. D_i, r_i and the NLL term
-  double Dd, rd;      // FP64 values of D_i and r_i
-  T Dt, rt;           // the same in T for the adjoint weights
+  double Dd = 0.0;    // FP64 value of D_i (factor output)
+  T Dt, rt;           // D_i and r_i in T for the adjoint weights
   df a_ref = {0.f, 0.f};  // mixed: refined A_i entry of this lane
   if constexpr (MIXED) {
-    // one refinement step: res = k - K_N a (double-float), a += K_N^{-1} res
+    // One refinement step: res = k - K_N a (double-float), a += K_N^{-1} res.
+    // The FP32 diagonal is sigma1^2 + nugget rounded once, the same way for
+    // every row; the residual and D use its double-float value (dg_hi, dg_lo)
+    // so that this rounding does not bias every D_i in the same direction.
     if (lane < PM) s.v0[lane] = (lane < LAST) ? aj : 0.0f;
     __syncwarp();
-    // The FP32 diagonal is sigma1^2 + nugget rounded once, the same way for
-    // every row; the residual and D use the double-float value so that this
-    // rounding does not bias every D_i in the same direction.
-    const df dg = df_split(th.sigma1sq + th.nugget);
-    df res = {(lane < LAST) ? s.K[lj][LAST] : 0.0f, 0.0f};
+    df res = {0.0f, 0.0f};
     if (lane < LAST) {
+      res.hi = s.K[lane][LAST];
 #pragma unroll
-      for (int l = 0; l < LAST; ++l) df_fma_acc(res, -s.K[lane][l], df{s.v0[l], 0.0f});
-      if (valid) res.lo = fmaf(-dg.lo, aj, res.lo);
+      for (int q = 0; q < LAST; q += 4) {
+        float kv[4], av[4];
+        ld16<float, 4>(kv, &s.K[lane][q]);
+        ld16<float, 4>(av, &s.v0[q]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          if (q + u < LAST) df_fma_acc(res, -kv[u], df{av[u], 0.0f});
+      }
+      if (valid) res.lo = fmaf(-th.dg_lo, aj, res.lo);
     }
     const float rf = res.hi + res.lo;
-    float acc = (lane < LAST) ? rf : 0.0f, dz = 0.0f;
+    float accr = (lane < LAST) ? rf : 0.0f, dz = 0.0f;
 #pragma unroll
     for (int k = 0; k < LAST; ++k) {
-      const float zk = __shfl_sync(kFull, acc * dinv, k);
+      const float zk = __shfl_sync(kFull, accr * dinv, k);
       if (lane == k) dz = zk;
-      if (lane > k) acc = fmaf(-a[k], zk, acc);
+      if (lane > k) accr = fmaf(-a[k], zk, accr);
     }
     float acc2 = (lane < LAST) ? dz : 0.0f, da = 0.0f;
 #pragma unroll
@@ -302,44 +429,43 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     }
     a_ref = (lane < LAST) ? df{aj, da} : df{0.0f, 0.0f};
     // D = K_ii - k . a   and   r = y_i - y_N . a   in double-float
-    df Ds = (lane == LAST) ? dg : df{0.0f, 0.0f};
-    df rs = (lane == LAST) ? df_split(rj) : df{0.0f, 0.0f};
+    df Ds = (lane == LAST) ? df{th.dg_hi, th.dg_lo} : df{0.0f, 0.0f};
+    const df yl = df_split(rj);
+    df rs = (lane == LAST) ? yl : df{0.0f, 0.0f};
     if (lane < LAST) {
-      df_fma_acc(Ds, -s.K[lane][LAST], a_ref);
-      const df yl = df_split(rj);
+      df_fma_acc(Ds, -s.K[LAST][lane], a_ref);
       df_fma_acc(rs, -yl.hi, a_ref);
       rs.lo = fmaf(-yl.lo, a_ref.hi, rs.lo);
     }
     Ds = df_warp_sum(Ds);
     rs = df_warp_sum(rs);
-    Dd = df_to_double(Ds);
-    rd = df_to_double(rs);
-    Dt = (float)Dd;
-    rt = (float)rd;
-    if (!(Dd > 0.0) || !(rd == rd)) {  // lost to FP32 rounding: redo in FP64
+    Dt = Ds.hi + Ds.lo;
+    rt = rs.hi + rs.lo;
+    if (!(Dt > 0.0f) || !(rt == rt)) {  // lost to FP32 rounding: redo in FP64
       if (lane == 0) {
         g.flag[gi] = 1;
         atomicAdd(&g.hdr->n_fallback, 1ull);
       }
       return;
     }
+    if (MODE == kModeFactor) Dd = df_to_double(Ds);
     if (MODE != kModeFactor && lane == 0) {
-      const float Df = Ds.hi + Ds.lo, rf2 = rs.hi + rs.lo;
+      // log D = log(D_hi) + log(1 + D_lo / D_hi), the second term to first order
       const float logD = logf(Ds.hi) + Ds.lo / Ds.hi;
-      acc_nll += 0.5 * (double)logD + 0.5 * (double)(rf2 * rf2 / Df);
+      acc.add(0, 0.5f * logD);
+      acc.add(0, 0.5f * (rt * rt / Dt));
     }
   } else {
     const double Ll = (double)Llast;
     const double zl = __shfl_sync(kFull, (double)zj, LAST);
     Dd = Ll * Ll;
-    rd = zl * Ll;
     Dt = (T)Dd;
-    rt = (T)rd;
+    rt = (T)(zl * Ll);
     if (!(Dd > 0.0)) {
       if (lane == 0) report_error(g.hdr, VST_ENOTSPD, gi);
       return;
     }
-    if (MODE != kModeFactor && lane == 0) acc_nll += log(Ll) + 0.5 * zl * zl;
+    if (MODE != kModeFactor && lane == 0) acc.add(0, log(Ll) + 0.5 * zl * zl);
   }
 
   if (MODE == kModeFactor) {
@@ -360,56 +486,85 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     if (lane < PM) {
       const T at = (lane < cnt) ? -aj : (lane == LAST ? T(1) : T(0));
       const T bt = (lane < cnt) ? bj : T(0);
-      s.v0[lane] = at;
-      s.v1[lane] = bt;
+      s.ab[lane][0] = at;
+      s.ab[lane][1] = bt;
     }
     __syncwarp();
-    T g0 = 0, g1 = 0, g2 = 0, g3 = 0, g4 = 0;
-    const T inv_s1 = T(1.0 / th.sigma1sq), inv_c = T(1.0 / th.c);
-    const T pexp = (T)th.p, hg = (T)(0.5 * th.gamma);
+    // off-diagonal sums of w K and w X are scaled by 1/sigma1^2 and 1/c at the end
+    T gd = 0, g0 = 0, g1 = 0, g2 = 0, g3 = 0;
+    const T pexp = (T)th.p, hg = (T)(0.5 * th.gamma), hc2 = T(0.5) * c2;
+#pragma unroll 2
     for (int e = lane; e < NPAIR; e += 32) {
-      const int pr = e / (PM + 1), off = e - pr * (PM + 1);
-      int r, c;
-      if (off <= pr) { r = pr; c = off; } else { r = PM - 1 - pr; c = off - pr - 1; }
-      if (!s.valid[r] || !s.valid[c]) continue;
-      const T ar = s.v0[r], ac = s.v0[c], br = s.v1[r], bc = s.v1[c];
-      T w = c1 * ar * ac - c2 * T(0.5) * (ar * bc + br * ac);
+      const int rc = bs->pairs[e];
+      const int r = rc & 0xff, c = rc >> 8;
+      const Pos<T> pr = s.pos[r], pc = s.pos[c];
+      if (!pr.valid || !pc.valid) continue;
+      const T ar = s.ab[r][0], br = s.ab[r][1], ac = s.ab[c][0], bc = s.ab[c][1];
+      const T w = ar * (c1 * ac - hc2 * bc) - hc2 * br * ac;
       if (r == c) {
-        g0 += w;  // dC(0,0)/dsigma1^2 = 1
-        g4 += w;  // nugget
+        gd += w;  // dC(0,0)/dsigma1^2 = 1 and d/dnugget = 1
       } else {
-        w *= T(2);
-        const T dx = s.ox[r] - s.ox[c], dy = s.oy[r] - s.oy[c];
-        const T h = dsqrt<T>(dx * dx + dy * dy);
         T P, G, Qa, L;
-        lag_lookup<T>(g, th, lagd, lagf, allint, s.td[r], s.td[c], s.tt[r], s.tt[c], P, G, Qa, L);
-        const T x = G * h;
-        const T E = dexp<T>(-x);
-        const T M = matern_M<NU, T>(x, E), xM = matern_xdM<NU, T>(x, E);
-        const T wP = w * P;
-        g0 = fma(wP * M, inv_s1, g0);
-        g1 = fma(wP * xM, inv_c, g1);
-        g2 = fma(wP * Qa, -pexp * M - hg * xM, g2);
-        g3 = fma(-wP * L, M + T(0.5) * xM, g3);
+        lag_lookup<T>(th, lagd, lagf, lags, allint, pr.td, pc.td, s.tt[r], s.tt[c], P, G, Qa, L);
+        T Kv, Xv;  // P M(x) and P x M'(x)
+        if constexpr (MIXED) {
+          Kv = s.K[r][c];
+          Xv = s.q1[e];
+        } else {
+          const T x = s.xe[e][0], E = s.xe[e][1];
+          Kv = P * matern_M<NU, T>(x, E);
+          Xv = P * matern_xdM<NU, T>(x, E);
+        }
+        const T w2 = w + w;
+        g0 = fma(w2, Kv, g0);
+        g1 = fma(w2, Xv, g1);
+        g2 = fma(w2 * Qa, -pexp * Kv - hg * Xv, g2);
+        g3 = fma(-w2 * L, Kv + T(0.5) * Xv, g3);
       }
     }
-    acc_g[0] += (double)g0;
-    acc_g[1] += (double)g1;
-    acc_g[2] += (double)g2;
-    acc_g[3] += (double)g3;
-    acc_g[4] += (double)g4;
+    const T inv_s1 = T(1.0 / th.sigma1sq), inv_c = T(1.0 / th.c);
+    acc.add(1, fma(g0, inv_s1, gd));
+    acc.add(2, g1 * inv_c);
+    acc.add(3, g2);
+    acc.add(4, g3);
+    acc.add(5, gd);
   }
 }
 
+template <typename T, int PM>
+__host__ __device__ constexpr size_t block_sm_bytes() {
+  return (sizeof(BlockSm<T, PM>) + 15) / 16 * 16;
+}
+
+template <typename T, int PM, int WARPS>
+__host__ __device__ constexpr size_t rows_smem_bytes() {
+  return block_sm_bytes<T, PM>() + sizeof(WarpSm<T, PM>) * WARPS;
+}
+
 template <typename T, int NU, int PM, int MODE, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) rows_kernel(RowArgs g) {
+__global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) rows_kernel(RowArgs g) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  WarpSm<T, PM>* sm = reinterpret_cast<WarpSm<T, PM>*>(smem_raw);
+  BlockSm<T, PM>* bs = reinterpret_cast<BlockSm<T, PM>*>(smem_raw);
+  WarpSm<T, PM>* sm = reinterpret_cast<WarpSm<T, PM>*>(smem_raw + block_sm_bytes<T, PM>());
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpSm<T, PM>& s = sm[wib];
+  for (int e = threadIdx.x; e < WarpSm<T, PM>::NPAIR; e += WARPS * 32) {
+    int r, c;
+    pair_of<PM>(e, r, c);
+    bs->pairs[e] = (uint16_t)(r | (c << 8));
+  }
+  if (g.offsets == nullptr) {
+    for (int u = threadIdx.x; u < kLagSmem; u += WARPS * 32) {
+      if constexpr (std::is_same<T, float>::value) bs->lag[u] = g.lagf[u];
+      else bs->lag[u] = g.lagd[u];
+    }
+  }
+  __syncthreads();
+  const BlockSm<T, PM>* bsc = bs;
   const int64_t warp = (int64_t)blockIdx.x * WARPS + wib;
   const int64_t total = (int64_t)gridDim.x * WARPS;
-  double acc_nll = 0.0, acc_g[5] = {0, 0, 0, 0, 0};
+  RowAcc<T> acc;
+  acc.zero();
 
   if (g.offsets == nullptr) {
     const int64_t n = g.n;
@@ -418,33 +573,32 @@ __global__ void __launch_bounds__(WARPS * 32) rows_kernel(RowArgs g) {
     if (any) {
       for (int64_t i = warp; i < n; i += total) {
         if (g.fallback_only && g.flag[i] == 0) continue;
-        row_body<T, NU, PM, MODE>(g, g.th, g.lagd, g.lagf, s, i, 0, lane, acc_nll, acc_g);
+        row_body<T, NU, PM, MODE>(g, g.th, g.lagd, g.lagf, bsc, true, s, i, 0, lane, acc);
       }
     }
-    // fixed-order reduction of this warp's partial sums
-    double v[6] = {acc_nll, acc_g[0], acc_g[1], acc_g[2], acc_g[3], acc_g[4]};
+    // fixed-order reduction of this warp's partial sums (FP64)
+    double v[6];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) v[q] = warp_sum(v[q]);
+    for (int q = 0; q < 6; ++q) v[q] = warp_sum(acc.get(q));
     if (lane == 0) {
 #pragma unroll
       for (int q = 0; q < 6; ++q) g.partial[warp * 8 + q] = v[q];
     }
   } else {
-    // batched form: global rows across datasets, per-row outputs
+    // batched form: global rows across datasets, per-row outputs; the lag
+    // table differs per dataset, so only the pair table is shared
     const int64_t n = g.offsets[g.nsets];
     int set = 0;
     for (int64_t gi = warp; gi < n; gi += total) {
       if (g.fallback_only && g.flag[gi] == 0) continue;
       while (set + 1 < g.nsets && g.offsets[set + 1] <= gi) ++set;
       const int64_t row0 = g.offsets[set];
-      acc_nll = 0.0;
-      acc_g[0] = acc_g[1] = acc_g[2] = acc_g[3] = acc_g[4] = 0.0;
+      acc.zero();
       row_body<T, NU, PM, MODE>(g, g.thetas[set], g.lagd_sets + (int64_t)set * kLagTab,
-                                g.lagf_sets + (int64_t)set * kLagTab, s, gi - row0, row0, lane, acc_nll,
-                                acc_g);
-      double v[6] = {acc_nll, acc_g[0], acc_g[1], acc_g[2], acc_g[3], acc_g[4]};
+                                g.lagf_sets + (int64_t)set * kLagTab, bsc, false, s, gi - row0, row0, lane, acc);
+      double v[6];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) v[q] = warp_sum(v[q]);
+      for (int q = 0; q < 6; ++q) v[q] = warp_sum(acc.get(q));
       if (lane == 0 && !(g.flag != nullptr && !g.fallback_only && g.flag[gi])) {
 #pragma unroll
         for (int q = 0; q < 6; ++q) g.row_out[gi * 6 + q] = v[q];

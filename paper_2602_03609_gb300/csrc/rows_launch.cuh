@@ -9,7 +9,7 @@ namespace vst {
 template <typename T, int NU, int PM, int MODE>
 static cudaError_t launch_one(const RowArgs& g, cudaStream_t st, int64_t* warps_out) {
   auto kern = rows_kernel<T, NU, PM, MODE, kRowWarps>;
-  const size_t smem = sizeof(WarpSm<T, PM>) * kRowWarps;
+  const size_t smem = rows_smem_bytes<T, PM, kRowWarps>();
   static int grid = 0;  // resident blocks x SMs, computed once per kernel
   if (grid == 0) {
     int dev = 0, sms = 0, per_sm = 0;
