@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--workload", default="continental", choices=["continental", "box", "tiny"])
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-baseline leg")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-datasets leg")
     return ap.parse_args()
 
 
@@ -136,6 +137,56 @@ class Clocks:
         if not sm:
             return None
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def batched_leg(vst, torch, dev, steps):
+    """64 independent datasets (n_d log-uniform in [5e3, 5e4], m = 20, own
+    parameters each): neighbours and responses per dataset, then one captured
+    CUDA graph of the batched NLL + gradient (one persistent launch), launch
+    shape autotuned first.  One step = all datasets evaluated once."""
+    import synthetic_inputs as si
+    sets = si.batched()
+    m = sets[0].m
+    xs, ts, ys, nns, cnts, ths = [], [], [], [], [], []
+    for w in sets:
+        th = vst.vst_theta_from_ranges(*w.theta.astuple())
+        xy = torch.from_numpy(w.xy).to(dev)
+        t = torch.from_numpy(w.t).to(dev)
+        ws = vst.Workspace(w.n, m, device=dev)
+        nn, cnt = vst.vif_build_neighbors(xy, t, th, m, ws=ws)
+        y = vst.vecchia_sample(xy, t, th, m, nn, cnt, torch.from_numpy(w.z).to(dev), ws=ws)
+        vst.vst_workspace_status(ws)
+        xs.append(xy); ts.append(t); ys.append(y); nns.append(nn); cnts.append(cnt); ths.append(th)
+    offs = torch.tensor(np.concatenate([[0], np.cumsum([w.n for w in sets])]), dtype=torch.int64, device=dev)
+    xy, t, y = torch.cat(xs), torch.cat(ts), torch.cat(ys)
+    nn, cnt = torch.cat(nns), torch.cat(cnts)
+    thetas = torch.tensor(ths, dtype=torch.float64, device=dev)
+    ns, n = len(sets), int(t.shape[0])
+    ws = vst.BatchedWorkspace(ns, n, m, device=dev)
+    shape = vst.vst_autotune_nll_grad_batched(offs, thetas, 1.5, xy, t, m, nn, cnt, y, precision=vst.MIXED, ws=ws)
+    nll = torch.empty(ns, dtype=torch.float64, device=dev)
+    grad = torch.empty((ns, 5), dtype=torch.float64, device=dev)
+    out = {}
+    for name, prec in (("mixed", vst.MIXED), ("fp64", vst.FP64)):
+        gr = vst.BatchedGraph(offs, thetas, 1.5, xy, t, m, nn, cnt, y, prec, nll, grad, ws)
+        k = steps if prec == vst.MIXED else max(2, steps // 5)
+        for _ in range(3):
+            gr.launch()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(k):
+            gr.launch()
+        b.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b) / k
+        vst.vst_workspace_status(ws)
+        out[name] = {"value": 1e3 / ms, "unit": "batch evals/s", "ms": ms, "nll_sum": float(nll.sum().item())}
+        gr.close()
+    out["workload"] = f"{ns} datasets, {n} points, m={m}, per-dataset parameters, one graph-captured launch"
+    out["autotuned_shape"] = {"blocks_per_sm": shape[0], "row_chunk": shape[1]}
+    out["dnll_per_n_mixed_vs_fp64"] = abs(out["mixed"]["nll_sum"] - out["fp64"]["nll_sum"]) / n
+    return out
 
 
 def cpu_baseline(w, th, seconds_hint=True):
@@ -356,6 +407,8 @@ def run_ours(args):
         "gpu_launches": 5 * args.steps,
         "clocks": clk,
     }
+    if not args.no_batched:
+        line["batched"] = batched_leg(vst, torch, dev, args.steps)
     if not args.no_baseline:
         import oracle  # CPU-baseline leg only
         line["cpu_baseline"] = cpu_baseline(w, oracle.theta_native(w.theta))

@@ -165,6 +165,66 @@ vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m
                             const double* y, int precision, double* nll, double* grad,
                             void* workspace, size_t ws_bytes, void* stream);
 
+/* Batched NLL and gradient of nsets independent datasets (one Vecchia model
+ * each, Sect. 4.1 and 3.1) in one persistent launch.  Dataset d owns rows
+ * offsets[d] .. offsets[d+1]-1 of the concatenated arrays xy, t, y, nn,
+ * nn_cnt (layouts as above); its neighbour indices are local to the dataset
+ * (0 = its first row).  offsets: nsets+1 int64 DEVICE values, offsets[0] = 0,
+ * non-decreasing, offsets[nsets] = n_total.  thetas: nsets vst_theta in
+ * DEVICE memory (so that a captured graph can be replayed after the caller
+ * updates them in place); every dataset must use the same nu, passed as
+ * `nu`.  nll: nsets FP64 device outputs; grad: [nsets][5] FP64 device
+ * outputs (sigma1sq, c, a, gamma, nugget order).  Invalid offsets or
+ * parameters are found on the device: vst_workspace_status then reports
+ * VST_EINVAL with bad_row = the dataset index (or -2 for the offsets).
+ * Workspace: vst_workspace_size_batched(nsets, n_total, m) bytes. */
+size_t vst_workspace_size_batched(int nsets, int64_t n_total, int m);
+vst_status vecchia_nll_grad_batched(int nsets, int64_t n_total, const int64_t* offsets,
+                                    const vst_theta* thetas, double nu, const double* xy,
+                                    const double* t, int m, const int32_t* nn, const int32_t* nn_cnt,
+                                    const double* y, int precision, double* nll, double* grad,
+                                    void* workspace, size_t ws_bytes, void* stream);
+
+/* A CUDA graph holding one vecchia_nll_grad_batched evaluation with the
+ * given (device) buffers, captured once and replayed by vst_graph_launch on
+ * any stream.  Replays read the buffers' current contents, so parameters,
+ * responses or coordinates may be updated in place between replays; sizes,
+ * pointers, m, nu and precision are fixed at capture.  The capture runs the
+ * evaluation once (synchronously) before capturing it. */
+typedef struct vst_graph_s* vst_graph;
+vst_status vst_graph_capture_nll_grad_batched(int nsets, int64_t n_total, const int64_t* offsets,
+                                              const vst_theta* thetas, double nu, const double* xy,
+                                              const double* t, int m, const int32_t* nn,
+                                              const int32_t* nn_cnt, const double* y, int precision,
+                                              double* nll, double* grad, void* workspace,
+                                              size_t ws_bytes, vst_graph* out);
+vst_status vst_graph_launch(vst_graph graph, void* stream);
+vst_status vst_graph_destroy(vst_graph graph);
+
+/* Launch-shape autotuner.  Times the row kernel's launch shapes (resident
+ * blocks per SM in {1, 2, 3, all that fit} x consecutive rows per warp in
+ * {1, 4, 16, 64}) on the caller's inputs, keeps the fastest in the library's
+ * tuned-shape cache (its only state across calls, keyed by batched/single,
+ * precision, nu and the padded block size) and returns it.  Synchronises the
+ * stream.  The environment variables VST_BLOCKS_PER_SM and VST_ROW_CHUNK
+ * override the cache.  Results do not depend on the shape beyond rounding. */
+typedef struct {
+  int blocks_per_sm;  /* 0 = as many as fit */
+  int row_chunk;
+  float ms;           /* time of one evaluation with this shape */
+} vst_tune_result;
+vst_status vst_autotune_nll_grad(const vst_points* pts, const vst_theta* theta, int m,
+                                 const int32_t* nn, const int32_t* nn_cnt, const double* y,
+                                 int precision, void* workspace, size_t ws_bytes, void* stream,
+                                 vst_tune_result* out);
+vst_status vst_autotune_nll_grad_batched(int nsets, int64_t n_total, const int64_t* offsets,
+                                         const vst_theta* thetas, double nu, const double* xy,
+                                         const double* t, int m, const int32_t* nn,
+                                         const int32_t* nn_cnt, const double* y, int precision,
+                                         double* nll, double* grad, void* workspace, size_t ws_bytes,
+                                         void* stream, vst_tune_result* out);
+void vst_autotune_clear(void);
+
 /* Draw y = B^{-1} D^{1/2} z, a sample of the Vecchia-approximated response
  * (y_i = A_i y_N(i) + sqrt(D_i) z_i in row order), with the FP64 factor of
  * (pts, theta, nn).  z: n FP64 device values; y: n FP64 device outputs. */

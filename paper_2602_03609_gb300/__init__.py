@@ -28,6 +28,8 @@ __all__ = [
     "Workspace", "vif_build_neighbors", "vecchia_factor", "vecchia_nll", "vecchia_nll_grad",
     "vecchia_sample", "vst_workspace_status", "VecchiaNLL", "theta_tuple", "vst_profile_enable",
     "vst_profile_read", "vecchia_nll_grad_noalloc", "vst_noalloc_status", "NOALLOC_MAX_N",
+    "BatchedWorkspace", "vecchia_nll_grad_batched", "BatchedGraph", "vst_autotune_nll_grad",
+    "vst_autotune_nll_grad_batched", "vst_autotune_clear",
 ]
 
 FP64 = 0
@@ -65,6 +67,10 @@ class WsInfo(ctypes.Structure):
 
     def asdict(self):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class TuneResult(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_int), ("row_chunk", ctypes.c_int), ("ms", ctypes.c_float)]
 
 
 _lib = None
@@ -109,6 +115,26 @@ def lib():
         L.vst_noalloc_scratch_bytes.argtypes = []
         L.vst_noalloc_status.restype = ctypes.c_int
         L.vst_noalloc_status.argtypes = [_P, ctypes.POINTER(WsInfo)]
+        I64 = ctypes.c_int64
+        L.vst_workspace_size_batched.restype = ctypes.c_size_t
+        L.vst_workspace_size_batched.argtypes = [ctypes.c_int, I64, ctypes.c_int]
+        bargs = [ctypes.c_int, I64, _P, _P, ctypes.c_double, _P, _P, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, _P,
+                 _P, ctypes.c_size_t]
+        L.vecchia_nll_grad_batched.restype = ctypes.c_int
+        L.vecchia_nll_grad_batched.argtypes = bargs + [_P]
+        L.vst_graph_capture_nll_grad_batched.restype = ctypes.c_int
+        L.vst_graph_capture_nll_grad_batched.argtypes = bargs + [ctypes.POINTER(ctypes.c_void_p)]
+        L.vst_graph_launch.restype = ctypes.c_int
+        L.vst_graph_launch.argtypes = [_P, _P]
+        L.vst_graph_destroy.restype = ctypes.c_int
+        L.vst_graph_destroy.argtypes = [_P]
+        L.vst_autotune_nll_grad.restype = ctypes.c_int
+        L.vst_autotune_nll_grad.argtypes = [PT, TH, ctypes.c_int, _P, _P, _P, ctypes.c_int, _P, ctypes.c_size_t, _P,
+                                            ctypes.POINTER(TuneResult)]
+        L.vst_autotune_nll_grad_batched.restype = ctypes.c_int
+        L.vst_autotune_nll_grad_batched.argtypes = bargs + [_P, ctypes.POINTER(TuneResult)]
+        L.vst_autotune_clear.restype = None
+        L.vst_autotune_clear.argtypes = []
         L.vst_workspace_status.restype = ctypes.c_int
         L.vst_workspace_status.argtypes = [_P, _P, ctypes.POINTER(WsInfo)]
         _lib = L
@@ -242,6 +268,104 @@ def vecchia_nll_grad(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, nll=None, g
                                   _ptr(y, torch.float64, "y"), int(precision), _ptr(nll, torch.float64, "nll"),
                                   _ptr(grad, torch.float64, "grad"), ws.ptr, ws.nbytes, _stream(stream)))
     return nll, grad
+
+
+class BatchedWorkspace(Workspace):
+    """Workspace of the batched entry points."""
+
+    def __init__(self, nsets, n_total, m, device=None):
+        self.nbytes = int(lib().vst_workspace_size_batched(int(nsets), int(n_total), int(m)))
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+        self.ptr = (self.buf.data_ptr() + 255) // 256 * 256
+
+    def fits(self, nsets, n_total, m):
+        return self.nbytes >= int(lib().vst_workspace_size_batched(int(nsets), int(n_total), int(m)))
+
+
+def _batched_args(offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, precision, nll, grad, ws):
+    nsets = offsets.numel() - 1
+    n = t.shape[0]
+    if thetas.shape != (nsets, 8):
+        raise ValueError("thetas must be a CUDA float64 tensor [nsets, 8] "
+                         "(sigma1sq, c, a, gamma, nugget, alpha, delta, nu)")
+    if xy.shape != (n, 2):
+        raise ValueError("xy must be [n, 2]")
+    if not ws.fits(nsets, n, m):
+        raise ValueError("workspace too small")
+    return [nsets, n, _ptr(offsets, torch.int64, "offsets"), _ptr(thetas, torch.float64, "thetas"), float(nu),
+            _ptr(xy, torch.float64, "xy"), _ptr(t, torch.float64, "t"), int(m), _ptr(nn, torch.int32, "nn"),
+            _ptr(nn_cnt, torch.int32, "nn_cnt"), _ptr(y, torch.float64, "y"), int(precision),
+            _ptr(nll, torch.float64, "nll"), _ptr(grad, torch.float64, "grad"), ws.ptr, ws.nbytes]
+
+
+def vecchia_nll_grad_batched(offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, precision=FP64, nll=None, grad=None,
+                             ws=None, stream=None):
+    """NLL [nsets] and gradient [nsets, 5] of independent datasets in one launch.
+    offsets: CUDA int64 [nsets+1]; thetas: CUDA float64 [nsets, 8]; neighbour
+    indices local to each dataset."""
+    nsets = offsets.numel() - 1
+    nll = nll if nll is not None else torch.empty(nsets, dtype=torch.float64, device=t.device)
+    grad = grad if grad is not None else torch.empty((nsets, 5), dtype=torch.float64, device=t.device)
+    ws = ws if ws is not None else BatchedWorkspace(nsets, t.shape[0], m)
+    args = _batched_args(offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, precision, nll, grad, ws)
+    _check(lib().vecchia_nll_grad_batched(*args, _stream(stream)))
+    return nll, grad
+
+
+class BatchedGraph:
+    """A captured CUDA graph of one batched evaluation (vst_graph_*)."""
+
+    def __init__(self, offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, precision, nll, grad, ws):
+        self._keep = (offsets, thetas, xy, t, nn, nn_cnt, y, nll, grad, ws)
+        self.nll, self.grad = nll, grad
+        h = ctypes.c_void_p(None)
+        args = _batched_args(offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, precision, nll, grad, ws)
+        _check(lib().vst_graph_capture_nll_grad_batched(*args, ctypes.byref(h)))
+        self._h = h
+
+    def launch(self, stream=None):
+        _check(lib().vst_graph_launch(self._h, _stream(stream)))
+        return self.nll, self.grad
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().vst_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def vst_autotune_nll_grad(xy, t, theta, m, nn, nn_cnt, y, precision=MIXED, ws=None, stream=None):
+    """Pick and cache the fastest launch shape; returns (blocks_per_sm, row_chunk, ms)."""
+    n = t.shape[0]
+    ws = _ws(ws, n, m)
+    pts = _points(xy, t)
+    r = TuneResult()
+    _check(lib().vst_autotune_nll_grad(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m),
+                                       _ptr(nn, torch.int32, "nn"), _ptr(nn_cnt, torch.int32, "nn_cnt"),
+                                       _ptr(y, torch.float64, "y"), int(precision), ws.ptr, ws.nbytes,
+                                       _stream(stream), ctypes.byref(r)))
+    return r.blocks_per_sm, r.row_chunk, r.ms
+
+
+def vst_autotune_nll_grad_batched(offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, precision=MIXED, nll=None,
+                                  grad=None, ws=None, stream=None):
+    nsets = offsets.numel() - 1
+    nll = nll if nll is not None else torch.empty(nsets, dtype=torch.float64, device=t.device)
+    grad = grad if grad is not None else torch.empty((nsets, 5), dtype=torch.float64, device=t.device)
+    ws = ws if ws is not None else BatchedWorkspace(nsets, t.shape[0], m)
+    args = _batched_args(offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, precision, nll, grad, ws)
+    r = TuneResult()
+    _check(lib().vst_autotune_nll_grad_batched(*args, _stream(stream), ctypes.byref(r)))
+    return r.blocks_per_sm, r.row_chunk, r.ms
+
+
+def vst_autotune_clear():
+    lib().vst_autotune_clear()
 
 
 NOALLOC_MAX_N = 1 << 21

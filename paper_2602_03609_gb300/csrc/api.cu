@@ -15,6 +15,9 @@ namespace vst {
 
 static thread_local std::string g_last_error;
 
+void apply_launch_shape(RowArgs& g, int batched, int precision, int nu, int pm);
+void forced_launch_shape(RowArgs& g);
+
 vst_status fail(vst_status s, const char* fmt, ...) {
   char buf[512];
   va_list ap;
@@ -188,6 +191,8 @@ vst_status run_rows(const vst_points* pts, const vst_theta* theta, int m, const 
   g.tau = 1.0e4f;
   g.offsets = nullptr;
   const int pm = m + 1;
+  apply_launch_shape(g, 0, precision, nu, pm);
+  forced_launch_shape(g);
   int64_t w0 = 0, w1 = 0;
   if (n > 0) {
     g.partial = part0;

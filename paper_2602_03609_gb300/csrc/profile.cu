@@ -31,6 +31,8 @@ void clear() {
 
 ProfileScope::ProfileScope(int cls, cudaStream_t st) : cls_(cls), st_(st), rec_(-1) {
   if (!g_on || cls < 0 || cls >= kClasses) return;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return;
   ++g_count[cls];
   if ((int)g_recs.size() >= kMaxRecords) {
     ++g_dropped[cls];

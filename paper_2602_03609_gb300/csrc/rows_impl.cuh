@@ -69,6 +69,8 @@ struct RowArgs {
   const LagF* lagf_sets;
   int nsets;
   double* row_out;            // batched: per-row [6] (nll term, grad[5])
+  int row_chunk;              // consecutive rows per warp assignment (>= 1)
+  int blocks_per_sm;          // launch shape: resident blocks per SM (0 = as many as fit)
 };
 
 // Per-position record of the local block: offsets from row i, integer day
@@ -571,9 +573,13 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) rows_kernel(RowArgs g)
     bool any = true;
     if (g.fallback_only) any = g.hdr->n_fallback != 0ull;
     if (any) {
-      for (int64_t i = warp; i < n; i += total) {
-        if (g.fallback_only && g.flag[i] == 0) continue;
-        row_body<T, NU, PM, MODE>(g, g.th, g.lagd, g.lagf, bsc, true, s, i, 0, lane, acc);
+      const int64_t chunk = g.row_chunk > 0 ? g.row_chunk : 1;
+      for (int64_t base = warp * chunk; base < n; base += total * chunk) {
+        const int64_t end = base + chunk < n ? base + chunk : n;
+        for (int64_t i = base; i < end; ++i) {
+          if (g.fallback_only && g.flag[i] == 0) continue;
+          row_body<T, NU, PM, MODE>(g, g.th, g.lagd, g.lagf, bsc, true, s, i, 0, lane, acc);
+        }
       }
     }
     // fixed-order reduction of this warp's partial sums (FP64)
@@ -587,21 +593,41 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) rows_kernel(RowArgs g)
   } else {
     // batched form: global rows across datasets, per-row outputs; the lag
     // table differs per dataset, so only the pair table is shared
-    const int64_t n = g.offsets[g.nsets];
+    // rows beyond the caller's n are never touched, whatever the offsets hold
+    const int64_t n = g.offsets[g.nsets] < g.n ? g.offsets[g.nsets] : g.n;
+    const int64_t chunk = g.row_chunk > 0 ? g.row_chunk : 1;
     int set = 0;
-    for (int64_t gi = warp; gi < n; gi += total) {
-      if (g.fallback_only && g.flag[gi] == 0) continue;
-      while (set + 1 < g.nsets && g.offsets[set + 1] <= gi) ++set;
-      const int64_t row0 = g.offsets[set];
-      acc.zero();
-      row_body<T, NU, PM, MODE>(g, g.thetas[set], g.lagd_sets + (int64_t)set * kLagTab,
-                                g.lagf_sets + (int64_t)set * kLagTab, bsc, false, s, gi - row0, row0, lane, acc);
-      double v[6];
+    for (int64_t base = warp * chunk; base < n; base += total * chunk) {
+      const int64_t end = base + chunk < n ? base + chunk : n;
+      for (int64_t gi = base; gi < end; ++gi) {
+        if (g.fallback_only && g.flag[gi] == 0) continue;
+        while (set + 1 < g.nsets && g.offsets[set + 1] <= gi) ++set;
+        const int64_t row0 = g.offsets[set];
+        acc.zero();
+        row_body<T, NU, PM, MODE>(g, g.thetas[set], g.lagd_sets + (int64_t)set * kLagTab,
+                                  g.lagf_sets + (int64_t)set * kLagTab, bsc, false, s, gi - row0, row0, lane,
+                                  acc);
+        // per-row results: FP64 rows as double[6]; mixed rows as double-float
+        // pairs float2[6] (same 48 bytes), combined by the segmented reduction
+        const bool skip = g.flag != nullptr && !g.fallback_only && g.flag[gi];
+        if constexpr (std::is_same<T, float>::value) {
+          df v[6];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) v[q] = warp_sum(acc.get(q));
-      if (lane == 0 && !(g.flag != nullptr && !g.fallback_only && g.flag[gi])) {
+          for (int q = 0; q < 6; ++q) v[q] = df_warp_sum(acc.v[q]);
+          if (lane == 0 && !skip) {
+            float2* o = reinterpret_cast<float2*>(g.row_out + gi * 6);
 #pragma unroll
-        for (int q = 0; q < 6; ++q) g.row_out[gi * 6 + q] = v[q];
+            for (int q = 0; q < 6; ++q) o[q] = make_float2(v[q].hi, v[q].lo);
+          }
+        } else {
+          double v[6];
+#pragma unroll
+          for (int q = 0; q < 6; ++q) v[q] = warp_sum(acc.get(q));
+          if (lane == 0 && !skip) {
+#pragma unroll
+            for (int q = 0; q < 6; ++q) g.row_out[gi * 6 + q] = v[q];
+          }
+        }
       }
     }
   }

@@ -22,8 +22,17 @@ static cudaError_t launch_one(const RowArgs& g, cudaStream_t st, int64_t* warps_
     int64_t gmax = kMaxPartialWarps / kRowWarps;
     grid = (int)std::min<int64_t>((int64_t)per_sm * sms, gmax);
   }
-  kern<<<grid, kRowWarps * 32, smem, st>>>(g);
-  *warps_out = (int64_t)grid * kRowWarps;
+  static int per_sm_max = 0, sms_count = 0;
+  if (per_sm_max == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms_count, cudaDevAttrMultiProcessorCount, dev);
+    per_sm_max = std::max(1, grid / std::max(1, sms_count));
+  }
+  int launch_grid = grid;
+  if (g.blocks_per_sm > 0 && g.blocks_per_sm < per_sm_max) launch_grid = g.blocks_per_sm * sms_count;
+  kern<<<launch_grid, kRowWarps * 32, smem, st>>>(g);
+  *warps_out = (int64_t)launch_grid * kRowWarps;
   return cudaGetLastError();
 }
 
