@@ -1,0 +1,136 @@
+"""VIF oracle: the Vecchia-inducing-point full-scale approximation (Sect. 4.3).
+
+TEST INFRASTRUCTURE (see oracle/__init__.py).  Plain numpy/scipy, FP64, for
+small n (dense k x k algebra, per-row loops).  Library primitives (Cholesky,
+triangular solve) are used as steps; everything else is written out.
+
+Model (reading recorded in the design doc): the latent process is b = b_l + b_s
+with the predictive-process part Cov(b_l) = Sigma_nk Sigma_kk^{-1} Sigma_kn
+(k inducing points) and the residual Cov(b_s) = Sigma - Sigma_nk Sigma_kk^{-1}
+Sigma_kn.  The residual plus the nugget, R~ = Cov(b_s) + sigma^2 I, is
+Vecchia-approximated with the residual coefficients A_i, D_i of Sect. 4.3
+(nugget on the diagonal), so the response covariance is
+
+    Sigma~_VIF = U U^T + B^{-1} D B^{-T},   U = Sigma_nk L_kk^{-T},  L_kk L_kk^T = Sigma_kk.
+
+Neighbours are chosen by the residual correlation |R_ij| / sqrt(R_ii R_jj)
+(the d_c metric of Sect. 4.4.1 applied to Cov(b_s), no nugget).  The NLL is
+evaluated with the Sherman-Woodbury-Morrison identity (the complexity remark
+at the end of Sect. 4.3):
+
+    W = D^{-1/2} B U,  e = D^{-1/2} B y,  M = I_k + W^T W,
+    log det Sigma~_VIF = sum_i log D_i + log det M,
+    y^T Sigma~_VIF^{-1} y = e^T e - (W^T e)^T M^{-1} (W^T e).
+
+Pinned by (tests/test_oracle_vif.py): m = n-1 gives the exact GP likelihood
+for any k; k = 0 gives plain Vecchia; m = 0 gives the dense FITC likelihood
+(Sect. 4.2); the Woodbury value equals the dense Sigma~_VIF likelihood.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+
+from . import cov_matrix
+
+
+def lowrank(xy, t, xyk, tk, theta):
+    """U = Sigma_nk L_kk^{-T} (n x k), residual variances r_i = Sigma_ii - ||U_i||^2."""
+    n, k = t.shape[0], (tk.shape[0] if tk is not None else 0)
+    if k == 0:
+        return np.zeros((n, 0)), np.full(n, theta[0])
+    Skk = cov_matrix(xyk, tk, xyk, tk, theta)
+    Snk = cov_matrix(xy, t, xyk, tk, theta)
+    L = np.linalg.cholesky(Skk)
+    U = sla.solve_triangular(L, Snk.T, lower=True).T
+    r = theta[0] - (U * U).sum(1)
+    return U, r
+
+
+def residual_block(xy, t, theta, U, rows, cols):
+    """Latent residual covariance R[rows, cols] = Sigma - U U^T (no nugget)."""
+    C = cov_matrix(xy[rows], t[rows], xy[cols], t[cols], theta)
+    return C - U[rows] @ U[cols].T
+
+
+def knn(xy, t, theta, U, r, m):
+    """Brute-force residual-correlation neighbours: for each i, the min(i, m)
+    predecessors with the largest |R_ij| / sqrt(R_ii R_jj); ties -> smaller
+    index; sorted by decreasing |rho|.  A point whose residual variance is at
+    most 1e-12 sigma1^2 (an inducing point on top of it) has no defined
+    residual correlation; it is taken as 0 (the design doc reading).
+    Returns nn, cnt, rho_m, rho_m1."""
+    n = t.shape[0]
+    nn = np.full((n, m), -1, dtype=np.int32)
+    cnt = np.zeros(n, dtype=np.int32)
+    rm = np.full(n, np.nan)
+    rm1 = np.full(n, np.nan)
+    for i in range(1, n):
+        j = np.arange(i)
+        R = residual_block(xy, t, theta, U, np.array([i]), j)[0]
+        tiny = 1e-12 * theta[0]
+        ok = (r[j] > tiny) & (r[i] > tiny)
+        rho = np.where(ok, np.abs(R) / np.sqrt(np.where(ok, r[i] * r[j], 1.0)), 0.0)
+        order = np.lexsort((j, -rho))
+        c = min(i, m)
+        nn[i, :c] = j[order[:c]]
+        cnt[i] = c
+        if c == m and m > 0:
+            rm[i] = rho[order[m - 1]]
+        if i > m:
+            rm1[i] = rho[order[m]]
+    return nn, cnt, rm, rm1
+
+
+def factor(xy, t, theta, U, m, nn, cnt):
+    """Residual Vecchia factor of R~ = R + sigma^2 I (Sect. 4.3): A_i, D_i."""
+    n = t.shape[0]
+    A = np.zeros((n, m))
+    D = np.zeros(n)
+    for i in range(n):
+        N = nn[i, :cnt[i]].astype(np.int64)
+        Rii = residual_block(xy, t, theta, U, np.array([i]), np.array([i]))[0, 0] + theta[4]
+        if N.size == 0:
+            D[i] = Rii
+            continue
+        RN = residual_block(xy, t, theta, U, N, N) + theta[4] * np.eye(N.size)
+        k = residual_block(xy, t, theta, U, N, np.array([i]))[:, 0]
+        a = np.linalg.solve(RN, k)
+        A[i, :N.size] = a
+        D[i] = Rii - a @ k
+    return A, D
+
+
+def nll(xy, t, theta, U, m, nn, cnt, y, A=None, D=None):
+    """VIF negative log-likelihood by the Woodbury identity (see module doc)."""
+    n, k = t.shape[0], U.shape[1]
+    if A is None:
+        A, D = factor(xy, t, theta, U, m, nn, cnt)
+    By = y.copy()
+    BU = U.copy()
+    for i in range(n):
+        N = nn[i, :cnt[i]].astype(np.int64)
+        if N.size:
+            By[i] -= A[i, :N.size] @ y[N]
+            BU[i] -= A[i, :N.size] @ U[N]
+    s = 1.0 / np.sqrt(D)
+    e = By * s
+    W = BU * s[:, None]
+    M = np.eye(k) + W.T @ W
+    Lm = np.linalg.cholesky(M) if k else np.zeros((0, 0))
+    z = sla.solve_triangular(Lm, W.T @ e, lower=True) if k else np.zeros(0)
+    logdet = np.log(D).sum() + 2.0 * np.log(np.diag(Lm)).sum()
+    quad = e @ e - z @ z
+    return 0.5 * n * np.log(2 * np.pi) + 0.5 * logdet + 0.5 * quad
+
+
+def dense_sigma(xy, t, theta, U, m, nn, cnt, A=None, D=None):
+    """Sigma~_VIF = U U^T + B^{-1} D B^{-T} formed densely (small n)."""
+    n = t.shape[0]
+    if A is None:
+        A, D = factor(xy, t, theta, U, m, nn, cnt)
+    B = np.eye(n)
+    for i in range(n):
+        B[i, nn[i, :cnt[i]]] = -A[i, :cnt[i]]
+    Binv = sla.solve_triangular(B, np.eye(n), lower=True)
+    return U @ U.T + Binv @ np.diag(D) @ Binv.T

@@ -1,0 +1,93 @@
+"""Pins for the VIF oracle (Sect. 4.3, oracle/vif.py) against the exact GP
+likelihood, plain Vecchia, FITC (Sect. 4.2) and the dense Sigma~_VIF."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.vif as vif
+import synthetic_inputs as si
+
+
+def setup(n_st=40, n_days=5, k=12, seed=1, order="time"):
+    st = si.stations_uniform(n_st, seed)
+    xy, t = si.station_days(st, n_days)
+    perm = si.time_stratified_order(t, seed) if order == "time" else si.random_order(t.shape[0], seed)
+    xy, t = np.ascontiguousarray(xy[perm]), np.ascontiguousarray(t[perm])
+    th = oracle.theta_from_ranges(1.0, 0.2, 2.0, 0.5, 0.05)
+    # inducing points: plain kMeans++ on scaled space-time coordinates
+    X = np.concatenate([xy / 0.2, (t / 2.0)[:, None]], axis=1)
+    C = si.kmeanspp(X, k, seed, lloyd_iters=10) if k else np.zeros((0, 3))
+    xyk, tk = np.ascontiguousarray(C[:, :2] * 0.2), np.ascontiguousarray(C[:, 2] * 2.0)
+    y = oracle.dense_sample(xy, t, th, si.standard_normal(t.shape[0], seed + 5))
+    return xy, t, th, xyk, tk, y
+
+
+def dense_nll(S, y):
+    sign, ld = np.linalg.slogdet(S)
+    assert sign > 0
+    return 0.5 * y.shape[0] * np.log(2 * np.pi) + 0.5 * ld + 0.5 * y @ np.linalg.solve(S, y)
+
+
+def test_all_predecessors_is_exact_for_any_k():
+    # m = n-1: the residual's Vecchia factorisation is exact, so
+    # Sigma~_VIF = U U^T + R + sigma^2 I = Sigma + sigma^2 I
+    xy, t, th, xyk, tk, y = setup(n_st=30, n_days=4, k=15)
+    U, r = vif.lowrank(xy, t, xyk, tk, th)
+    m, nn, cnt = oracle.all_predecessors(t.shape[0])
+    v = vif.nll(xy, t, th, U, m, nn, cnt, y)
+    assert abs(v - oracle.dense_nll(xy, t, th, y)) / t.shape[0] < 1e-11
+
+
+def test_k0_reduces_to_plain_vecchia():
+    xy, t, th, xyk, tk, y = setup(k=0)
+    U, r = vif.lowrank(xy, t, None, None, th)
+    nn, cnt, rm, rm1 = vif.knn(xy, t, th, U, r, 8)
+    nn_p, cnt_p, _, _ = oracle.knn(xy, t, th, 8)
+    assert np.array_equal(nn, nn_p) and np.array_equal(cnt, cnt_p)
+    assert vif.nll(xy, t, th, U, 8, nn, cnt, y) == pytest.approx(oracle.nll(xy, t, th, 8, nn, cnt, y), rel=1e-12)
+
+
+def test_m0_reduces_to_fitc():
+    # FITC (Sect. 4.2): Sigma_nk Sigma_kk^{-1} Sigma_kn + diag(Sigma - that) + sigma^2 I
+    xy, t, th, xyk, tk, y = setup(k=10)
+    n = t.shape[0]
+    Skk = oracle.cov_matrix(xyk, tk, xyk, tk, th)
+    Snk = oracle.cov_matrix(xy, t, xyk, tk, th)
+    low = Snk @ np.linalg.solve(Skk, Snk.T)
+    S = low + np.diag(th[0] - np.diag(low)) + th[4] * np.eye(n)
+    U, r = vif.lowrank(xy, t, xyk, tk, th)
+    nn = np.zeros((n, 0), dtype=np.int32)
+    cnt = np.zeros(n, dtype=np.int32)
+    assert abs(vif.nll(xy, t, th, U, 0, nn, cnt, y) - dense_nll(S, y)) / n < 1e-11
+
+
+@pytest.mark.parametrize("order", ["time", "random"])
+def test_woodbury_matches_dense_sigma(order):
+    xy, t, th, xyk, tk, y = setup(k=12, order=order)
+    U, r = vif.lowrank(xy, t, xyk, tk, th)
+    assert np.all(r > 0)
+    nn, cnt, rm, rm1 = vif.knn(xy, t, th, U, r, 6)
+    A, D = vif.factor(xy, t, th, U, 6, nn, cnt)
+    assert np.all(D >= th[4] * (1 - 1e-12))
+    S = vif.dense_sigma(xy, t, th, U, 6, nn, cnt, A, D)
+    v = vif.nll(xy, t, th, U, 6, nn, cnt, y, A, D)
+    assert abs(v - dense_nll(S, y)) / t.shape[0] < 1e-11
+
+
+def test_residual_neighbours_match_python_sort():
+    xy, t, th, xyk, tk, y = setup(n_st=20, n_days=4, k=8, order="random")
+    U, r = vif.lowrank(xy, t, xyk, tk, th)
+    nn, cnt, _, _ = vif.knn(xy, t, th, U, r, 5)
+    n = t.shape[0]
+    C = oracle.cov_matrix(xy, t, xy, t, th)
+    R = C - U @ U.T
+    tiny = 1e-12 * th[0]
+    for i in range(n):
+        rho = [abs(R[i, j]) / np.sqrt(R[i, i] * R[j, j]) if min(r[i], r[j]) > tiny else 0.0 for j in range(i)]
+        ref = sorted(range(i), key=lambda j: (-rho[j], j))[:5]
+        assert list(nn[i, :cnt[i]]) == ref
+    # the residual is a covariance: |rho| <= 1
+    keep = r > tiny
+    d = np.sqrt(np.diag(R)[keep])
+    assert np.all(np.abs(R[np.ix_(keep, keep)] / d[:, None] / d[None, :]) <= 1 + 1e-9)
+    assert np.all(r >= -1e-12)
