@@ -206,50 +206,69 @@ def _points(xy, t):
     return _Points(_ptr(xy, torch.float64, "xy"), _ptr(t, torch.float64, "t"), n)
 
 
-def _ws(ws, n, m):
+def _ws(ws, n, m, k=0):
     if ws is None:
-        ws = Workspace(n, m)
-    if not ws.fits(n, m):
+        ws = Workspace(n, m, k)
+    if not ws.fits(n, m, k):
         raise ValueError("workspace too small")
     return ws
 
 
-def vif_build_neighbors(xy, t, theta, m, nn=None, nn_cnt=None, tie_rows=None, ws=None, stream=None):
-    """Correlation-based neighbour sets (Sect. 4.4.1).  Returns (nn, nn_cnt)."""
+def _inducing(inducing):
+    """(xyk [k,2], tk [k]) CUDA float64 tensors, or None for plain Vecchia."""
+    if inducing is None:
+        return None, 0
+    xyk, tk = inducing
+    k = tk.shape[0]
+    if xyk.shape != (k, 2):
+        raise ValueError("inducing xy must be [k, 2]")
+    return _Inducing(_ptr(xyk, torch.float64, "inducing xy"), _ptr(tk, torch.float64, "inducing t"), k), k
+
+
+def vif_build_neighbors(xy, t, theta, m, nn=None, nn_cnt=None, tie_rows=None, ws=None, stream=None, inducing=None):
+    """Correlation-based neighbour sets (Sect. 4.4.1); with inducing=(xyk, tk),
+    by the VIF residual correlation (Sect. 4.3).  Returns (nn, nn_cnt)."""
     n = t.shape[0]
+    ind, k = _inducing(inducing)
     nn = nn if nn is not None else torch.empty((n, m), dtype=torch.int32, device=t.device)
     nn_cnt = nn_cnt if nn_cnt is not None else torch.empty(n, dtype=torch.int32, device=t.device)
-    ws = _ws(ws, n, m)
+    ws = _ws(ws, n, m, k)
     pts = _points(xy, t)
     cap = 0 if tie_rows is None else tie_rows.numel()
-    _check(lib().vif_build_neighbors(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), None,
+    _check(lib().vif_build_neighbors(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m),
+                                     ctypes.byref(ind) if ind else None,
                                      _ptr(nn, torch.int32, "nn"), _ptr(nn_cnt, torch.int32, "nn_cnt"),
                                      _ptr(tie_rows, torch.int64, "tie_rows"), cap, ws.ptr, ws.nbytes,
                                      _stream(stream)))
     return nn, nn_cnt
 
 
-def vecchia_factor(xy, t, theta, m, nn, nn_cnt, precision=FP64, A=None, D=None, ws=None, stream=None):
-    """Vecchia factor (A, D) of the response covariance (Sect. 4.1)."""
+def vecchia_factor(xy, t, theta, m, nn, nn_cnt, precision=FP64, A=None, D=None, ws=None, stream=None,
+                   inducing=None):
+    """Vecchia factor (A, D) of the response covariance (Sect. 4.1), or of the
+    VIF residual with inducing=(xyk, tk) (Sect. 4.3)."""
     n = t.shape[0]
+    ind, k = _inducing(inducing)
     A = A if A is not None else torch.empty((n, m), dtype=torch.float64, device=t.device)
     D = D if D is not None else torch.empty(n, dtype=torch.float64, device=t.device)
-    ws = _ws(ws, n, m)
+    ws = _ws(ws, n, m, k)
     pts = _points(xy, t)
-    _check(lib().vecchia_factor(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), None,
+    _check(lib().vecchia_factor(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), ctypes.byref(ind) if ind else None,
                                 _ptr(nn, torch.int32, "nn"), _ptr(nn_cnt, torch.int32, "nn_cnt"), int(precision),
                                 _ptr(A, torch.float64, "A"), _ptr(D, torch.float64, "D"), ws.ptr, ws.nbytes,
                                 _stream(stream)))
     return A, D
 
 
-def vecchia_nll(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, out=None, ws=None, stream=None):
-    """Vecchia negative log-likelihood; returns a 1-element CUDA float64 tensor."""
+def vecchia_nll(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, out=None, ws=None, stream=None, inducing=None):
+    """Vecchia (or, with inducing=(xyk, tk), VIF) negative log-likelihood;
+    returns a 1-element CUDA float64 tensor."""
     n = t.shape[0]
+    ind, k = _inducing(inducing)
     out = out if out is not None else torch.empty(1, dtype=torch.float64, device=t.device)
-    ws = _ws(ws, n, m)
+    ws = _ws(ws, n, m, k)
     pts = _points(xy, t)
-    _check(lib().vecchia_nll(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), None,
+    _check(lib().vecchia_nll(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), ctypes.byref(ind) if ind else None,
                              _ptr(nn, torch.int32, "nn"), _ptr(nn_cnt, torch.int32, "nn_cnt"),
                              _ptr(y, torch.float64, "y"), int(precision), _ptr(out, torch.float64, "nll"),
                              ws.ptr, ws.nbytes, _stream(stream)))

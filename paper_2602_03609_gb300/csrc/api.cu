@@ -9,6 +9,7 @@
 
 #include "kernels.h"
 #include "profile.h"
+#include "vif.h"
 #include "workspace.h"
 
 namespace vst {
@@ -128,6 +129,14 @@ DevTheta dev_theta(const vst_theta* th) {
   d.dg_hi = (float)dg;
   d.dg_lo = (float)(dg - (double)d.dg_hi);
   return d;
+}
+
+vst_status check_inducing(const vst_inducing* ind) {
+  if (!ind || ind->k <= 0) return VST_OK;
+  if (ind->k > kVifMaxK) return fail(VST_EINVAL, "k=%lld inducing points exceeds %lld", (long long)ind->k,
+                                     (long long)kVifMaxK);
+  if (!ind->xy || !ind->t) return fail(VST_EINVAL, "inducing xy/t is NULL");
+  return VST_OK;
 }
 
 vst_status check_common(const vst_points* pts, const vst_theta* theta, int m, const int32_t* nn,
@@ -283,11 +292,17 @@ size_t vst_workspace_size(int64_t n, int m, int64_t k) { return ws_layout(n, m, 
 vst_status vecchia_factor(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind,
                           const int32_t* nn, const int32_t* nn_cnt, int precision, double* A, double* D,
                           void* ws, size_t ws_bytes, void* stream) {
-  if (ind && ind->k > 0) return fail(VST_EINVAL, "VIF (inducing points) is not available in this entry point");
-  vst_status s = check_common(pts, theta, m, nn, nn_cnt, ws, ws_bytes, 0);
+  const int64_t k = (ind && ind->k > 0) ? ind->k : 0;
+  vst_status s = check_inducing(ind);
+  if (s == VST_OK) s = check_common(pts, theta, m, nn, nn_cnt, ws, ws_bytes, k);
   if (s != VST_OK) return s;
   if (precision != VST_FP64 && precision != VST_MIXED) return fail(VST_EINVAL, "bad precision %d", precision);
   if (pts->n > 0 && (!D || (m > 0 && !A))) return fail(VST_EINVAL, "A/D is NULL");
+  if (k > 0) {
+    const WsLayout L = ws_layout(pts->n, m, k);
+    launch_init_header(reinterpret_cast<WsHeader*>(static_cast<char*>(ws) + L.hdr), (cudaStream_t)stream);
+    return vif_factor(pts, theta, m, ind, nu_code(theta->nu), nn, nn_cnt, precision, A, D, ws, (cudaStream_t)stream);
+  }
   return run_rows(pts, theta, m, nn, nn_cnt, nullptr, precision, kModeFactor, nullptr, nullptr, A, D, ws,
                   (cudaStream_t)stream);
 }
@@ -295,11 +310,17 @@ vst_status vecchia_factor(const vst_points* pts, const vst_theta* theta, int m, 
 vst_status vecchia_nll(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind,
                        const int32_t* nn, const int32_t* nn_cnt, const double* y, int precision, double* nll,
                        void* ws, size_t ws_bytes, void* stream) {
-  if (ind && ind->k > 0) return fail(VST_EINVAL, "VIF (inducing points) is not available in this entry point");
-  vst_status s = check_common(pts, theta, m, nn, nn_cnt, ws, ws_bytes, 0);
+  const int64_t k = (ind && ind->k > 0) ? ind->k : 0;
+  vst_status s = check_inducing(ind);
+  if (s == VST_OK) s = check_common(pts, theta, m, nn, nn_cnt, ws, ws_bytes, k);
   if (s != VST_OK) return s;
   if (precision != VST_FP64 && precision != VST_MIXED) return fail(VST_EINVAL, "bad precision %d", precision);
   if (!nll || (pts->n > 0 && !y)) return fail(VST_EINVAL, "y/nll is NULL");
+  if (k > 0) {
+    const WsLayout L = ws_layout(pts->n, m, k);
+    launch_init_header(reinterpret_cast<WsHeader*>(static_cast<char*>(ws) + L.hdr), (cudaStream_t)stream);
+    return vif_nll(pts, theta, m, ind, nu_code(theta->nu), nn, nn_cnt, y, precision, nll, ws, (cudaStream_t)stream);
+  }
   return run_rows(pts, theta, m, nn, nn_cnt, y, precision, kModeNll, nll, nullptr, nullptr, nullptr, ws,
                   (cudaStream_t)stream);
 }
@@ -307,7 +328,8 @@ vst_status vecchia_nll(const vst_points* pts, const vst_theta* theta, int m, con
 vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind,
                             const int32_t* nn, const int32_t* nn_cnt, const double* y, int precision, double* nll,
                             double* grad, void* ws, size_t ws_bytes, void* stream) {
-  if (ind && ind->k > 0) return fail(VST_EINVAL, "VIF (inducing points) is not available in this entry point");
+  if (ind && ind->k > 0)
+    return fail(VST_EINVAL, "the VIF gradient is not available in this version (vecchia_nll gives the VIF NLL)");
   vst_status s = check_common(pts, theta, m, nn, nn_cnt, ws, ws_bytes, 0);
   if (s != VST_OK) return s;
   if (precision != VST_FP64 && precision != VST_MIXED) return fail(VST_EINVAL, "bad precision %d", precision);

@@ -24,6 +24,7 @@
 
 #include "kernels.h"
 #include "profile.h"
+#include "vif.h"
 #include "workspace.h"
 
 namespace vst {
@@ -31,7 +32,7 @@ namespace vst {
 vst_status fail(vst_status s, const char* fmt, ...);
 vst_status cuda_fail(cudaError_t e, const char* where);
 vst_status check_theta(const vst_theta* th);
-DevTheta dev_theta(const vst_theta* th);
+vst_status check_inducing(const vst_inducing* ind);
 int nu_code(double nu);
 void launch_lag_table(const DevTheta& th, LagD* d, LagF* f, cudaStream_t st);
 void launch_init_header(WsHeader* h, cudaStream_t st);
@@ -482,7 +483,6 @@ extern "C" vst_status vif_build_neighbors(const vst_points* pts, const vst_theta
                                           const vst_inducing* ind, int32_t* nn, int32_t* nn_cnt,
                                           int64_t* tie_rows, int64_t tie_cap, void* ws, size_t ws_bytes,
                                           void* stream) {
-  if (ind && ind->k > 0) return fail(VST_EINVAL, "VIF residual-correlation neighbours are not available in this version");
   if (!pts) return fail(VST_EINVAL, "pts is NULL");
   const int64_t n = pts->n;
   if (n < 0 || n >= (int64_t(1) << 30)) return fail(VST_EINVAL, "n out of range [0, 2^30)");
@@ -490,7 +490,10 @@ extern "C" vst_status vif_build_neighbors(const vst_points* pts, const vst_theta
   vst_status s = check_theta(theta);
   if (s != VST_OK) return s;
   if (!ws || reinterpret_cast<uintptr_t>(ws) % 256) return fail(VST_EINVAL, "workspace NULL or not 256-byte aligned");
-  if (ws_bytes < vst_workspace_size(n, m, 0)) return fail(VST_ENOMEM, "workspace too small");
+  const int64_t kind = (ind && ind->k > 0) ? ind->k : 0;
+  s = check_inducing(ind);
+  if (s != VST_OK) return s;
+  if (ws_bytes < vst_workspace_size(n, m, kind)) return fail(VST_ENOMEM, "workspace too small");
   if (n > 0 && (!pts->xy || !pts->t || !nn_cnt || (m > 0 && !nn))) return fail(VST_EINVAL, "NULL array");
   if (tie_cap < 0) return fail(VST_EINVAL, "tie_cap < 0");
   cudaStream_t st = (cudaStream_t)stream;
@@ -502,6 +505,11 @@ extern "C" vst_status vif_build_neighbors(const vst_points* pts, const vst_theta
   if (m == 0) {
     cudaError_t e = cudaMemsetAsync(nn_cnt, 0, sizeof(int32_t) * n, st);
     return e == cudaSuccess ? VST_OK : cuda_fail(e, "memset");
+  }
+  if (kind > 0) {
+    const WsLayout LV = ws_layout(n, m, kind);
+    return vif_knn(pts, theta, m, ind, nu_code(theta->nu), nn, nn_cnt, tie_rows, tie_cap, base + LV.vif,
+                   vif_layout(n, m, kind), hdr, st);
   }
   const DevTheta th = dev_theta(theta);
   LagD* lagd = reinterpret_cast<LagD*>(base + L.lagd);

@@ -71,6 +71,10 @@ struct RowArgs {
   double* row_out;            // batched: per-row [6] (nll term, grad[5])
   int row_chunk;              // consecutive rows per warp assignment (>= 1)
   int blocks_per_sm;          // launch shape: resident blocks per SM (0 = as many as fit)
+  // VIF: per-row Gram U_p . U_q of the local block (packed pair order),
+  // subtracted from the covariance; at most one of the two is set
+  const double* gram_d;
+  const float* gram_f;
 };
 
 // Per-position record of the local block: offsets from row i, integer day
@@ -237,6 +241,8 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
 
   // ---- 2. local covariance, lower triangle distributed over the lanes
   const T diag = MIXED ? (T)th.dg_hi : (T)(th.sigma1sq + th.nugget);
+  const bool vif = g.gram_d != nullptr || g.gram_f != nullptr;
+  (void)vif;
   const auto* lags = lag_smem ? bs->lag : nullptr;
 #pragma unroll 2
   for (int e = lane; e < NPAIR; e += 32) {
@@ -268,6 +274,10 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
         ev = exp(-xv);
         v = P * matern_M<NU, T>(xv, ev);
       }
+    }
+    if (pr.valid && pc.valid) {
+      if (g.gram_d) v -= (T)g.gram_d[gi * NPAIR + e];
+      else if (g.gram_f) v -= (T)g.gram_f[gi * NPAIR + e];
     }
     s.K[r][c] = v;
     s.K[c][r] = v;
@@ -412,7 +422,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
         for (int u = 0; u < 4; ++u)
           if (q + u < LAST) df_fma_acc(res, -kv[u], df{av[u], 0.0f});
       }
-      if (valid) res.lo = fmaf(-th.dg_lo, aj, res.lo);
+      if (valid && !vif) res.lo = fmaf(-th.dg_lo, aj, res.lo);
     }
     const float rf = res.hi + res.lo;
     float accr = (lane < LAST) ? rf : 0.0f, dz = 0.0f;
@@ -431,7 +441,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     }
     a_ref = (lane < LAST) ? df{aj, da} : df{0.0f, 0.0f};
     // D = K_ii - k . a   and   r = y_i - y_N . a   in double-float
-    df Ds = (lane == LAST) ? df{th.dg_hi, th.dg_lo} : df{0.0f, 0.0f};
+    df Ds = (lane == LAST) ? (vif ? df{s.K[LAST][LAST], 0.0f} : df{th.dg_hi, th.dg_lo}) : df{0.0f, 0.0f};
     const df yl = df_split(rj);
     df rs = (lane == LAST) ? yl : df{0.0f, 0.0f};
     if (lane < LAST) {

@@ -1,0 +1,761 @@
+// VIF: the Vecchia-inducing-point full-scale approximation (Sect. 4.3).
+//
+//   Sigma~_VIF = U U^T + B^{-1} D B^{-T},  U = Sigma_nk L_kk^{-T},  L_kk L_kk^T = Sigma_kk,
+//
+// with (B, D) the Vecchia factor of the residual R + sigma^2 I,
+// R = Sigma - U U^T, and neighbours chosen by the residual correlation
+// |R_ij| / sqrt(R_ii R_jj).  The NLL uses the Sherman-Woodbury-Morrison
+// identity (the complexity remark closing Sect. 4.3):
+//   W = D^{-1/2} B U,  e = D^{-1/2} B y,  M = I + W^T W,
+//   log det = sum_i log D_i + log det M,
+//   quad    = e^T e - (W^T e)^T M^{-1} (W^T e).
+//
+// Kernels (T = double for the FP64 form, float for the mixed form):
+//   kk_kernel            Sigma_kk in FP64
+//   chol_panel/syrk_trail blocked FP64 Cholesky (in place, lower)
+//   trinv_kernel         L^{-1}, FP64, one warp per column
+//   ugemm_kernel<T>      U = Sigma_nk L^{-T} (tiled; Sigma_nk evaluated on the fly)
+//   rdiag_kernel<T>      r_i = sigma1^2 - ||U_i||^2
+//   vif_knn_kernel       residual-correlation kNN, FP64 brute force
+//   gram_kernel<T>       per-row U_p . U_q over the local block (fed to the row kernel)
+//   wvec_kernel<T>       rows of [W e] and sum log D_i
+//   syrk_kernel<T>       partial [W e]^T [W e] over row chunks, then a fixed-order sum
+//   final_kernel         M = I + G, FP64 Cholesky, z = L_M^{-1} W^T e, the NLL
+#include <algorithm>
+#include <cfloat>
+#include <climits>
+#include <cmath>
+
+#include "kernels.h"
+#include "profile.h"
+#include "vif.h"
+#include "workspace.h"
+
+namespace vst {
+
+vst_status fail(vst_status s, const char* fmt, ...);
+vst_status cuda_fail(cudaError_t e, const char* where);
+void launch_init_header(WsHeader* h, cudaStream_t st);
+void launch_lag_table(const DevTheta& th, LagD* d, LagF* f, cudaStream_t st);
+void apply_launch_shape(RowArgs& g, int batched, int precision, int nu, int pm);
+
+// ---------------------------------------------------------------------------
+// covariance of Eq. (2) for one pair, FP64 (any lag)
+template <int NU>
+__device__ __forceinline__ double cov64(const DevTheta& th, double dx, double dy, double u) {
+  const LagD f = lag_factors(th, u);
+  const double x = f.G * sqrt(dx * dx + dy * dy);
+  return f.P * matern_M<NU, double>(x, exp(-x));
+}
+
+// the same in FP32 for the mixed form (psi powers through log2/exp2)
+template <int NU>
+__device__ __forceinline__ float cov32(const DevTheta& th, float dx, float dy, float u) {
+  const float au = fabsf(u);
+  const float l2 = au > 0.f ? __log2f(au) : -126.f;
+  const float psi = au > 0.f ? fmaf((float)th.a, exp2f(2.0f * (float)th.alpha * l2), 1.0f) : 1.0f;
+  const float lp = __log2f(psi);
+  const float P = (float)th.sigma1sq * exp2f(-(float)th.p * lp);
+  const float G = (float)th.c * exp2f(-0.5f * (float)th.gamma * lp);
+  const float d2 = dx * dx + dy * dy;
+  const float x = G * (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f);
+  return P * matern_M<NU, float>(x, __expf(-x));
+}
+
+template <int NU>
+__global__ void kk_kernel(const double* xyk, const double* tk, int k, DevTheta th, double* S) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (id >= (int64_t)k * k) return;
+  const int r = (int)(id / k), c = (int)(id % k);
+  S[id] = cov64<NU>(th, xyk[2 * r] - xyk[2 * c], xyk[2 * r + 1] - xyk[2 * c + 1], tk[r] - tk[c]);
+}
+
+// ---------------------------------------------------------------------------
+// blocked Cholesky, FP64, lower, in place (A row-major k x k)
+constexpr int kPanel = 32;
+
+__global__ void chol_panel_kernel(double* A, int k, int j0, int jb, WsHeader* hdr, int err_code) {
+  __shared__ double inv;
+  for (int c = j0; c < j0 + jb; ++c) {
+    if (threadIdx.x == 0) {
+      double d = A[(int64_t)c * k + c];
+      if (!(d > 0.0)) {
+        report_error(hdr, err_code, c);
+        d = 1.0;
+      }
+      d = sqrt(d);
+      A[(int64_t)c * k + c] = d;
+      inv = 1.0 / d;
+    }
+    __syncthreads();
+    for (int r = c + 1 + threadIdx.x; r < k; r += blockDim.x) A[(int64_t)r * k + c] *= inv;
+    __syncthreads();
+    const int w = j0 + jb - (c + 1);  // remaining panel columns
+    if (w > 0) {
+      const int64_t cnt = (int64_t)(k - c - 1) * w;
+      for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
+        const int r = c + 1 + (int)(q / w), c2 = c + 1 + (int)(q % w);
+        if (c2 <= r) A[(int64_t)r * k + c2] -= A[(int64_t)r * k + c] * A[(int64_t)c2 * k + c];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// trailing update A[r][c] -= sum_{p in panel} A[r][p] A[c][p], j0+jb <= c <= r < k
+__global__ void chol_trail_kernel(double* A, int k, int j0, int jb) {
+  __shared__ double Ar[32][kPanel + 1], Ac[32][kPanel + 1];
+  const int t0 = j0 + jb;
+  const int br = blockIdx.y, bc = blockIdx.x;
+  if (bc > br) return;
+  const int r0 = t0 + br * 32, c0 = t0 + bc * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int q = threadIdx.x; q < 32 * jb; q += blockDim.x) {
+    const int rr = q / jb, pp = q % jb;
+    Ar[rr][pp] = (r0 + rr < k) ? A[(int64_t)(r0 + rr) * k + j0 + pp] : 0.0;
+    Ac[rr][pp] = (c0 + rr < k) ? A[(int64_t)(c0 + rr) * k + j0 + pp] : 0.0;
+  }
+  __syncthreads();
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int r = r0 + rr, c = c0 + tx;
+    if (r >= k || c >= k || c > r) continue;
+    double s = 0.0;
+    for (int p = 0; p < jb; ++p) s += Ar[rr][p] * Ac[tx][p];
+    A[(int64_t)r * k + c] -= s;
+  }
+}
+
+vst_status chol64(double* A, int k, WsHeader* hdr, int err_code, cudaStream_t st) {
+  for (int j0 = 0; j0 < k; j0 += kPanel) {
+    const int jb = std::min(kPanel, k - j0);
+    chol_panel_kernel<<<1, 256, 0, st>>>(A, k, j0, jb, hdr, err_code);
+    const int rest = k - (j0 + jb);
+    if (rest > 0) {
+      const int nb = (rest + 31) / 32;
+      chol_trail_kernel<<<dim3(nb, nb), 256, 0, st>>>(A, k, j0, jb);
+    }
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VST_OK : cuda_fail(e, "cholesky");
+}
+
+// X = L^{-1} (lower); one warp per column j: forward substitution of L x = e_j
+__global__ void trinv_kernel(const double* L, int k, double* X) {
+  extern __shared__ double xs_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  double* x = xs_raw + (int64_t)wib * k;
+  for (int j = blockIdx.x * wpb + wib; j < k; j += gridDim.x * wpb) {
+    for (int r = lane; r < k; r += 32) x[r] = 0.0;
+    __syncwarp();
+    if (lane == 0) x[j] = 1.0 / L[(int64_t)j * k + j];
+    __syncwarp();
+    for (int r = j + 1; r < k; ++r) {
+      double s = 0.0;
+      for (int p = j + lane; p < r; p += 32) s += L[(int64_t)r * k + p] * x[p];
+      s = warp_sum(s);
+      if (lane == 0) x[r] = -s / L[(int64_t)r * k + r];
+      __syncwarp();
+    }
+    for (int r = lane; r < k; r += 32) X[(int64_t)r * k + j] = x[r];
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// U[i][c] = sum_{p <= c} S[i][p] X[c][p], S[i][p] = C(x_i, z_p), X = L^{-1}.
+// 64 x 64 output tile per block of 256 threads, 4 x 4 per thread, K step 16.
+template <typename T, int NU>
+__global__ void __launch_bounds__(256) ugemm_kernel(const double* xy, const double* t, int64_t n,
+                                                    const double* xyk, const double* tk, int k, DevTheta th,
+                                                    const double* X, T* U) {
+  constexpr int BM = 64, BN = 64, BK = 16;
+  __shared__ T As[BK][BM + 4];
+  __shared__ T Bs[BK][BN + 4];
+  __shared__ double rx[BM], ry[BM], rt[BM];
+  __shared__ double zx[BK], zy[BK], zt[BK];
+  const int64_t i0 = (int64_t)blockIdx.y * BM;
+  const int c0 = blockIdx.x * BN;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  if (tid < BM) {
+    const int64_t i = i0 + tid;
+    rx[tid] = i < n ? xy[2 * i] : 0.0;
+    ry[tid] = i < n ? xy[2 * i + 1] : 0.0;
+    rt[tid] = i < n ? t[i] : 0.0;
+  }
+  T acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+  const int pend = k < c0 + BN ? k : c0 + BN;  // X[c][p] = 0 for p > c
+  for (int p0 = 0; p0 < pend; p0 += BK) {
+    __syncthreads();
+    if (tid < BK) {
+      const int p = p0 + tid;
+      zx[tid] = p < k ? xyk[2 * p] : 0.0;
+      zy[tid] = p < k ? xyk[2 * p + 1] : 0.0;
+      zt[tid] = p < k ? tk[p] : 0.0;
+    }
+    __syncthreads();
+    // S tile: 64 rows x 16 inducing points, 4 per thread
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * 256;
+      const int ii = e & (BM - 1), kk = e >> 6;
+      T v = T(0);
+      if (i0 + ii < n && p0 + kk < k) {
+        if constexpr (std::is_same<T, double>::value) {
+          v = cov64<NU>(th, rx[ii] - zx[kk], ry[ii] - zy[kk], rt[ii] - zt[kk]);
+        } else {
+          v = cov32<NU>(th, (float)(rx[ii] - zx[kk]), (float)(ry[ii] - zy[kk]), (float)(rt[ii] - zt[kk]));
+        }
+      }
+      As[kk][ii] = v;
+    }
+    // X tile: Bs[kk][cc] = X[c0 + cc][p0 + kk]
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * 256;
+      const int kk = e & (BK - 1), cc = e >> 4;
+      const int c = c0 + cc, p = p0 + kk;
+      Bs[kk][cc] = (c < k && p < k && p <= c) ? (T)X[(int64_t)c * k + p] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[kk][ty * 4 + u];
+        b[u] = Bs[kk][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t i = i0 + ty * 4 + u;
+    if (i >= n) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int c = c0 + tx * 4 + v;
+      if (c < k) U[i * k + c] = acc[u][v];
+    }
+  }
+}
+
+template <typename T>
+__global__ void rdiag_kernel(const T* U, int64_t n, int k, double s1, double* r) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = warp; i < n; i += nw) {
+    double s = 0.0;
+    for (int c = lane; c < k; c += 32) {
+      const double u = (double)U[i * k + c];
+      s += u * u;
+    }
+    s = warp_sum(s);
+    if (lane == 0) r[i] = s1 - s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// residual-correlation kNN, FP64 brute force over all predecessors
+struct VifKnnArgs {
+  const double* xy;
+  const double* t;
+  int64_t n;
+  int m;
+  int k;
+  DevTheta th;
+  const double* U;  // FP64 [n][k]
+  const double* r;  // [n]
+  int32_t* nn;
+  int32_t* nn_cnt;
+  int64_t* tie_rows;
+  int64_t tie_cap;
+  WsHeader* hdr;
+};
+
+template <int NU, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32) vif_knn_kernel(VifKnnArgs A) {
+  extern __shared__ double ui_raw[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double* ui = ui_raw + (int64_t)wib * A.k;
+  const int64_t warp = (int64_t)blockIdx.x * WARPS + wib;
+  const int64_t total = (int64_t)gridDim.x * WARPS;
+  const int K = A.m + 1;
+  const double NEG = -1.0e300;
+  const double tiny = 1e-12 * A.th.sigma1sq;
+  for (int64_t i = warp; i < A.n; i += total) {
+    for (int c = lane; c < A.k; c += 32) ui[c] = A.U[i * A.k + c];
+    __syncwarp();
+    const double xi = A.xy[2 * i], yi = A.xy[2 * i + 1], ti = A.t[i], ri = A.r[i];
+    double lr = NEG;
+    int lid = INT_MAX, count = 0;
+    double thr = NEG;
+    for (int64_t j0 = 0; j0 < i; j0 += 32) {
+      const int64_t j = j0 + lane;
+      double rho = NEG;
+      if (j < i) {
+        const double* uj = A.U + j * A.k;
+        double dot = 0.0;
+        for (int c = 0; c < A.k; ++c) dot = fma(ui[c], uj[c], dot);
+        const double R = cov64<NU>(A.th, xi - A.xy[2 * j], yi - A.xy[2 * j + 1], ti - A.t[j]) - dot;
+        const double rj = A.r[j];
+        rho = (ri > tiny && rj > tiny) ? fabs(R) / sqrt(ri * rj) : 0.0;
+      }
+      unsigned mm = __ballot_sync(kFull, j < i && (count < K || rho >= thr));
+      while (mm) {
+        const int src = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const double cr = __shfl_sync(kFull, rho, src);
+        const int cj = (int)(j0 + src);
+        if (count >= K && cr < thr) continue;
+        const bool better = lane < count && (lr > cr || (lr == cr && lid < cj));
+        const int p = __popc(__ballot_sync(kFull, better));
+        if (p >= K) continue;
+        const double ur = __shfl_up_sync(kFull, lr, 1);
+        const int uid = __shfl_up_sync(kFull, lid, 1);
+        if (lane > p) { lr = ur; lid = uid; }
+        if (lane == p) { lr = cr; lid = cj; }
+        count = min(count + 1, K);
+        if (count >= K) thr = __shfl_sync(kFull, lr, K - 1);
+      }
+    }
+    const int cnt = min(count, A.m);
+    if (lane < A.m) A.nn[i * A.m + lane] = lane < cnt ? lid : -1;
+    if (lane == 0) A.nn_cnt[i] = cnt;
+    if (count == K && A.m > 0) {
+      const double rm = __shfl_sync(kFull, lr, A.m - 1);
+      const double rm1 = __shfl_sync(kFull, lr, A.m);
+      if (lane == 0 && (rm - rm1) <= 1e-12 * fabs(rm)) {
+        const unsigned long long slot = atomicAdd(&A.hdr->n_tie, 1ull);
+        if (A.tie_rows && (int64_t)slot < A.tie_cap) A.tie_rows[slot] = i;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// per-row Gram of the local block: gram[i][e] = U_{pos r} . U_{pos c}, pairs e
+// in the packed order of the row kernel (positions 0..cnt-1 neighbours,
+// PM-1 = row i, the rest unused)
+template <typename T, int PM>
+__global__ void __launch_bounds__(128) gram_kernel(const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k,
+                                                   const T* U, T* gram) {
+  constexpr int NPAIR = PM * (PM + 1) / 2;
+  constexpr int NPL = (NPAIR + 31) / 32;  // pairs per lane
+  __shared__ T Us[4][PM][33];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t warp = (int64_t)blockIdx.x * 4 + wib;
+  const int64_t total = (int64_t)gridDim.x * 4;
+  int pr[NPL], pc[NPL];
+#pragma unroll
+  for (int q = 0; q < NPL; ++q) {
+    const int e = lane + 32 * q;
+    int r = 0, c = 0;
+    if (e < NPAIR) pair_of<PM>(e, r, c);
+    pr[q] = r;
+    pc[q] = c;
+  }
+  for (int64_t i = warp; i < n; i += total) {
+    const int cnt = min(max(nn_cnt[i], 0), min(m, PM - 1));
+    int idx[PM];
+#pragma unroll
+    for (int p = 0; p < PM; ++p) {
+      int v = -1;
+      if (p < cnt) v = nn[i * m + p];
+      if (p == PM - 1) v = (int)i;
+      idx[p] = (v >= 0 && v <= i) ? v : -1;
+    }
+    T acc[NPL];
+#pragma unroll
+    for (int q = 0; q < NPL; ++q) acc[q] = T(0);
+    for (int c0 = 0; c0 < k; c0 += 32) {
+      const int c = c0 + lane;
+#pragma unroll
+      for (int p = 0; p < PM; ++p) Us[wib][p][lane] = (idx[p] >= 0 && c < k) ? U[(int64_t)idx[p] * k + c] : T(0);
+      __syncwarp();
+#pragma unroll
+      for (int q = 0; q < NPL; ++q) {
+        T s = T(0);
+        const T* a = Us[wib][pr[q]];
+        const T* b = Us[wib][pc[q]];
+#pragma unroll 8
+        for (int u = 0; u < 32; ++u) s = fma(a[u], b[u], s);
+        acc[q] += s;
+      }
+      __syncwarp();
+    }
+#pragma unroll
+    for (int q = 0; q < NPL; ++q) {
+      const int e = lane + 32 * q;
+      if (e < NPAIR) gram[i * NPAIR + e] = acc[q];
+    }
+  }
+}
+
+// rows of [W e]: W_i = (U_i - sum_q A_iq U_{nn(i,q)}) / sqrt(D_i), e_i likewise
+// with y; writes WE[i][0..k) = W_i and WE[i][k] = e_i; per-warp partial sums
+// of log D_i into part[warp]
+template <typename T>
+__global__ void wvec_kernel(const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, const T* U,
+                            const double* y, const double* A, const double* D, T* WE, double* part) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  double slog = 0.0;
+  for (int64_t i = warp; i < n; i += nw) {
+    const int cnt = min(max(nn_cnt[i], 0), m);
+    const double Di = D[i];
+    const double s = 1.0 / sqrt(Di);
+    int myj = -1;
+    double mya = 0.0;
+    if (lane < cnt) {
+      myj = nn[i * m + lane];
+      mya = A[i * m + lane];
+      if (myj < 0 || myj >= i) { myj = -1; mya = 0.0; }
+    }
+    double ey = (lane < cnt && myj >= 0) ? mya * y[myj] : 0.0;
+    ey = warp_sum(ey);
+    for (int c0 = 0; c0 < k + 1; c0 += 32) {
+      const int c = c0 + lane;
+      double v = 0.0;
+      if (c < k) v = (double)U[i * k + c];
+      for (int q = 0; q < cnt; ++q) {
+        const int j = __shfl_sync(kFull, myj, q);
+        const double aq = __shfl_sync(kFull, mya, q);
+        if (c < k && j >= 0) v -= aq * (double)U[(int64_t)j * k + c];
+      }
+      if (c == k) v = y[i] - ey;
+      if (c <= k) WE[i * (k + 1) + c] = (T)(v * s);
+    }
+    if (lane == 0) slog += log(Di);
+  }
+  slog = warp_sum(slog);
+  if (lane == 0) part[warp] = slog;
+}
+
+// partial G = WE^T WE over a row chunk: output tile 32 x 32 of the (k+1)^2
+// lower triangle, blockIdx.z = row chunk; fixed-order sum in syrk_sum_kernel
+template <typename T>
+__global__ void __launch_bounds__(256) syrk_kernel(const T* WE, int64_t n, int kk, int64_t chunk, double* part) {
+  __shared__ T Ar[32][33], Ac[32][33];
+  const int br = blockIdx.y, bc = blockIdx.x;
+  if (bc > br) return;
+  const int r0 = br * 32, c0 = bc * 32;
+  const int64_t n0 = (int64_t)blockIdx.z * chunk, n1 = n < n0 + chunk ? n : n0 + chunk;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+  T acc[4] = {T(0), T(0), T(0), T(0)};
+  for (int64_t b = n0; b < n1; b += 32) {
+    for (int q = threadIdx.x; q < 32 * 32; q += 256) {
+      const int rr = q >> 5, cc = q & 31;  // rr: row of WE (sample), cc: column
+      const int64_t s = b + rr;
+      Ar[rr][cc] = (s < n1 && r0 + cc < kk) ? WE[s * kk + r0 + cc] : T(0);
+      Ac[rr][cc] = (s < n1 && c0 + cc < kk) ? WE[s * kk + c0 + cc] : T(0);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int rr = ty + 8 * u;
+      T s = T(0);
+#pragma unroll 8
+      for (int q = 0; q < 32; ++q) s = fma(Ar[q][rr], Ac[q][tx], s);
+      acc[u] += s;
+    }
+    __syncthreads();
+  }
+  const int64_t kk2 = (int64_t)kk * kk;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int r = r0 + ty + 8 * u, c = c0 + tx;
+    if (r < kk && c < kk && c <= r) part[(int64_t)blockIdx.z * kk2 + (int64_t)r * kk + c] = (double)acc[u];
+  }
+}
+
+__global__ void syrk_sum_kernel(const double* part, int nchunk, int kk, double* G) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t kk2 = (int64_t)kk * kk;
+  if (id >= kk2) return;
+  const int r = (int)(id / kk), c = (int)(id % kk);
+  if (c > r) return;
+  double s = 0.0;
+  for (int q = 0; q < nchunk; ++q) s += part[q * kk2 + id];
+  G[id] = s;
+  G[(int64_t)c * kk + r] = s;
+}
+
+// M = I + G[0..k) (in place into Mout, k x k), v = G[0..k][k], ete = G[k][k]
+__global__ void make_m_kernel(const double* G, int k, double* M, double* v, double* ete) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int kk = k + 1;
+  if (id < (int64_t)k * k) {
+    const int r = (int)(id / k), c = (int)(id % k);
+    M[id] = G[(int64_t)r * kk + c] + (r == c ? 1.0 : 0.0);
+  }
+  if (id < k) v[id] = G[(int64_t)id * kk + k];
+  if (id == 0) *ete = G[(int64_t)k * kk + k];
+}
+
+// z = L_M^{-1} v (one block), then the NLL
+__global__ void final_kernel(const double* Lm, int k, const double* v, const double* ete, const double* logd_part,
+                             int64_t nparts, int64_t n, double* z, double* nll) {
+  __shared__ double sh[256];
+  // sum log D_i (fixed order) and log det M
+  double s = 0.0;
+  for (int64_t q = threadIdx.x; q < nparts; q += 256) s += logd_part[q];
+  double ld = 0.0;
+  for (int r = threadIdx.x; r < k; r += 256) ld += 2.0 * log(Lm[(int64_t)r * k + r]);
+  sh[threadIdx.x] = s + ld;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  const double logdet = sh[0];
+  __syncthreads();
+  // forward substitution, row by row, block-parallel dot products
+  for (int r = 0; r < k; ++r) {
+    double d = 0.0;
+    for (int p = threadIdx.x; p < r; p += 256) d += Lm[(int64_t)r * k + p] * z[p];
+    sh[threadIdx.x] = d;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+      if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) z[r] = (v[r] - sh[0]) / Lm[(int64_t)r * k + r];
+    __syncthreads();
+  }
+  double zz = 0.0;
+  for (int r = threadIdx.x; r < k; r += 256) zz += z[r] * z[r];
+  sh[threadIdx.x] = zz;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *nll = 0.5 * (double)n * log(2.0 * M_PI) + 0.5 * logdet + 0.5 * (*ete - sh[0]);
+}
+
+// ---------------------------------------------------------------------------
+// host side
+
+template <typename T>
+static vst_status lowrank_T(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu,
+                            char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
+  const int64_t n = pts->n;
+  const int k = (int)ind->k;
+  const DevTheta th = dev_theta_vif(theta);
+  double* S = reinterpret_cast<double*>(vbase + V.S);
+  double* X = reinterpret_cast<double*>(vbase + V.X);
+  T* U = reinterpret_cast<T*>(vbase + V.U);
+  double* r = reinterpret_cast<double*>(vbase + V.r);
+  const int64_t kk = (int64_t)k * k;
+  const int gb = (int)((kk + 255) / 256);
+  if (nu == 0) kk_kernel<0><<<gb, 256, 0, st>>>(ind->xy, ind->t, k, th, S);
+  else if (nu == 1) kk_kernel<1><<<gb, 256, 0, st>>>(ind->xy, ind->t, k, th, S);
+  else kk_kernel<2><<<gb, 256, 0, st>>>(ind->xy, ind->t, k, th, S);
+  vst_status s = chol64(S, k, hdr, VST_ENOTSPD, st);
+  if (s != VST_OK) return s;
+  const int wpb = 4;
+  const size_t smem = sizeof(double) * k * wpb;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(trinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  trinv_kernel<<<(k + wpb - 1) / wpb, 32 * wpb, smem, st>>>(S, k, X);
+  if (n > 0) {
+    const dim3 grid((k + 63) / 64, (unsigned)((n + 63) / 64));
+    if (nu == 0) ugemm_kernel<T, 0><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U);
+    else if (nu == 1) ugemm_kernel<T, 1><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U);
+    else ugemm_kernel<T, 2><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U);
+    rdiag_kernel<T><<<(int)std::min<int64_t>((n + 7) / 8, 65535), 256, 0, st>>>(U, n, k, theta->sigma1sq, r);
+  }
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VST_OK : cuda_fail(e, "VIF low-rank kernels");
+}
+
+vst_status vif_lowrank(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu, bool fp64,
+                       char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
+  return fp64 ? lowrank_T<double>(pts, theta, ind, nu, vbase, V, hdr, st)
+              : lowrank_T<float>(pts, theta, ind, nu, vbase, V, hdr, st);
+}
+
+vst_status vif_knn(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
+                   int32_t* nn, int32_t* nn_cnt, int64_t* tie_rows, int64_t tie_cap, char* vbase,
+                   const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
+  vst_status s = vif_lowrank(pts, theta, ind, nu, true, vbase, V, hdr, st);
+  if (s != VST_OK) return s;
+  VifKnnArgs A{};
+  A.xy = pts->xy;
+  A.t = pts->t;
+  A.n = pts->n;
+  A.m = m;
+  A.k = (int)ind->k;
+  A.th = dev_theta_vif(theta);
+  A.U = reinterpret_cast<const double*>(vbase + V.U);
+  A.r = reinterpret_cast<const double*>(vbase + V.r);
+  A.nn = nn;
+  A.nn_cnt = nn_cnt;
+  A.tie_rows = tie_rows;
+  A.tie_cap = tie_rows ? tie_cap : 0;
+  A.hdr = hdr;
+  constexpr int W = 4;
+  const size_t smem = sizeof(double) * A.k * W;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  auto launch = [&](auto kern) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, W * 32, smem);
+    ProfileScope ps(kProfKnn, st);
+    kern<<<std::max(1, per) * sms, W * 32, smem, st>>>(A);
+  };
+  if (nu == 0) launch(vif_knn_kernel<0, W>);
+  else if (nu == 1) launch(vif_knn_kernel<1, W>);
+  else launch(vif_knn_kernel<2, W>);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VST_OK : cuda_fail(e, "VIF knn kernel");
+}
+
+template <typename T>
+static void launch_gram(int pm, const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, const T* U, T* gram,
+                        cudaStream_t st) {
+  const int blocks = (int)std::min<int64_t>((n + 3) / 4, 152 * 16);
+  if (pm <= 8) gram_kernel<T, 8><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
+  else if (pm <= 16) gram_kernel<T, 16><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
+  else gram_kernel<T, 32><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
+}
+
+// factor of the residual (A, D) with the fused row kernel fed the Gram
+template <typename T>
+static vst_status vif_factor_T(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
+                               const int32_t* nn, const int32_t* nn_cnt, int precision, double* Aout, double* Dout,
+                               char* base, const WsLayout& L, char* vbase, const VifLayout& V, cudaStream_t st) {
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
+  vst_status s = vif_lowrank(pts, theta, ind, nu, std::is_same<T, double>::value, vbase, V, hdr, st);
+  if (s != VST_OK) return s;
+  const int64_t n = pts->n;
+  const int k = (int)ind->k;
+  T* U = reinterpret_cast<T*>(vbase + V.U);
+  T* gram = reinterpret_cast<T*>(vbase + V.gram);
+  if (n > 0) launch_gram<T>(m + 1, nn, nn_cnt, n, m, k, U, gram, st);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "gram kernel");
+  LagD* lagd = reinterpret_cast<LagD*>(base + L.lagd);
+  LagF* lagf = reinterpret_cast<LagF*>(base + L.lagf);
+  uint8_t* flag = reinterpret_cast<uint8_t*>(base + L.flag);
+  const DevTheta th = dev_theta_vif(theta);
+  launch_lag_table(th, lagd, lagf, st);
+  const bool mixed = precision == VST_MIXED;
+  if (mixed && n > 0) {
+    e = cudaMemsetAsync(flag, 0, (size_t)n, st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+  }
+  RowArgs g{};
+  g.xy = pts->xy;
+  g.t = pts->t;
+  g.nn = nn;
+  g.nn_cnt = nn_cnt;
+  g.n = n;
+  g.m = m;
+  g.th = th;
+  g.lagd = lagd;
+  g.lagf = lagf;
+  g.A = Aout;
+  g.D = Dout;
+  g.flag = flag;
+  g.hdr = hdr;
+  g.tau = 1.0e4f;
+  g.partial = reinterpret_cast<double*>(base + L.partial);
+  if constexpr (std::is_same<T, double>::value) g.gram_d = gram;
+  else g.gram_f = gram;
+  apply_launch_shape(g, 0, precision, nu, m + 1);
+  int64_t w = 0;
+  if (n > 0) {
+    {
+      ProfileScope ps(kProfRows, st);
+      e = launch_rows(mixed, nu, m + 1, kModeFactor, g, st, &w);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "VIF row kernel");
+    if (mixed) {
+      // FP64 redo of flagged rows: needs the FP64 Gram of those rows
+      g.fallback_only = 1;
+      e = launch_rows(false, nu, m + 1, kModeFactor, g, st, &w);
+      if (e != cudaSuccess) return cuda_fail(e, "VIF fallback kernel");
+    }
+  }
+  return VST_OK;
+}
+
+vst_status vif_factor(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
+                      const int32_t* nn, const int32_t* nn_cnt, int precision, double* A, double* D, void* ws,
+                      cudaStream_t st) {
+  char* base = static_cast<char*>(ws);
+  const WsLayout L = ws_layout(pts->n, m, ind->k);
+  char* vbase = base + L.vif;
+  const VifLayout V = vif_layout(pts->n, m, ind->k);
+  return precision == VST_FP64 ? vif_factor_T<double>(pts, theta, m, ind, nu, nn, nn_cnt, precision, A, D, base, L,
+                                                      vbase, V, st)
+                               : vif_factor_T<float>(pts, theta, m, ind, nu, nn, nn_cnt, precision, A, D, base, L,
+                                                     vbase, V, st);
+}
+
+template <typename T>
+static vst_status vif_nll_T(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
+                            const int32_t* nn, const int32_t* nn_cnt, const double* y, int precision, double* nll,
+                            void* ws, cudaStream_t st) {
+  char* base = static_cast<char*>(ws);
+  const int64_t n = pts->n;
+  const int k = (int)ind->k;
+  const WsLayout L = ws_layout(n, m, k);
+  char* vbase = base + L.vif;
+  const VifLayout V = vif_layout(n, m, k);
+  double* A = reinterpret_cast<double*>(base + L.sA);
+  double* D = reinterpret_cast<double*>(base + L.sD);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
+  vst_status s = vif_factor_T<T>(pts, theta, m, ind, nu, nn, nn_cnt, precision, A, D, base, L, vbase, V, st);
+  if (s != VST_OK) return s;
+  T* U = reinterpret_cast<T*>(vbase + V.U);
+  T* WE = reinterpret_cast<T*>(vbase + V.WE);
+  double* logd = reinterpret_cast<double*>(vbase + V.logd);
+  double* part = reinterpret_cast<double*>(vbase + V.syrk);
+  double* G = reinterpret_cast<double*>(vbase + V.G);
+  double* M = reinterpret_cast<double*>(vbase + V.M);
+  double* v = reinterpret_cast<double*>(vbase + V.v);
+  double* z = reinterpret_cast<double*>(vbase + V.z);
+  const int wblocks = (int)std::min<int64_t>((n + 7) / 8, kVifMaxWarps / 8);
+  int64_t nparts = 0;
+  if (n > 0) {
+    wvec_kernel<T><<<wblocks, 256, 0, st>>>(nn, nn_cnt, n, m, k, U, y, A, D, WE, logd);
+    nparts = (int64_t)wblocks * 8;
+  }
+  const int kk = k + 1;
+  const int64_t chunk = std::max<int64_t>((n + kVifSyrkChunks - 1) / kVifSyrkChunks, 1);
+  const int nchunk = (int)std::min<int64_t>(kVifSyrkChunks, (n + chunk - 1) / chunk);
+  const int nb = (kk + 31) / 32;
+  if (n > 0) syrk_kernel<T><<<dim3(nb, nb, nchunk), 256, 0, st>>>(WE, n, kk, chunk, part);
+  const int64_t kk2 = (int64_t)kk * kk;
+  if (nchunk > 0) syrk_sum_kernel<<<(int)((kk2 + 255) / 256), 256, 0, st>>>(part, nchunk, kk, G);
+  else cudaMemsetAsync(G, 0, sizeof(double) * kk2, st);
+  make_m_kernel<<<(int)(((int64_t)k * k + 255) / 256 + 1), 256, 0, st>>>(G, k, M, v, z + k);
+  s = chol64(M, k, hdr, VST_ENOTSPD, st);
+  if (s != VST_OK) return s;
+  final_kernel<<<1, 256, 0, st>>>(M, k, v, z + k, logd, nparts, n, z, nll);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VST_OK : cuda_fail(e, "VIF Woodbury kernels");
+}
+
+vst_status vif_nll(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
+                   const int32_t* nn, const int32_t* nn_cnt, const double* y, int precision, double* nll, void* ws,
+                   cudaStream_t st) {
+  return precision == VST_FP64 ? vif_nll_T<double>(pts, theta, m, ind, nu, nn, nn_cnt, y, precision, nll, ws, st)
+                               : vif_nll_T<float>(pts, theta, m, ind, nu, nn, nn_cnt, y, precision, nll, ws, st);
+}
+
+}  // namespace vst

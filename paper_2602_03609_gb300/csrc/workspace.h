@@ -15,8 +15,47 @@ constexpr int kBBoxBlocks = 512;            // neighbour search: bounding-box pa
 
 inline int64_t max_buckets(int64_t n) { return 2 * n + 4096; }
 
+// VIF scratch (only when k > 0), sized for FP64 buffers
+constexpr int64_t kVifMaxWarps = 1 << 16;
+constexpr int kVifSyrkChunks = 16;
+constexpr int64_t kVifMaxK = 4096;
+
+struct VifLayout {
+  size_t S, X, U, r, gram, WE, logd, syrk, G, M, v, z, total;
+};
+
+inline size_t align256(size_t v);
+
+inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
+  VifLayout L{};
+  size_t off = 0;
+  auto take = [&off](size_t b) {
+    const size_t at = off;
+    off = (off + b + 255) & ~size_t(255);
+    return at;
+  };
+  const size_t nn = n > 0 ? (size_t)n : 1, kk = k > 0 ? (size_t)k : 1;
+  const int pm = m + 1 <= 8 ? 8 : m + 1 <= 16 ? 16 : 32;
+  const size_t npair = (size_t)pm * (pm + 1) / 2;
+  L.S = take(sizeof(double) * kk * kk);
+  L.X = take(sizeof(double) * kk * kk);
+  L.U = take(sizeof(double) * nn * kk);
+  L.r = take(sizeof(double) * nn);
+  L.gram = take(sizeof(double) * nn * npair);
+  L.WE = take(sizeof(double) * nn * (kk + 1));
+  L.logd = take(sizeof(double) * kVifMaxWarps);
+  L.syrk = take(sizeof(double) * (kk + 1) * (kk + 1) * kVifSyrkChunks);
+  L.G = take(sizeof(double) * (kk + 1) * (kk + 1));
+  L.M = take(sizeof(double) * kk * kk);
+  L.v = take(sizeof(double) * (kk + 1));
+  L.z = take(sizeof(double) * (kk + 2));
+  L.total = off;
+  return L;
+}
+
 struct WsLayout {
   size_t hdr, lagd, lagf, partial, flag;
+  size_t vif;  // VIF scratch (k > 0 only)
   // neighbour search
   size_t bbox_part, bbox, binmin, offsets, cursor, blocksums, sidx, sx, sy, pbucket;
   // Vecchia sampling
@@ -27,7 +66,6 @@ struct WsLayout {
 inline size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
 inline WsLayout ws_layout(int64_t n, int m, int64_t k) {
-  (void)k;
   WsLayout L{};
   size_t off = 0;
   auto take = [&off](size_t bytes) {
@@ -56,6 +94,7 @@ inline WsLayout ws_layout(int64_t n, int m, int64_t k) {
   L.sD = take(sizeof(double) * (size_t)nn);
   L.ready = take(sizeof(int32_t) * (size_t)nn);
   L.counter = take(sizeof(unsigned long long) * 2);
+  L.vif = take(k > 0 ? vif_layout(n, m, k).total : 0);
   L.total = off;
   return L;
 }

@@ -80,8 +80,12 @@ def test_host_validation_without_gpu(vst):
     rc = L.vecchia_factor(ctypes.byref(pts), ctypes.byref(th), 5, None, 1024, 2048, 0, 4096, 8192, 256, 16,
                           None)
     assert rc == 2
-    # VIF is rejected by the plain entry points of this version
+    # the VIF gradient is not available in this version; too many inducing points
     ind = vst._Inducing(256, 512, 5)
-    rc = L.vif_build_neighbors(ctypes.byref(pts), ctypes.byref(th), 5, ctypes.byref(ind), 1024, 2048, None, 0,
-                               256, 1 << 30, None)
-    assert rc == 1
+    rc = L.vecchia_nll_grad(ctypes.byref(pts), ctypes.byref(th), 5, ctypes.byref(ind), 1024, 2048, 4096, 0, 8192,
+                            8448, 256, 1 << 40, None)
+    assert rc == 1 and b"VIF gradient" in L.vst_last_error()
+    big = vst._Inducing(256, 512, 1 << 20)
+    rc = L.vif_build_neighbors(ctypes.byref(pts), ctypes.byref(th), 5, ctypes.byref(big), 1024, 2048, None, 0,
+                               256, 1 << 40, None)
+    assert rc == 1 and b"inducing" in L.vst_last_error()

@@ -1,0 +1,72 @@
+"""VIF (Sect. 4.3) on the GPU against the VIF oracle: residual-correlation
+neighbour sets (bit-exact except listed cut-off ties, 1e-12 relative), the
+residual factor (FP64: 1e-9), the Woodbury NLL (FP64: |dNLL|/n <= 1e-10;
+mixed: <= 1e-6), the FITC special case m = 0 and k = 1."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.vif as ovif
+import synthetic_inputs as si
+from gpu_util import check_neighbours, cuda_or_skip, dev, load_vst
+
+pytestmark = pytest.mark.gpu
+
+
+def problem(n_st, n_days, k, seed, order="time", rs=0.12, rt=2.0, nug=0.05):
+    st = si.stations_uniform(n_st, seed)
+    xy, t = si.station_days(st, n_days)
+    perm = si.time_stratified_order(t, seed) if order == "time" else si.random_order(t.shape[0], seed)
+    xy, t = np.ascontiguousarray(xy[perm]), np.ascontiguousarray(t[perm])
+    th = oracle.theta_from_ranges(1.0, rs, rt, 0.5, nug)
+    X = np.concatenate([xy / rs, (t / rt)[:, None]], axis=1)
+    C = si.kmeanspp(X, k, seed + 3, lloyd_iters=10)
+    xyk, tk = np.ascontiguousarray(C[:, :2] * rs), np.ascontiguousarray(C[:, 2] * rt)
+    y = oracle.dense_sample(xy, t, th, si.standard_normal(t.shape[0], seed + 9))
+    return xy, t, th, xyk, tk, y
+
+
+@pytest.fixture(scope="module")
+def env():
+    return cuda_or_skip(), load_vst()
+
+
+@pytest.mark.parametrize("k,m,order", [(24, 8, "time"), (40, 12, "random"), (1, 5, "time")])
+def test_vif_neighbours_factor_nll(env, k, m, order):
+    torch, vst = env
+    xy, t, th, xyk, tk, y = problem(40, 10, k, seed=k + m, order=order)
+    n = t.shape[0]
+    U, r = ovif.lowrank(xy, t, xyk, tk, th)
+    nn_o, cnt_o, rm, rm1 = ovif.knn(xy, t, th, U, r, m)
+    xy_d, t_d, y_d, xyk_d, tk_d = dev(torch, xy, t, y, xyk, tk)
+    ind = (xyk_d, tk_d)
+    ws = vst.Workspace(n, m, k)
+    nn_g, cnt_g = vst.vif_build_neighbors(xy_d, t_d, th, m, ws=ws, inducing=ind)
+    vst.vst_workspace_status(ws)
+    check_neighbours(nn_g.cpu().numpy(), cnt_g.cpu().numpy(), nn_o, cnt_o, rm, rm1)
+    nn_d, cnt_d = dev(torch, nn_o, cnt_o)
+    A_o, D_o = ovif.factor(xy, t, th, U, m, nn_o, cnt_o)
+    A, D = vst.vecchia_factor(xy_d, t_d, th, m, nn_d, cnt_d, precision=vst.FP64, ws=ws, inducing=ind)
+    vst.vst_workspace_status(ws)
+    np.testing.assert_allclose(A.cpu().numpy(), A_o, atol=1e-9)
+    np.testing.assert_allclose(D.cpu().numpy(), D_o, rtol=1e-9)
+    v_o = ovif.nll(xy, t, th, U, m, nn_o, cnt_o, y, A_o, D_o)
+    v = vst.vecchia_nll(xy_d, t_d, th, m, nn_d, cnt_d, y_d, precision=vst.FP64, ws=ws, inducing=ind)
+    vst.vst_workspace_status(ws)
+    assert abs(v.item() - v_o) / n <= 1e-10
+    vm = vst.vecchia_nll(xy_d, t_d, th, m, nn_d, cnt_d, y_d, precision=vst.MIXED, ws=ws, inducing=ind)
+    vst.vst_workspace_status(ws)
+    assert abs(vm.item() - v_o) / n <= 1e-6
+
+
+def test_vif_m0_is_fitc(env):
+    torch, vst = env
+    xy, t, th, xyk, tk, y = problem(30, 6, 16, seed=4)
+    n = t.shape[0]
+    U, r = ovif.lowrank(xy, t, xyk, tk, th)
+    nn = np.zeros((n, 0), dtype=np.int32)
+    cnt = np.zeros(n, dtype=np.int32)
+    v_o = ovif.nll(xy, t, th, U, 0, nn, cnt, y)
+    xy_d, t_d, y_d, xyk_d, tk_d, nn_d, cnt_d = dev(torch, xy, t, y, xyk, tk, nn, cnt)
+    v = vst.vecchia_nll(xy_d, t_d, th, 0, nn_d, cnt_d, y_d, precision=vst.FP64, inducing=(xyk_d, tk_d))
+    assert abs(v.item() - v_o) / n <= 1e-10
