@@ -265,10 +265,24 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
         // FP32: h = d2 * rsqrt(d2), e^-x via the exp2 unit (relative errors
         // of a few 1e-7, inside the mixed form's covariance error budget)
         const float h = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
-        const float x = G * h;
-        const float E = __expf(-x);
-        v = P * matern_M<NU, float>(x, E);
-        q1 = P * matern_xdM<NU, float>(x, E);
+        if (vif) {
+          // VIF: the residual C - U U^T is a small difference, which
+          // amplifies any systematic FP32 error in C (a rounded lag factor,
+          // an approximate exp): C is evaluated in FP64 and C - G rounded once
+          double P64, G64, Q64, L64;
+          lag_lookup<double>(th, lagd, lagf, (const LagD*)nullptr, allint, pr.td, pc.td, s.tt[r], s.tt[c], P64,
+                             G64, Q64, L64);
+          const double ddx = (double)pr.ox - (double)pc.ox, ddy = (double)pr.oy - (double)pc.oy;
+          const double x = G64 * sqrt(ddx * ddx + ddy * ddy);
+          const double c64 = P64 * matern_M<NU, double>(x, exp(-x));
+          const double gv = g.gram_f ? (double)g.gram_f[gi * NPAIR + e] : 0.0;
+          v = (float)(c64 - gv);
+        } else {
+          const float x = G * h;
+          const float E = __expf(-x);
+          v = P * matern_M<NU, float>(x, E);
+          q1 = P * matern_xdM<NU, float>(x, E);
+        }
       } else {
         xv = G * sqrt(d2);
         ev = exp(-xv);
@@ -276,8 +290,13 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       }
     }
     if (pr.valid && pc.valid) {
-      if (g.gram_d) v -= (T)g.gram_d[gi * NPAIR + e];
-      else if (g.gram_f) v -= (T)g.gram_f[gi * NPAIR + e];
+      if (g.gram_d) {
+        v -= (T)g.gram_d[gi * NPAIR + e];
+      } else if (g.gram_f && r == c) {
+        v = (T)((th.sigma1sq + th.nugget) - (double)g.gram_f[gi * NPAIR + e]);
+      } else if (g.gram_f && !MIXED) {
+        v -= (T)g.gram_f[gi * NPAIR + e];
+      }
     }
     s.K[r][c] = v;
     s.K[c][r] = v;
@@ -441,6 +460,8 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     }
     a_ref = (lane < LAST) ? df{aj, da} : df{0.0f, 0.0f};
     // D = K_ii - k . a   and   r = y_i - y_N . a   in double-float
+    // with a Gram (VIF) every entry of K, the diagonal included, is the FP64
+    // value rounded once, and K itself is the matrix the refinement solves with
     df Ds = (lane == LAST) ? (vif ? df{s.K[LAST][LAST], 0.0f} : df{th.dg_hi, th.dg_lo}) : df{0.0f, 0.0f};
     const df yl = df_split(rj);
     df rs = (lane == LAST) ? yl : df{0.0f, 0.0f};

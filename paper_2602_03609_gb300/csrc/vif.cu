@@ -52,14 +52,60 @@ __device__ __forceinline__ double cov64(const DevTheta& th, double dx, double dy
 template <int NU>
 __device__ __forceinline__ float cov32(const DevTheta& th, float dx, float dy, float u) {
   const float au = fabsf(u);
-  const float l2 = au > 0.f ? __log2f(au) : -126.f;
+  const float l2 = au > 0.f ? log2f(au) : -126.f;
   const float psi = au > 0.f ? fmaf((float)th.a, exp2f(2.0f * (float)th.alpha * l2), 1.0f) : 1.0f;
-  const float lp = __log2f(psi);
+  const float lp = log2f(psi);
   const float P = (float)th.sigma1sq * exp2f(-(float)th.p * lp);
   const float G = (float)th.c * exp2f(-0.5f * (float)th.gamma * lp);
   const float d2 = dx * dx + dy * dy;
   const float x = G * (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f);
-  return P * matern_M<NU, float>(x, __expf(-x));
+  return P * matern_M<NU, float>(x, expf(-x));
+}
+
+// integer-day range of the data times: info[0] = min day, info[1] = number of
+// days, info[2] = 1 if every time is an integer and the span is tabulable
+__global__ void day_range_kernel(const double* t, int64_t n, int64_t* info) {
+  __shared__ double smin[256], smax[256];
+  __shared__ int sint[256];
+  double lo = DBL_MAX, hi = -DBL_MAX;
+  int allint = 1;
+  for (int64_t i = threadIdx.x; i < n; i += 256) {
+    const double v = t[i];
+    lo = fmin(lo, v);
+    hi = fmax(hi, v);
+    allint &= (v == floor(v)) && fabs(v) < 1.0e9;
+  }
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  sint[threadIdx.x] = allint;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + w]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + w]);
+      sint[threadIdx.x] &= sint[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const bool ok = n > 0 && sint[0] && (smax[0] - smin[0]) < (double)kVifMaxDays;
+    info[0] = ok ? (int64_t)smin[0] : 0;
+    info[1] = ok ? (int64_t)(smax[0] - smin[0]) + 1 : 0;
+    info[2] = ok ? 1 : 0;
+  }
+}
+
+// per (data day d, inducing point p): amplitude and Matern scale of the lag
+// |dmin + d - t_p|, evaluated in FP64 and rounded once to FP32
+__global__ void day_lag_kernel(const double* tk, int k, DevTheta th, const int64_t* info, float2* tab) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (info[2] == 0) return;
+  const int64_t nd = info[1];
+  if (id >= nd * k) return;
+  const int64_t d = id / k;
+  const int p = (int)(id % k);
+  const LagD f = lag_factors(th, (double)(info[0] + d) - tk[p]);
+  tab[id] = make_float2((float)f.P, (float)f.G);
 }
 
 template <int NU>
@@ -167,12 +213,15 @@ __global__ void trinv_kernel(const double* L, int k, double* X) {
 template <typename T, int NU>
 __global__ void __launch_bounds__(256) ugemm_kernel(const double* xy, const double* t, int64_t n,
                                                     const double* xyk, const double* tk, int k, DevTheta th,
-                                                    const double* X, T* U) {
+                                                    const double* X, T* U, const int64_t* dinfo,
+                                                    const float2* dtab) {
   constexpr int BM = 64, BN = 64, BK = 16;
   __shared__ T As[BK][BM + 4];
   __shared__ T Bs[BK][BN + 4];
   __shared__ double rx[BM], ry[BM], rt[BM];
   __shared__ double zx[BK], zy[BK], zt[BK];
+  __shared__ int rday[BM];
+  const bool use_tab = std::is_same<T, float>::value && dinfo[2] != 0;
   const int64_t i0 = (int64_t)blockIdx.y * BM;
   const int c0 = blockIdx.x * BN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -181,6 +230,7 @@ __global__ void __launch_bounds__(256) ugemm_kernel(const double* xy, const doub
     rx[tid] = i < n ? xy[2 * i] : 0.0;
     ry[tid] = i < n ? xy[2 * i + 1] : 0.0;
     rt[tid] = i < n ? t[i] : 0.0;
+    rday[tid] = (i < n && use_tab) ? (int)((int64_t)rt[tid] - dinfo[0]) : 0;
   }
   T acc[4][4];
 #pragma unroll
@@ -206,6 +256,11 @@ __global__ void __launch_bounds__(256) ugemm_kernel(const double* xy, const doub
       if (i0 + ii < n && p0 + kk < k) {
         if constexpr (std::is_same<T, double>::value) {
           v = cov64<NU>(th, rx[ii] - zx[kk], ry[ii] - zy[kk], rt[ii] - zt[kk]);
+        } else if (use_tab) {
+          const float2 pg = dtab[(int64_t)rday[ii] * k + p0 + kk];
+          const float dx = (float)(rx[ii] - zx[kk]), dy = (float)(ry[ii] - zy[kk]);
+          const float x = pg.y * sqrtf(dx * dx + dy * dy);
+          v = pg.x * matern_M<NU, float>(x, expf(-x));
         } else {
           v = cov32<NU>(th, (float)(rx[ii] - zx[kk]), (float)(ry[ii] - zy[kk]), (float)(rt[ii] - zt[kk]));
         }
@@ -374,9 +429,17 @@ __global__ void __launch_bounds__(128) gram_kernel(const int32_t* nn, const int3
       if (p == PM - 1) v = (int)i;
       idx[p] = (v >= 0 && v <= i) ? v : -1;
     }
+    // FP64: plain accumulation.  FP32: every product split exactly
+    // (FMA TwoProduct) and summed in double-float, then rounded once; plain
+    // FP32 accumulation over k terms leaves errors that are correlated
+    // across the nearly collinear rows of a neighbourhood and bias the NLL.
+    constexpr bool F = std::is_same<T, float>::value;
     T acc[NPL];
+    df accd[F ? NPL : 1];
 #pragma unroll
     for (int q = 0; q < NPL; ++q) acc[q] = T(0);
+#pragma unroll
+    for (int q = 0; q < (F ? NPL : 1); ++q) accd[q] = df{0.f, 0.f};
     for (int c0 = 0; c0 < k; c0 += 32) {
       const int c = c0 + lane;
 #pragma unroll
@@ -384,18 +447,26 @@ __global__ void __launch_bounds__(128) gram_kernel(const int32_t* nn, const int3
       __syncwarp();
 #pragma unroll
       for (int q = 0; q < NPL; ++q) {
-        T s = T(0);
         const T* a = Us[wib][pr[q]];
         const T* b = Us[wib][pc[q]];
+        if constexpr (F) {
+          df sd = accd[q];
 #pragma unroll 8
-        for (int u = 0; u < 32; ++u) s = fma(a[u], b[u], s);
-        acc[q] += s;
+          for (int u = 0; u < 32; ++u) df_fma_acc(sd, a[u], df{b[u], 0.f});
+          accd[q] = sd;
+        } else {
+          T s = T(0);
+#pragma unroll 8
+          for (int u = 0; u < 32; ++u) s = fma(a[u], b[u], s);
+          acc[q] += s;
+        }
       }
       __syncwarp();
     }
 #pragma unroll
     for (int q = 0; q < NPL; ++q) {
       const int e = lane + 32 * q;
+      if constexpr (F) acc[q] = accd[q].hi + accd[q].lo;
       if (e < NPAIR) gram[i * NPAIR + e] = acc[q];
     }
   }
@@ -424,17 +495,19 @@ __global__ void wvec_kernel(const int32_t* nn, const int32_t* nn_cnt, int64_t n,
     }
     double ey = (lane < cnt && myj >= 0) ? mya * y[myj] : 0.0;
     ey = warp_sum(ey);
+    const T sT = (T)s;
+    const T myaT = (T)mya;
     for (int c0 = 0; c0 < k + 1; c0 += 32) {
       const int c = c0 + lane;
-      double v = 0.0;
-      if (c < k) v = (double)U[i * k + c];
+      T v = T(0);
+      if (c < k) v = U[i * k + c];
       for (int q = 0; q < cnt; ++q) {
         const int j = __shfl_sync(kFull, myj, q);
-        const double aq = __shfl_sync(kFull, mya, q);
-        if (c < k && j >= 0) v -= aq * (double)U[(int64_t)j * k + c];
+        const T aq = __shfl_sync(kFull, myaT, q);
+        if (c < k && j >= 0) v = fma(-aq, U[(int64_t)j * k + c], v);
       }
-      if (c == k) v = y[i] - ey;
-      if (c <= k) WE[i * (k + 1) + c] = (T)(v * s);
+      if (c < k) WE[i * (k + 1) + c] = v * sT;
+      if (c == k) WE[i * (k + 1) + c] = (T)((y[i] - ey) * s);
     }
     if (lane == 0) slog += log(Di);
   }
@@ -452,7 +525,7 @@ __global__ void __launch_bounds__(256) syrk_kernel(const T* WE, int64_t n, int k
   const int r0 = br * 32, c0 = bc * 32;
   const int64_t n0 = (int64_t)blockIdx.z * chunk, n1 = n < n0 + chunk ? n : n0 + chunk;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  T acc[4] = {T(0), T(0), T(0), T(0)};
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // 32-row products in T, their sum in FP64
   for (int64_t b = n0; b < n1; b += 32) {
     for (int q = threadIdx.x; q < 32 * 32; q += 256) {
       const int rr = q >> 5, cc = q & 31;  // rr: row of WE (sample), cc: column
@@ -467,7 +540,7 @@ __global__ void __launch_bounds__(256) syrk_kernel(const T* WE, int64_t n, int k
       T s = T(0);
 #pragma unroll 8
       for (int q = 0; q < 32; ++q) s = fma(Ar[q][rr], Ac[q][tx], s);
-      acc[u] += s;
+      acc[u] += (double)s;
     }
     __syncthreads();
   }
@@ -475,7 +548,7 @@ __global__ void __launch_bounds__(256) syrk_kernel(const T* WE, int64_t n, int k
 #pragma unroll
   for (int u = 0; u < 4; ++u) {
     const int r = r0 + ty + 8 * u, c = c0 + tx;
-    if (r < kk && c < kk && c <= r) part[(int64_t)blockIdx.z * kk2 + (int64_t)r * kk + c] = (double)acc[u];
+    if (r < kk && c < kk && c <= r) part[(int64_t)blockIdx.z * kk2 + (int64_t)r * kk + c] = acc[u];
   }
 }
 
@@ -569,10 +642,17 @@ static vst_status lowrank_T(const vst_points* pts, const vst_theta* theta, const
   if (smem > 48 * 1024) cudaFuncSetAttribute(trinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   trinv_kernel<<<(k + wpb - 1) / wpb, 32 * wpb, smem, st>>>(S, k, X);
   if (n > 0) {
+    int64_t* dinfo = reinterpret_cast<int64_t*>(vbase + V.dinfo);
+    float2* dtab = reinterpret_cast<float2*>(vbase + V.dtab);
+    day_range_kernel<<<1, 256, 0, st>>>(pts->t, n, dinfo);
+    day_lag_kernel<<<(int)((kVifMaxDays * (int64_t)k + 255) / 256), 256, 0, st>>>(ind->t, k, th, dinfo, dtab);
     const dim3 grid((k + 63) / 64, (unsigned)((n + 63) / 64));
-    if (nu == 0) ugemm_kernel<T, 0><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U);
-    else if (nu == 1) ugemm_kernel<T, 1><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U);
-    else ugemm_kernel<T, 2><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U);
+    if (nu == 0)
+      ugemm_kernel<T, 0><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U, dinfo, dtab);
+    else if (nu == 1)
+      ugemm_kernel<T, 1><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U, dinfo, dtab);
+    else
+      ugemm_kernel<T, 2><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U, dinfo, dtab);
     rdiag_kernel<T><<<(int)std::min<int64_t>((n + 7) / 8, 65535), 256, 0, st>>>(U, n, k, theta->sigma1sq, r);
   }
   const cudaError_t e = cudaGetLastError();

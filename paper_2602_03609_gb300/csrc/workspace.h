@@ -19,9 +19,10 @@ inline int64_t max_buckets(int64_t n) { return 2 * n + 4096; }
 constexpr int64_t kVifMaxWarps = 1 << 16;
 constexpr int kVifSyrkChunks = 16;
 constexpr int64_t kVifMaxK = 4096;
+constexpr int64_t kVifMaxDays = 4096;  // data-day x inducing-point lag table
 
 struct VifLayout {
-  size_t S, X, U, r, gram, WE, logd, syrk, G, M, v, z, total;
+  size_t S, X, U, r, gram, WE, logd, syrk, G, M, v, z, dinfo, dtab, total;
 };
 
 inline size_t align256(size_t v);
@@ -49,6 +50,8 @@ inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
   L.M = take(sizeof(double) * kk * kk);
   L.v = take(sizeof(double) * (kk + 1));
   L.z = take(sizeof(double) * (kk + 2));
+  L.dinfo = take(sizeof(int64_t) * 4);
+  L.dtab = take(sizeof(float) * 2 * kk * (size_t)kVifMaxDays);
   L.total = off;
   return L;
 }
