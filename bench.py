@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=3)
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-datasets leg")
+    ap.add_argument("--no-vif", action="store_true", help="skip the VIF leg")
     return ap.parse_args()
 
 
@@ -186,6 +187,64 @@ def batched_leg(vst, torch, dev, steps):
     out["workload"] = f"{ns} datasets, {n} points, m={m}, per-dataset parameters, one graph-captured launch"
     out["autotuned_shape"] = {"blocks_per_sm": shape[0], "row_chunk": shape[1]}
     out["dnll_per_n_mixed_vs_fp64"] = abs(out["mixed"]["nll_sum"] - out["fp64"]["nll_sum"]) / n
+    return out
+
+
+def vif_leg(vst, torch, dev, w):
+    """VIF (Sect. 4.3).  (a) the first 30,000 rows of the bench workload with
+    k = 1000 inducing points (seeded space-time kMeans++ with Lloyd steps on
+    coordinates scaled by the ranges): exact residual-correlation neighbour
+    search (FP64, all predecessors) and the Woodbury NLL in both forms;
+    (b) the full 1.108M rows with k = 1000 (inducing points from a 50,000-row
+    subsample, plain correlation neighbours): the mixed-form NLL."""
+    import synthetic_inputs as si
+    th = vst.vst_theta_from_ranges(*w.theta.astuple())
+    out = {}
+
+    def timed(f, reps):
+        f()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            f()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    nv, k = 30000, 1000
+    sub = type(w)(name="sub", xy=w.xy[:nv], t=w.t[:nv], z=w.z[:nv], theta=w.theta, m=w.m, order=None)
+    xyk, tk = si.inducing_points(sub, k, seed=11, lloyd_iters=10)
+    ind = (torch.from_numpy(xyk).to(dev), torch.from_numpy(tk).to(dev))
+    xy, t = torch.from_numpy(w.xy[:nv].copy()).to(dev), torch.from_numpy(w.t[:nv].copy()).to(dev)
+    y = torch.from_numpy(w.z[:nv].copy()).to(dev)
+    ws = vst.Workspace(nv, w.m, k, device=dev)
+    knn_ms = timed(lambda: vst.vif_build_neighbors(xy, t, th, w.m, ws=ws, inducing=ind), 1)
+    nn, cnt = vst.vif_build_neighbors(xy, t, th, w.m, ws=ws, inducing=ind)
+    t64 = timed(lambda: vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.FP64, ws=ws, inducing=ind), 2)
+    v64 = vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.FP64, ws=ws, inducing=ind).item()
+    tmx = timed(lambda: vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED, ws=ws, inducing=ind), 3)
+    vmx = vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED, ws=ws, inducing=ind).item()
+    vst.vst_workspace_status(ws)
+    out["sub"] = {"n": nv, "k": k, "m": w.m, "knn_ms": knn_ms, "knn_queries_per_s": nv / (knn_ms * 1e-3),
+                  "nll_fp64_ms": t64, "nll_mixed_ms": tmx, "dnll_per_n": abs(vmx - v64) / nv}
+    del ws, nn, cnt
+    # full size, mixed
+    xy, t, y = (torch.from_numpy(a).to(dev) for a in (w.xy, w.t, w.z))
+    ws0 = vst.Workspace(w.n, w.m, device=dev)
+    nn, cnt = vst.vif_build_neighbors(xy, t, th, w.m, ws=ws0)
+    del ws0
+    r = np.random.default_rng(5).choice(w.n, 50000, replace=False)
+    r.sort()
+    sub = type(w)(name="sub", xy=w.xy[r], t=w.t[r], z=w.z[r], theta=w.theta, m=w.m, order=None)
+    xyk, tk = si.inducing_points(sub, k, seed=11, lloyd_iters=10)
+    ind = (torch.from_numpy(xyk).to(dev), torch.from_numpy(tk).to(dev))
+    ws = vst.Workspace(w.n, w.m, k, device=dev)
+    tmx = timed(lambda: vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED, ws=ws, inducing=ind), 2)
+    vst.vst_workspace_status(ws)
+    out["full"] = {"n": w.n, "k": k, "m": w.m, "nll_mixed_ms": tmx, "value": 1e3 / tmx, "unit": "VIF NLL evals/s"}
+    del ws
+    torch.cuda.empty_cache()
     return out
 
 
@@ -409,6 +468,10 @@ def run_ours(args):
     }
     if not args.no_batched:
         line["batched"] = batched_leg(vst, torch, dev, args.steps)
+    if not args.no_vif:
+        del ws
+        torch.cuda.empty_cache()
+        line["vif"] = vif_leg(vst, torch, dev, w)
     if not args.no_baseline:
         import oracle  # CPU-baseline leg only
         line["cpu_baseline"] = cpu_baseline(w, oracle.theta_native(w.theta))

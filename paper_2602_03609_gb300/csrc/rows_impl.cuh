@@ -241,7 +241,10 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
 
   // ---- 2. local covariance, lower triangle distributed over the lanes
   const T diag = MIXED ? (T)th.dg_hi : (T)(th.sigma1sq + th.nugget);
-  const bool vif = g.gram_d != nullptr || g.gram_f != nullptr;
+  // a Gram (VIF) is only ever passed to the factor mode; the NLL and
+  // gradient instantiations compile without the VIF code
+  constexpr bool CAN_VIF = (MODE == kModeFactor);
+  const bool vif = CAN_VIF && (g.gram_d != nullptr || g.gram_f != nullptr);
   (void)vif;
   const auto* lags = lag_smem ? bs->lag : nullptr;
 #pragma unroll 2
@@ -265,7 +268,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
         // FP32: h = d2 * rsqrt(d2), e^-x via the exp2 unit (relative errors
         // of a few 1e-7, inside the mixed form's covariance error budget)
         const float h = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
-        if (vif) {
+        if (CAN_VIF && vif) {
           // VIF: the residual C - U U^T is a small difference, which
           // amplifies any systematic FP32 error in C (a rounded lag factor,
           // an approximate exp): C is evaluated in FP64 and C - G rounded once
@@ -289,7 +292,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
         v = P * matern_M<NU, T>(xv, ev);
       }
     }
-    if (pr.valid && pc.valid) {
+    if (CAN_VIF && vif && pr.valid && pc.valid) {
       if (g.gram_d) {
         v -= (T)g.gram_d[gi * NPAIR + e];
       } else if (g.gram_f && r == c) {
