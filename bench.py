@@ -65,6 +65,10 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-datasets leg")
     ap.add_argument("--no-vif", action="store_true", help="skip the VIF leg")
+    ap.add_argument("--legs", default="main,batched,vif,baseline",
+                    help="comma list of legs to run: main, batched, vif, baseline")
+    ap.add_argument("--vif-n", type=int, default=30000, help="rows of the exact-search VIF leg")
+    ap.add_argument("--vif-full", type=int, default=1, help="1: also time the full-size VIF NLL")
     return ap.parse_args()
 
 
@@ -190,7 +194,7 @@ def batched_leg(vst, torch, dev, steps):
     return out
 
 
-def vif_leg(vst, torch, dev, w):
+def vif_leg(vst, torch, dev, w, nv=30000, full=True):
     """VIF (Sect. 4.3).  (a) the first 30,000 rows of the bench workload with
     k = 1000 inducing points (seeded space-time kMeans++ with Lloyd steps on
     coordinates scaled by the ranges): exact residual-correlation neighbour
@@ -212,7 +216,7 @@ def vif_leg(vst, torch, dev, w):
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
-    nv, k = 30000, 1000
+    k = 1000
     sub = type(w)(name="sub", xy=w.xy[:nv], t=w.t[:nv], z=w.z[:nv], theta=w.theta, m=w.m, order=None)
     xyk, tk = si.inducing_points(sub, k, seed=11, lloyd_iters=10)
     ind = (torch.from_numpy(xyk).to(dev), torch.from_numpy(tk).to(dev))
@@ -229,6 +233,8 @@ def vif_leg(vst, torch, dev, w):
     out["sub"] = {"n": nv, "k": k, "m": w.m, "knn_ms": knn_ms, "knn_queries_per_s": nv / (knn_ms * 1e-3),
                   "nll_fp64_ms": t64, "nll_mixed_ms": tmx, "dnll_per_n": abs(vmx - v64) / nv}
     del ws, nn, cnt
+    if not full:
+        return out
     # full size, mixed
     xy, t, y = (torch.from_numpy(a).to(dev) for a in (w.xy, w.t, w.z))
     ws0 = vst.Workspace(w.n, w.m, device=dev)
@@ -320,6 +326,16 @@ def run_ours(args):
 
     w = workload(args.workload)
     th = vst.vst_theta_from_ranges(*w.theta.astuple())
+    legs = set(args.legs.split(","))
+    if "main" not in legs:
+        out = {"legs": sorted(legs)}
+        if "vif" in legs:
+            out["vif"] = vif_leg(vst, torch, dev, w, args.vif_n, args.vif_full != 0)
+        if "batched" in legs:
+            out["batched"] = batched_leg(vst, torch, dev, args.steps)
+        if rank == 0:
+            print(json.dumps(out), flush=True)
+        return 0
     stream = torch.cuda.current_stream()
     xy = torch.from_numpy(w.xy).to(dev)
     t = torch.from_numpy(w.t).to(dev)
@@ -466,13 +482,13 @@ def run_ours(args):
         "gpu_launches": 5 * args.steps,
         "clocks": clk,
     }
-    if not args.no_batched:
+    if not args.no_batched and "batched" in legs:
         line["batched"] = batched_leg(vst, torch, dev, args.steps)
-    if not args.no_vif:
+    if not args.no_vif and "vif" in legs:
         del ws
         torch.cuda.empty_cache()
-        line["vif"] = vif_leg(vst, torch, dev, w)
-    if not args.no_baseline:
+        line["vif"] = vif_leg(vst, torch, dev, w, args.vif_n, args.vif_full != 0)
+    if not args.no_baseline and "baseline" in legs:
         import oracle  # CPU-baseline leg only
         line["cpu_baseline"] = cpu_baseline(w, oracle.theta_native(w.theta))
     print(json.dumps(line), flush=True)

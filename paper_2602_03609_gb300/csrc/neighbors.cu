@@ -205,6 +205,8 @@ __global__ void sort_buckets_kernel(int64_t nb, const int32_t* offsets, int32_t*
 
 // ---------------------------------------------------------------------------
 struct KnnArgs {
+  double inv_s1;  // 1 / sigma1^2 (correlation = covariance / sigma1^2)
+  float inv_s1f;
   const double* xy;
   const double* t;
   int64_t n;
@@ -235,11 +237,11 @@ __device__ __forceinline__ void lag_rho(const KnnArgs& A, double u, double& Prho
   const double ua = fabs(u);
   if (A.g.int_times && ua < kLagTab) {
     const LagD f = A.lagd[(int)ua];
-    Prho = f.P / A.th.sigma1sq;
+    Prho = f.P * A.inv_s1;
     G = f.G;
   } else {
     const LagD f = lag_factors(A.th, ua);
-    Prho = f.P / A.th.sigma1sq;
+    Prho = f.P * A.inv_s1;
     G = f.G;
   }
 }
@@ -253,6 +255,8 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
   const int K = A.m + 1;  // keep m+1 to detect cut-off ties
   const double NEG = -1.0e300;
 
+  __shared__ int sq_all[WARPS][64];
+  int* sq = sq_all[threadIdx.x >> 5];
   for (int64_t i = warp; i < A.n; i += total) {
     const double xi = A.xy[2 * i], yi = A.xy[2 * i + 1], ti = A.t[i];
     const float xif = (float)(xi - g.xmin), yif = (float)(yi - g.ymin);
@@ -263,6 +267,51 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
     int lid = INT_MAX;
     int count = 0;
     double thr = NEG;  // K-th best correlation once the list is full
+    float thr_lo = -FLT_MAX;  // thr rounded down to FP32 (for the FP32 filter and bounds)
+    int qn = 0;        // queued candidates awaiting the FP64 ranking
+
+    // exact FP64 correlation of the first nf queued candidates (one per lane),
+    // merged into the sorted top-K list, then the queue is compacted
+    auto flush = [&](int nf) {
+      int j = -1;
+      double rho64 = NEG;
+      if (lane < nf) {
+        j = sq[lane];
+        const double dx = A.xy[2 * (int64_t)j] - xi, dy = A.xy[2 * (int64_t)j + 1] - yi;
+        const double h = sqrt(dx * dx + dy * dy);
+        double Pj, Gj;
+        lag_rho(A, A.t[j] - ti, Pj, Gj);
+        const double x = Gj * h;
+        rho64 = Pj * matern_M<NU, double>(x, exp(-x));
+      }
+      unsigned mm = __ballot_sync(kFull, lane < nf);
+      while (mm) {
+        const int src = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const double cr64 = __shfl_sync(kFull, rho64, src);
+        const int cj = __shfl_sync(kFull, j, src);
+        if (count >= K && cr64 < thr) continue;
+        const bool better = lane < count && (lr > cr64 || (lr == cr64 && lid < cj));
+        const int p = __popc(__ballot_sync(kFull, better));
+        if (p >= K) continue;
+        const double ur = __shfl_up_sync(kFull, lr, 1);
+        const int uid = __shfl_up_sync(kFull, lid, 1);
+        if (lane > p) { lr = ur; lid = uid; }
+        if (lane == p) { lr = cr64; lid = cj; }
+        count = min(count + 1, K);
+        if (count >= K) {
+          thr = __shfl_sync(kFull, lr, K - 1);
+          thr_lo = __double2float_rd(thr);
+        }
+      }
+      __syncwarp();
+      const int rest = qn - nf;
+      const int moved = (lane < rest) ? sq[nf + lane] : 0;
+      __syncwarp();
+      if (lane < rest) sq[lane] = moved;
+      __syncwarp();
+      qn = rest;
+    };
 
     for (int w0 = 0;; w0 += 32) {
       // lane -> bin in order of increasing lag: offsets 0, -1, +1, -2, +2, ...
@@ -305,7 +354,7 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) bmax = fmaxf(bmax, __shfl_xor_sync(kFull, bmax, o));
         if (bmax == -FLT_MAX) break;
-        if (count >= K && (double)bmax + (double)g.margin < thr) break;
+        if (count >= K && bmax + g.margin < thr_lo) break;
         const unsigned bm = __ballot_sync(kFull, bound == bmax);
         if (bm == 0u) break;  // defensive: a NaN bound must not stall the loop
         const int bl = __ffs(bm) - 1;
@@ -317,8 +366,19 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
         const bool exact_lag = g.int_times != 0;
         // per-bin FP32 correlation scale for the filter (exact lag) and FP64 for the rank
         double P64 = 0.0, G64 = 0.0;
-        if (exact_lag) lag_rho(A, cu, P64, G64);
-        const float P32 = (float)P64, G32 = (float)G64;
+        float P32 = 0.f, G32 = 0.f;  // FP32 filter's lag factors (exact integer lag)
+        if (exact_lag) {
+          const int lg = (int)fabsf((float)cu);
+          if (lg < kLagTab) {
+            const float4 f = __ldg(reinterpret_cast<const float4*>(A.lagf) + lg);
+            P32 = f.x * A.inv_s1f;
+            G32 = f.y;
+          } else {
+            lag_rho(A, cu, P64, G64);
+            P32 = (float)P64;
+            G32 = (float)G64;
+          }
+        }
         (void)cPd;
 
         // enumerate the cells of ring cr around (qcx, qcy), 32 at a time
@@ -344,7 +404,7 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
               const float ddy = fmaxf(0.0f, fmaxf(y0 - yif, yif - (y0 + csf)));
               const float hlo = fmaxf(0.0f, sqrtf(ddx * ddx + ddy * ddy) - 1e-6f * csf);
               const float cbound = cP * M32<NU>(cG * hlo);
-              if (count < K || (double)cbound + (double)g.margin >= thr) {
+              if (count < K || cbound + g.margin >= thr_lo) {
                 const int b = cbin * g.ncell + cy * g.ncx + cx;
                 s = A.offsets[b];
                 int en = A.offsets[b + 1];
@@ -383,7 +443,6 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
             const int olen = __shfl_sync(kFull, len, owner);
             int j = -1;
             float rho32 = 0.0f;
-            double rho64 = NEG;
             bool pass = false;
             if (act) {
               const int pos = os + (c - (oincl - olen));
@@ -392,40 +451,24 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
                 const float dx = A.sx[pos] - xif, dy = A.sy[pos] - yif;
                 const float h = sqrtf(dx * dx + dy * dy);
                 rho32 = P32 * matern_M<NU, float>(G32 * h, __expf(-G32 * h));
-                pass = count < K || (double)rho32 + (double)g.margin + 1e-5 * thr >= thr;
+                pass = count < K || rho32 + g.margin + 1e-5f * thr_lo >= thr_lo;
               } else {
                 pass = true;
               }
             }
+            // queue the candidates that pass the FP32 filter; the exact FP64
+            // ranking runs on 32 queued candidates at a time (full lanes)
             const unsigned passm = __ballot_sync(kFull, pass);
             if (passm == 0u) continue;
-            if (pass) {
-              const double dx = A.xy[2 * (int64_t)j] - xi, dy = A.xy[2 * (int64_t)j + 1] - yi;
-              const double h = sqrt(dx * dx + dy * dy);
-              double Pj = P64, Gj = G64;
-              if (!exact_lag) lag_rho(A, A.t[j] - ti, Pj, Gj);
-              const double x = Gj * h;
-              rho64 = Pj * matern_M<NU, double>(x, exp(-x));
-            }
-            unsigned mm = passm;
-            while (mm) {
-              const int src = __ffs(mm) - 1;
-              mm &= mm - 1;
-              const double cr64 = __shfl_sync(kFull, rho64, src);
-              const int cj = __shfl_sync(kFull, j, src);
-              if (count >= K && cr64 < thr) continue;
-              const bool better = lane < count && (lr > cr64 || (lr == cr64 && lid < cj));
-              const int p = __popc(__ballot_sync(kFull, better));
-              if (p >= K) continue;
-              const double ur = __shfl_up_sync(kFull, lr, 1);
-              const int uid = __shfl_up_sync(kFull, lid, 1);
-              if (lane > p) { lr = ur; lid = uid; }
-              if (lane == p) { lr = cr64; lid = cj; }
-              count = min(count + 1, K);
-              if (count >= K) thr = __shfl_sync(kFull, lr, K - 1);
-            }
+            if (pass) sq[qn + __popc(passm & ((1u << lane) - 1u))] = j;
+            qn += __popc(passm);
+            __syncwarp();
+            if (qn >= 32) flush(32);
           }
         }
+        // before the next pruning decision: rank what is queued once it is
+        // worth a warp, or whenever the list is not full yet
+        if (qn > 0 && (qn >= 16 || count < K)) flush(qn);
         // advance the chosen lane to its next ring
         if (lane == bl) {
           ring += 1;
@@ -439,6 +482,7 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
       }
     }
 
+    while (qn > 0) flush(qn < 32 ? qn : 32);
     // write the sorted neighbour list
     const int want = (int)(i < (int64_t)A.m ? i : (int64_t)A.m);
     const int cnt = min(count, A.m);
@@ -600,6 +644,8 @@ extern "C" vst_status vif_build_neighbors(const vst_points* pts, const vst_theta
   if (e != cudaSuccess) return cuda_fail(e, "bucketing kernels");
 
   KnnArgs A{};
+  A.inv_s1 = 1.0 / theta->sigma1sq;
+  A.inv_s1f = (float)A.inv_s1;
   A.xy = pts->xy;
   A.t = pts->t;
   A.n = n;

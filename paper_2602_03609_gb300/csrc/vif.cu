@@ -220,6 +220,7 @@ __global__ void __launch_bounds__(256) ugemm_kernel(const double* xy, const doub
   __shared__ T Bs[BK][BN + 4];
   __shared__ double rx[BM], ry[BM], rt[BM];
   __shared__ double zx[BK], zy[BK], zt[BK];
+  __shared__ float4 rxy2[BM], zxy2[BK];  // (x_hi, x_lo, y_hi, y_lo) double-float coordinates
   __shared__ int rday[BM];
   const bool use_tab = std::is_same<T, float>::value && dinfo[2] != 0;
   const int64_t i0 = (int64_t)blockIdx.y * BM;
@@ -231,6 +232,8 @@ __global__ void __launch_bounds__(256) ugemm_kernel(const double* xy, const doub
     ry[tid] = i < n ? xy[2 * i + 1] : 0.0;
     rt[tid] = i < n ? t[i] : 0.0;
     rday[tid] = (i < n && use_tab) ? (int)((int64_t)rt[tid] - dinfo[0]) : 0;
+    const float xh = (float)rx[tid], yh = (float)ry[tid];
+    rxy2[tid] = make_float4(xh, (float)(rx[tid] - (double)xh), yh, (float)(ry[tid] - (double)yh));
   }
   T acc[4][4];
 #pragma unroll
@@ -245,6 +248,8 @@ __global__ void __launch_bounds__(256) ugemm_kernel(const double* xy, const doub
       zx[tid] = p < k ? xyk[2 * p] : 0.0;
       zy[tid] = p < k ? xyk[2 * p + 1] : 0.0;
       zt[tid] = p < k ? tk[p] : 0.0;
+      const float xh = (float)zx[tid], yh = (float)zy[tid];
+      zxy2[tid] = make_float4(xh, (float)(zx[tid] - (double)xh), yh, (float)(zy[tid] - (double)yh));
     }
     __syncthreads();
     // S tile: 64 rows x 16 inducing points, 4 per thread
@@ -258,7 +263,9 @@ __global__ void __launch_bounds__(256) ugemm_kernel(const double* xy, const doub
           v = cov64<NU>(th, rx[ii] - zx[kk], ry[ii] - zy[kk], rt[ii] - zt[kk]);
         } else if (use_tab) {
           const float2 pg = dtab[(int64_t)rday[ii] * k + p0 + kk];
-          const float dx = (float)(rx[ii] - zx[kk]), dy = (float)(ry[ii] - zy[kk]);
+          // differences of double-float coordinates, all in FP32
+          const float4 a = rxy2[ii], b = zxy2[kk];
+          const float dx = (a.x - b.x) + (a.y - b.y), dy = (a.z - b.z) + (a.w - b.w);
           const float x = pg.y * sqrtf(dx * dx + dy * dy);
           v = pg.x * matern_M<NU, float>(x, expf(-x));
         } else {
@@ -515,41 +522,74 @@ __global__ void wvec_kernel(const int32_t* nn, const int32_t* nn_cnt, int64_t n,
   if (lane == 0) part[warp] = slog;
 }
 
-// partial G = WE^T WE over a row chunk: output tile 32 x 32 of the (k+1)^2
-// lower triangle, blockIdx.z = row chunk; fixed-order sum in syrk_sum_kernel
+// partial G = WE^T WE over a row chunk: 64 x 64 output tile of the (k+1)^2
+// lower triangle per block (4 x 4 per thread), 16 rows per K step,
+// blockIdx.z = row chunk.  Products accumulate in T over 256 rows and then
+// in FP64; the chunks are summed in a fixed order by syrk_sum_kernel.
 template <typename T>
 __global__ void __launch_bounds__(256) syrk_kernel(const T* WE, int64_t n, int kk, int64_t chunk, double* part) {
-  __shared__ T Ar[32][33], Ac[32][33];
+  constexpr int BT = 64, BK = 16;
+  __shared__ T As[BK][BT + 4], Bs[BK][BT + 4];
   const int br = blockIdx.y, bc = blockIdx.x;
   if (bc > br) return;
-  const int r0 = br * 32, c0 = bc * 32;
-  const int64_t n0 = (int64_t)blockIdx.z * chunk, n1 = n < n0 + chunk ? n : n0 + chunk;
-  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};  // 32-row products in T, their sum in FP64
-  for (int64_t b = n0; b < n1; b += 32) {
-    for (int q = threadIdx.x; q < 32 * 32; q += 256) {
-      const int rr = q >> 5, cc = q & 31;  // rr: row of WE (sample), cc: column
-      const int64_t s = b + rr;
-      Ar[rr][cc] = (s < n1 && r0 + cc < kk) ? WE[s * kk + r0 + cc] : T(0);
-      Ac[rr][cc] = (s < n1 && c0 + cc < kk) ? WE[s * kk + c0 + cc] : T(0);
+  const int r0 = br * BT, c0 = bc * BT;
+  const int64_t n0 = (int64_t)blockIdx.z * chunk;
+  const int64_t n1 = n < n0 + chunk ? n : n0 + chunk;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  double acc[4][4];
+  T part_acc[4][4];
+#pragma unroll
+  for (int a = 0; a < 4; ++a)
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      acc[a][b] = 0.0;
+      part_acc[a][b] = T(0);
+    }
+  int steps = 0;
+  for (int64_t b0 = n0; b0 < n1; b0 += BK) {
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * 256;
+      const int kk2 = e >> 6, cc = e & (BT - 1);
+      const int64_t srow = b0 + kk2;
+      As[kk2][cc] = (srow < n1 && r0 + cc < kk) ? WE[srow * kk + r0 + cc] : T(0);
+      Bs[kk2][cc] = (srow < n1 && c0 + cc < kk) ? WE[srow * kk + c0 + cc] : T(0);
     }
     __syncthreads();
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int rr = ty + 8 * u;
-      T s = T(0);
-#pragma unroll 8
-      for (int q = 0; q < 32; ++q) s = fma(Ar[q][rr], Ac[q][tx], s);
-      acc[u] += (double)s;
+    for (int q = 0; q < BK; ++q) {
+      T a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[q][ty * 4 + u];
+        b[u] = Bs[q][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) part_acc[u][v] = fma(a[u], b[v], part_acc[u][v]);
     }
-    __syncthreads();
+    if (++steps == 16) {  // every 256 rows: fold into FP64
+      steps = 0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          acc[u][v] += (double)part_acc[u][v];
+          part_acc[u][v] = T(0);
+        }
+    }
   }
   const int64_t kk2 = (int64_t)kk * kk;
 #pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int r = r0 + ty + 8 * u, c = c0 + tx;
-    if (r < kk && c < kk && c <= r) part[(int64_t)blockIdx.z * kk2 + (int64_t)r * kk + c] = acc[u];
-  }
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int r = r0 + ty * 4 + u, c = c0 + tx * 4 + v;
+      if (r < kk && c < kk && c <= r)
+        part[(int64_t)blockIdx.z * kk2 + (int64_t)r * kk + c] = acc[u][v] + (double)part_acc[u][v];
+    }
 }
 
 __global__ void syrk_sum_kernel(const double* part, int nchunk, int kk, double* G) {
@@ -818,7 +858,7 @@ static vst_status vif_nll_T(const vst_points* pts, const vst_theta* theta, int m
   const int kk = k + 1;
   const int64_t chunk = std::max<int64_t>((n + kVifSyrkChunks - 1) / kVifSyrkChunks, 1);
   const int nchunk = (int)std::min<int64_t>(kVifSyrkChunks, (n + chunk - 1) / chunk);
-  const int nb = (kk + 31) / 32;
+  const int nb = (kk + 63) / 64;
   if (n > 0) syrk_kernel<T><<<dim3(nb, nb, nchunk), 256, 0, st>>>(WE, n, kk, chunk, part);
   const int64_t kk2 = (int64_t)kk * kk;
   if (nchunk > 0) syrk_sum_kernel<<<(int)((kk2 + 255) / 256), 256, 0, st>>>(part, nchunk, kk, G);
