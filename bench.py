@@ -479,7 +479,10 @@ def run_ours(args):
                             "query_kernel_ms": kms / max(kl, 1), "tie_rows": info_knn["n_tie"]},
         "fallback_kernel_ms": kfb / max(lfb, 1),
         "e2e": {"value": 1e3 / e2e_ms, "unit": "evals/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 5 * args.steps,
+        # per mixed step: header init, lag table, per-point records, row
+        # kernel, FP64 fallback row kernel (exits at once when no row is
+        # flagged), reduction of the per-warp partials
+        "gpu_launches": 6 * args.steps,
         "clocks": clk,
     }
     if not args.no_batched and "batched" in legs:

@@ -88,6 +88,43 @@ void launch_lag_table(const DevTheta& th, LagD* d, LagF* f, cudaStream_t st) {
 
 void launch_init_header(WsHeader* h, cudaStream_t st) { init_header_kernel<<<1, 1, 0, st>>>(h); }
 
+// Per-point records of the mixed form: x, y coordinates and the response
+// split into FP32 hi + lo parts, integer day test (same rule as the FP64 row
+// kernel: t integral and |t| < 1e9), fallback flags cleared.
+__global__ void prep_points_kernel(int64_t n, const double* xy, const double* t, const double* y, PrepPt* out,
+                                   uint8_t* flag) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const double2 c = make_double2(xy[2 * i], xy[2 * i + 1]);  // xy need not be 16-byte aligned
+    const double tt = t[i];
+    const double v = y ? y[i] : 0.0;
+    PrepPt p;
+    p.xhi = (float)c.x;
+    p.xlo = (float)(c.x - (double)p.xhi);
+    p.yhi = (float)c.y;
+    p.ylo = (float)(c.y - (double)p.yhi);
+    p.vhi = (float)v;
+    p.vlo = (float)(v - (double)p.vhi);
+    const bool tint = (tt == floor(tt)) && fabs(tt) < 1.0e9;
+    p.td = tint ? (int)tt : 0;
+    p.tint = tint ? 1 : 0;
+    float4* o = reinterpret_cast<float4*>(out + i);
+    o[0] = make_float4(p.xhi, p.xlo, p.yhi, p.ylo);
+    o[1] = make_float4(p.vhi, p.vlo, __int_as_float(p.td), __int_as_float(p.tint));
+    if (flag) flag[i] = 0;
+  }
+}
+
+void launch_prep_points(int64_t n, const double* xy, const double* t, const double* y, PrepPt* out,
+                        uint8_t* flag, cudaStream_t st) {
+  if (n <= 0) return;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n + 255) / 256, cap = (int64_t)(sms > 0 ? sms : 1) * 8;
+  prep_points_kernel<<<(unsigned)(want < cap ? want : cap), 256, 0, st>>>(n, xy, t, y, out, flag);
+}
+
 void launch_reduce_partials(const double* p0, int64_t w0, const double* p1, int64_t w1, double nll_const,
                             double* nll, double* grad, cudaStream_t st) {
   reduce_partials_kernel<<<1, 256, 0, st>>>(p0, w0, p1, w1, nll_const, nll, grad);
@@ -124,10 +161,7 @@ DevTheta dev_theta(const vst_theta* th) {
   d.alpha = th->alpha;
   d.delta = th->delta;
   d.nu = th->nu;
-  d.p = th->delta + th->gamma;  // delta + gamma d/2, d = 2
-  const double dg = th->sigma1sq + th->nugget;
-  d.dg_hi = (float)dg;
-  d.dg_lo = (float)(dg - (double)d.dg_hi);
+  finish_dev_theta(d);
   return d;
 }
 
@@ -175,10 +209,8 @@ vst_status run_rows(const vst_points* pts, const vst_theta* theta, int m, const 
 
   init_header_kernel<<<1, 1, 0, st>>>(hdr);
   lag_table_kernel<<<dim3((kLagTab + 127) / 128, 1), 128, 0, st>>>(nullptr, th, lagd, lagf);
-  if (mixed && n > 0) {
-    cudaError_t e = cudaMemsetAsync(flag, 0, (size_t)n, st);
-    if (e != cudaSuccess) return cuda_fail(e, "memset flags");
-  }
+  PrepPt* prep = reinterpret_cast<PrepPt*>(base + L.prep);
+  if (mixed) launch_prep_points(n, pts->xy, pts->t, mode == kModeFactor ? nullptr : y, prep, flag, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "launch");
 
@@ -199,6 +231,7 @@ vst_status run_rows(const vst_points* pts, const vst_theta* theta, int m, const 
   g.hdr = hdr;
   g.tau = 1.0e4f;
   g.offsets = nullptr;
+  g.prep = prep;
   const int pm = m + 1;
   apply_launch_shape(g, 0, precision, nu, pm);
   forced_launch_shape(g);

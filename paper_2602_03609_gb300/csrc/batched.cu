@@ -65,7 +65,7 @@ static void tuned_store(int batched, int precision, int nu, int pm, int bps, int
 // batched workspace: header | DevTheta[nsets] | LagD[nsets][kLagTab] |
 // LagF[nsets][kLagTab] | per-row results [n][6] (48 B) | flags [n]
 struct BatchLayout {
-  size_t hdr, th, lagd, lagf, rows, flag, total;
+  size_t hdr, th, lagd, lagf, rows, flag, prep, total;
 };
 static BatchLayout batch_layout(int nsets, int64_t n) {
   BatchLayout L{};
@@ -82,6 +82,7 @@ static BatchLayout batch_layout(int nsets, int64_t n) {
   L.lagf = take(sizeof(LagF) * kLagTab * ns);
   L.rows = take(48 * nn);
   L.flag = take(nn);
+  L.prep = take(sizeof(PrepPt) * nn);
   L.total = off;
   return L;
 }
@@ -114,10 +115,7 @@ __global__ void prep_sets_kernel(int nsets, int64_t n_total, const int64_t* offs
   o.alpha = ok ? th.alpha : 0.5;
   o.delta = ok ? th.delta : 0.5;
   o.nu = ok ? th.nu : 1.5;
-  o.p = o.delta + o.gamma;
-  const double dg = o.sigma1sq + o.nugget;
-  o.dg_hi = (float)dg;
-  o.dg_lo = (float)(dg - (double)o.dg_hi);
+  finish_dev_theta(o);
   out[d] = o;
 }
 
@@ -175,7 +173,10 @@ static vst_status batched_setup(int nsets, int64_t n_total, const int64_t* offse
   prep_sets_kernel<<<(nsets + 127) / 128, 128, 0, st>>>(nsets, n_total, offsets, thetas, nu, dth, hdr);
   lag_table_kernel<<<dim3((kLagTab + 127) / 128, nsets), 128, 0, st>>>(dth, DevTheta{}, lagd, lagf);
   cudaError_t e = cudaSuccess;
-  if (n_total > 0) e = cudaMemsetAsync(flag, 0, (size_t)n_total, st);
+  if (precision == VST_MIXED)
+    launch_prep_points(n_total, xy, t, y, reinterpret_cast<PrepPt*>(base + L.prep), flag, st);
+  else if (n_total > 0)
+    e = cudaMemsetAsync(flag, 0, (size_t)n_total, st);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "batched setup");
   return VST_OK;
@@ -245,6 +246,7 @@ static vst_status batched_entry(int nsets, int64_t n_total, const int64_t* offse
   g.lagf_sets = reinterpret_cast<LagF*>(base + L.lagf);
   g.nsets = nsets;
   g.row_out = reinterpret_cast<double*>(base + L.rows);
+  g.prep = reinterpret_cast<const PrepPt*>(base + L.prep);
   return launch_batched_rows(g, nuc, precision, m, nsets, offsets, nll, grad, st);
 }
 

@@ -24,6 +24,30 @@ struct DevTheta {
   double sigma1sq, c, a, gamma, nugget, alpha, delta, nu;
   double p;            // delta + gamma * d / 2 with d = 2
   float dg_hi, dg_lo;  // sigma1^2 + nugget as a double-float (mixed form's diagonal)
+  // FP32 constants of the mixed form's gradient: 1/sigma1^2, 1/c, gamma/2, p
+  float inv_s1f, inv_cf, hgf, pf;
+};
+
+// Derived fields of a DevTheta whose eight parameters are set.
+__host__ __device__ inline void finish_dev_theta(DevTheta& d) {
+  d.p = d.delta + d.gamma;  // delta + gamma d/2, d = 2
+  const double dg = d.sigma1sq + d.nugget;
+  d.dg_hi = (float)dg;
+  d.dg_lo = (float)(dg - (double)d.dg_hi);
+  d.inv_s1f = (float)(1.0 / d.sigma1sq);
+  d.inv_cf = (float)(1.0 / d.c);
+  d.hgf = (float)(0.5 * d.gamma);
+  d.pf = (float)d.p;
+}
+
+// Per-point record read by the mixed-precision row kernel, written once per
+// call so that the per-row work has no FP64 arithmetic: coordinates and the
+// response as double-floats (hi + lo), the day index and whether the time is
+// an integer day (|t| < 1e9).
+struct __align__(16) PrepPt {
+  float xhi, xlo, yhi, ylo;
+  float vhi, vlo;
+  int td, tint;
 };
 
 // Per-lag factors of Eq. (2) and of its parameter derivatives:
@@ -93,6 +117,12 @@ __device__ __forceinline__ void df_fma_acc(df& s, float a, df b) {
   const df t = df_two_sum(s.hi, p);
   s.hi = t.hi;
   s.lo = s.lo + (t.lo + q);
+}
+// (ah + al) - (bh + bl) rounded to FP32: TwoSum of the leading parts plus the
+// trailing parts; within an ulp or two of the exactly rounded difference.
+__device__ __forceinline__ float df_diff(float ah, float al, float bh, float bl) {
+  const df t = df_two_sum(ah, -bh);
+  return t.hi + (t.lo + (al - bl));
 }
 __device__ __forceinline__ df df_split(double v) {
   const float hi = (float)v;

@@ -28,8 +28,10 @@ constexpr size_t kLagFOff = kLagDOff + sizeof(LagD) * kLagTab;
 constexpr size_t kPartOff = kLagFOff + sizeof(LagF) * kLagTab;
 constexpr size_t kPartBytes = sizeof(double) * 8 * (size_t)kMaxPartialWarps;  // one buffer
 constexpr size_t kFlagOff = kPartOff + 2 * kPartBytes;
-constexpr size_t kScratchBytes = kFlagOff + (size_t)VST_NOALLOC_MAX_N;
-static_assert(kLagFOff % 256 == 0 && kPartOff % 256 == 0 && kFlagOff % 256 == 0, "alignment");
+constexpr size_t kPrepOff = kFlagOff + (size_t)VST_NOALLOC_MAX_N;
+constexpr size_t kScratchBytes = kPrepOff + sizeof(PrepPt) * (size_t)VST_NOALLOC_MAX_N;
+static_assert(kLagFOff % 256 == 0 && kPartOff % 256 == 0 && kFlagOff % 256 == 0 && kPrepOff % 256 == 0,
+              "alignment");
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
@@ -96,9 +98,9 @@ extern "C" vst_status vecchia_nll_grad_noalloc(const vst_points* pts, const vst_
   // the array keeps the previous call's contents: reset what must start at zero
   launch_init_header(hdr, st);
   launch_lag_table(th, lagd, lagf, st);
-  cudaError_t e = cudaSuccess;
-  if (mixed && n > 0) e = cudaMemsetAsync(flag, 0, (size_t)n, st);
-  if (e == cudaSuccess) e = cudaGetLastError();
+  PrepPt* prep = reinterpret_cast<PrepPt*>(base + kPrepOff);
+  if (mixed) launch_prep_points(n, pts->xy, pts->t, y, prep, flag, st);
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "launch");
 
   RowArgs g{};
@@ -116,6 +118,7 @@ extern "C" vst_status vecchia_nll_grad_noalloc(const vst_points* pts, const vst_
   g.hdr = hdr;
   g.tau = 1.0e4f;
   g.offsets = nullptr;
+  g.prep = prep;
   const int nu = nu_code(theta->nu);
   int64_t w0 = 0, w1 = 0;
   if (n > 0) {

@@ -75,6 +75,8 @@ struct RowArgs {
   // subtracted from the covariance; at most one of the two is set
   const double* gram_d;
   const float* gram_f;
+  // mixed form: per-point records (row0-relative like xy, t, y); required
+  const PrepPt* prep;
 };
 
 // Per-position record of the local block: offsets from row i, integer day
@@ -156,7 +158,9 @@ __device__ __forceinline__ void lag_lookup(const DevTheta& th, const LagD* lagd,
       P = a.x; G = a.y; Qa = b.x; L = b.y;
     }
   } else {
-    const LagD f = lag_factors(th, ttr - ttc);
+    // integer days beyond the table: the lag itself (exact); the mixed form
+    // stores the times of a block only when some are not integer days
+    const LagD f = lag_factors(th, allint ? (double)lag : ttr - ttc);
     P = (T)f.P; G = (T)f.G; Qa = (T)f.Qa; L = (T)f.L;
   }
 }
@@ -216,27 +220,53 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   }
   if (lane == LAST) idx = (int)i;
   const bool valid = idx >= 0;
-  const double* xy = g.xy + 2 * row0;
-  const double* tv = g.t + row0;
-  const double xi = xy[2 * i], yi = xy[2 * i + 1];
-  double xj = xi, yj = yi, tj = tv[i], rj = 0.0;
-  if (valid) {
-    xj = xy[2 * (int64_t)idx];
-    yj = xy[2 * (int64_t)idx + 1];
-    tj = tv[idx];
-    if (MODE != kModeFactor) rj = g.y[row0 + idx];
+  bool allint;
+  double rj = 0.0;         // FP64 form: y at this position (0 if unused)
+  df yl = {0.0f, 0.0f};    // mixed form: the same as a double-float
+  if constexpr (MIXED) {
+    // per-point records: FP32 offsets from double-float coordinates; unused
+    // positions read row i's record (zero offsets, its day)
+    const PrepPt* pp = g.prep + row0;
+    const int64_t src = valid ? (int64_t)idx : i;
+    const float4 ci = __ldg(reinterpret_cast<const float4*>(pp + i));
+    const float4 cj = __ldg(reinterpret_cast<const float4*>(pp + src));
+    const float4 qj = __ldg(reinterpret_cast<const float4*>(pp + src) + 1);
+    const int tdj = __float_as_int(qj.z);
+    allint = __all_sync(kFull, __float_as_int(qj.w) != 0);
+    if (MODE != kModeFactor && valid) yl = df{qj.x, qj.y};
+    if (lane < PM) {
+      Pos<T> p;
+      p.ox = df_diff(cj.x, cj.y, ci.x, ci.y);
+      p.oy = df_diff(cj.z, cj.w, ci.z, ci.w);
+      p.td = allint ? tdj : 0;
+      p.valid = valid;
+      s.pos[lane] = p;
+      if (!allint) s.tt[lane] = g.t[row0 + src];
+    }
+  } else {
+    const double* xy = g.xy + 2 * row0;
+    const double* tv = g.t + row0;
+    const double xi = xy[2 * i], yi = xy[2 * i + 1];
+    double xj = xi, yj = yi, tj = tv[i];
+    if (valid) {
+      xj = xy[2 * (int64_t)idx];
+      yj = xy[2 * (int64_t)idx + 1];
+      tj = tv[idx];
+      if (MODE != kModeFactor) rj = g.y[row0 + idx];
+    }
+    const bool tint = (tj == floor(tj)) && fabs(tj) < 1.0e9;
+    allint = __all_sync(kFull, tint);
+    if (lane < PM) {
+      Pos<T> p;
+      p.ox = (T)(xj - xi);
+      p.oy = (T)(yj - yi);
+      p.td = allint ? (int)tj : 0;
+      p.valid = valid;
+      s.pos[lane] = p;
+      s.tt[lane] = tj;
+    }
   }
-  const bool tint = (tj == floor(tj)) && fabs(tj) < 1.0e9;
-  const bool allint = __all_sync(kFull, tint);
-  if (lane < PM) {
-    Pos<T> p;
-    p.ox = (T)(xj - xi);
-    p.oy = (T)(yj - yi);
-    p.td = allint ? (int)tj : 0;
-    p.valid = valid;
-    s.pos[lane] = p;
-    s.tt[lane] = tj;
-  }
+  const T yv = MIXED ? (T)yl.hi : (T)rj;  // y in T (solves)
   __syncwarp();
 
   // ---- 2. local covariance, lower triangle distributed over the lanes
@@ -392,7 +422,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   // forward solve z = L^{-1} y_local (NLL of the FP64 form; b for the gradient)
   T zj = T(0);
   if ((!MIXED && MODE != kModeFactor) || MODE == kModeNllGrad) {
-    T accz = (lane < PM) ? (T)rj : T(0);
+    T accz = (lane < PM) ? yv : T(0);
 #pragma unroll
     for (int k = 0; k < PM; ++k) {
       const T zk = __shfl_sync(kFull, accz * dinv, k);
@@ -446,32 +476,44 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       }
       if (valid && !vif) res.lo = fmaf(-th.dg_lo, aj, res.lo);
     }
-    const float rf = res.hi + res.lo;
-    float accr = (lane < LAST) ? rf : 0.0f, dz = 0.0f;
-#pragma unroll
-    for (int k = 0; k < LAST; ++k) {
-      const float zk = __shfl_sync(kFull, accr * dinv, k);
-      if (lane == k) dz = zk;
-      if (lane > k) accr = fmaf(-a[k], zk, accr);
-    }
-    float acc2 = (lane < LAST) ? dz : 0.0f, da = 0.0f;
-#pragma unroll
-    for (int k = LAST - 1; k >= 0; --k) {
-      const float dk = __shfl_sync(kFull, acc2 * dinv, k);
-      if (lane == k) da = dk;
-      if (lane < k) acc2 = fmaf(-Lsm[k][lane], dk, acc2);
-    }
-    a_ref = (lane < LAST) ? df{aj, da} : df{0.0f, 0.0f};
-    // D = K_ii - k . a   and   r = y_i - y_N . a   in double-float
     // with a Gram (VIF) every entry of K, the diagonal included, is the FP64
     // value rounded once, and K itself is the matrix the refinement solves with
     df Ds = (lane == LAST) ? (vif ? df{s.K[LAST][LAST], 0.0f} : df{th.dg_hi, th.dg_lo}) : df{0.0f, 0.0f};
-    const df yl = df_split(rj);
     df rs = (lane == LAST) ? yl : df{0.0f, 0.0f};
-    if (lane < LAST) {
-      df_fma_acc(Ds, -s.K[LAST][lane], a_ref);
-      df_fma_acc(rs, -yl.hi, a_ref);
-      rs.lo = fmaf(-yl.lo, a_ref.hi, rs.lo);
+    if (MODE != kModeNllGrad) {
+      // explicit step a += K_N^{-1} res, then D = K_ii - k.a, r = y_i - y_N.a
+      const float rf = res.hi + res.lo;
+      float accr = (lane < LAST) ? rf : 0.0f, dz = 0.0f;
+#pragma unroll
+      for (int k = 0; k < LAST; ++k) {
+        const float zk = __shfl_sync(kFull, accr * dinv, k);
+        if (lane == k) dz = zk;
+        if (lane > k) accr = fmaf(-a[k], zk, accr);
+      }
+      float acc2 = (lane < LAST) ? dz : 0.0f, da = 0.0f;
+#pragma unroll
+      for (int k = LAST - 1; k >= 0; --k) {
+        const float dk = __shfl_sync(kFull, acc2 * dinv, k);
+        if (lane == k) da = dk;
+        if (lane < k) acc2 = fmaf(-Lsm[k][lane], dk, acc2);
+      }
+      a_ref = (lane < LAST) ? df{aj, da} : df{0.0f, 0.0f};
+      if (lane < LAST) {
+        df_fma_acc(Ds, -s.K[LAST][lane], a_ref);
+        df_fma_acc(rs, -yl.hi, a_ref);
+        rs.lo = fmaf(-yl.lo, a_ref.hi, rs.lo);
+      }
+    } else if (lane < LAST) {
+      // the same step without the correction solves: with a* = a + K_N^{-1} res
+      // and b = K_N^{-1} y_N (computed for the adjoint),
+      //   D* = K_ii - k.a - a.res,   r* = y_i - y_N.a - b.res,
+      // exact up to terms quadratic in the FP32 solve error
+      // (the corrections are ~1e-7 of D and r: FP32 products suffice)
+      const float rf = res.hi + res.lo;
+      df_fma_acc(Ds, -s.K[LAST][lane], df{aj, 0.0f});
+      Ds.lo = fmaf(-aj, rf, Ds.lo);
+      df_fma_acc(rs, -yl.hi, df{aj, 0.0f});
+      rs.lo = fmaf(-yl.lo, aj, fmaf(-bj, rf, rs.lo));
     }
     Ds = df_warp_sum(Ds);
     rs = df_warp_sum(rs);
@@ -528,7 +570,8 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     __syncwarp();
     // off-diagonal sums of w K and w X are scaled by 1/sigma1^2 and 1/c at the end
     T gd = 0, g0 = 0, g1 = 0, g2 = 0, g3 = 0;
-    const T pexp = (T)th.p, hg = (T)(0.5 * th.gamma), hc2 = T(0.5) * c2;
+    const T pexp = MIXED ? (T)th.pf : (T)th.p, hg = MIXED ? (T)th.hgf : (T)(0.5 * th.gamma);
+    const T hc2 = T(0.5) * c2;
 #pragma unroll 2
     for (int e = lane; e < NPAIR; e += 32) {
       const int rc = bs->pairs[e];
@@ -558,7 +601,8 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
         g3 = fma(-w2 * L, Kv + T(0.5) * Xv, g3);
       }
     }
-    const T inv_s1 = T(1.0 / th.sigma1sq), inv_c = T(1.0 / th.c);
+    const T inv_s1 = MIXED ? (T)th.inv_s1f : T(1.0 / th.sigma1sq);
+    const T inv_c = MIXED ? (T)th.inv_cf : T(1.0 / th.c);
     acc.add(1, fma(g0, inv_s1, gd));
     acc.add(2, g1 * inv_c);
     acc.add(3, g2);

@@ -773,10 +773,10 @@ static vst_status vif_factor_T(const vst_points* pts, const vst_theta* theta, in
   const DevTheta th = dev_theta_vif(theta);
   launch_lag_table(th, lagd, lagf, st);
   const bool mixed = precision == VST_MIXED;
-  if (mixed && n > 0) {
-    e = cudaMemsetAsync(flag, 0, (size_t)n, st);
-    if (e != cudaSuccess) return cuda_fail(e, "memset");
-  }
+  PrepPt* prep = reinterpret_cast<PrepPt*>(base + L.prep);
+  if (mixed) launch_prep_points(n, pts->xy, pts->t, nullptr, prep, flag, st);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "prep kernel");
   RowArgs g{};
   g.xy = pts->xy;
   g.t = pts->t;
@@ -793,6 +793,7 @@ static vst_status vif_factor_T(const vst_points* pts, const vst_theta* theta, in
   g.hdr = hdr;
   g.tau = 1.0e4f;
   g.partial = reinterpret_cast<double*>(base + L.partial);
+  g.prep = prep;
   if constexpr (std::is_same<T, double>::value) g.gram_d = gram;
   else g.gram_f = gram;
   apply_launch_shape(g, 0, precision, nu, m + 1);

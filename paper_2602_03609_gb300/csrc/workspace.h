@@ -57,7 +57,7 @@ inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
 }
 
 struct WsLayout {
-  size_t hdr, lagd, lagf, partial, flag;
+  size_t hdr, lagd, lagf, partial, flag, prep;
   size_t vif;  // VIF scratch (k > 0 only)
   // neighbour search
   size_t bbox_part, bbox, binmin, offsets, cursor, blocksums, sidx, sx, sy, pbucket;
@@ -83,6 +83,7 @@ inline WsLayout ws_layout(int64_t n, int m, int64_t k) {
   L.lagf = take(sizeof(LagF) * kLagTab);
   L.partial = take(sizeof(double) * 8 * (size_t)(1 << 16) * 2);
   L.flag = take((size_t)nn);
+  L.prep = take(sizeof(PrepPt) * (size_t)nn);
   L.bbox_part = take(sizeof(double) * 8 * kBBoxBlocks);
   L.bbox = take(sizeof(double) * 8);
   L.binmin = take(sizeof(int32_t) * kMaxTimeBins);
