@@ -25,12 +25,12 @@
 // per row, no stored factor.
 //
 // Mixed precision (T = float): covariance and Cholesky in FP32; one step of
-// iterative refinement of A_i whose residual k - K_N A_i is accumulated in
+// iterative refinement whose residual k - K_N A_i is accumulated in
 // double-float arithmetic; D_i and r_i are formed in double-float; per-warp
 // sums over rows are double-float, combined in FP64 at the end.  The FP64
-// pipe of this part runs at 1/64 of the FP32 rate, so the mixed form keeps
-// FP64 out of the per-pair and per-row work except for forming the
-// coordinate offsets and splitting y.  Rows whose Cholesky fails in FP32,
+// pipe of this part runs at 1/64 of the FP32 rate, so the mixed form has no
+// FP64 arithmetic per row: coordinates, response and day come from per-point
+// records written once per call (PrepPt).  Rows whose Cholesky fails in FP32,
 // whose D_i is not positive, or whose condition estimate
 // (max_j L_jj / min_j L_jj)^2 exceeds tau are flagged and redone by the FP64
 // instantiation.
