@@ -43,6 +43,19 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FP64_PEAK_TFLOPS = 1.25
 
 
+def _measured_peak(key, fallback):
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, KeyError, ValueError):
+        return fallback
+
+
+# dense BF16 tensor peak (a cuBLAS GEMM timed alone on this part), for the
+# VIF low-rank GEMM
+BF16_PEAK = _measured_peak("bf16_tflops", 1900.0)
+
+
 def flops_per_row(m: int) -> float:
     """Algorithmic FP operations of one row of NLL + gradient (p = m + 1):
     12 per covariance pair (distance 5, sqrt 1, scale 1, exp 1, Matern 3,
@@ -229,9 +242,13 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
     v64 = vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.FP64, ws=ws, inducing=ind).item()
     tmx = timed(lambda: vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED, ws=ws, inducing=ind), 3)
     vmx = vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED, ws=ws, inducing=ind).item()
+    t3 = timed(lambda: vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED_BF16X3, ws=ws,
+                                       inducing=ind), 3)
+    v3 = vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED_BF16X3, ws=ws, inducing=ind).item()
     vst.vst_workspace_status(ws)
     out["sub"] = {"n": nv, "k": k, "m": w.m, "knn_ms": knn_ms, "knn_queries_per_s": nv / (knn_ms * 1e-3),
-                  "nll_fp64_ms": t64, "nll_mixed_ms": tmx, "dnll_per_n": abs(vmx - v64) / nv}
+                  "nll_fp64_ms": t64, "nll_mixed_ms": tmx, "dnll_per_n": abs(vmx - v64) / nv,
+                  "nll_mixed_bf16x3_ms": t3, "dnll_per_n_bf16x3": abs(v3 - v64) / nv}
     del ws, nn, cnt
     if not full:
         return out
@@ -246,9 +263,29 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
     xyk, tk = si.inducing_points(sub, k, seed=11, lloyd_iters=10)
     ind = (torch.from_numpy(xyk).to(dev), torch.from_numpy(tk).to(dev))
     ws = vst.Workspace(w.n, w.m, k, device=dev)
-    tmx = timed(lambda: vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED, ws=ws, inducing=ind), 2)
-    vst.vst_workspace_status(ws)
-    out["full"] = {"n": w.n, "k": k, "m": w.m, "nll_mixed_ms": tmx, "value": 1e3 / tmx, "unit": "VIF NLL evals/s"}
+    full = {"n": w.n, "k": k, "m": w.m}
+    for name, prec, terms in (("mixed", vst.MIXED, 6), ("mixed_bf16x3", vst.MIXED_BF16X3, 3)):
+        f = (lambda p=prec: vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=p, ws=ws, inducing=ind))
+        tms = timed(f, 2)
+        vst.vst_profile_enable(1)
+        f()
+        parts = {nm: vst.vst_profile_read(c) for nm, c in (("u_gemm", 4), ("gram", 5), ("syrk", 6), ("rows", 0))}
+        vst.vst_profile_enable(0)
+        vst.vst_workspace_status(ws)
+        gemm_ms = parts["u_gemm"][1]
+        # algorithmic tensor work: `terms` BF16 products of the triangular
+        # GEMM U[i][c] = sum_{p <= c} S[i][p] X[c][p]: 2 (c + 1) flops per entry
+        flops = terms * float(w.n) * k * (k + 1)
+        full[name] = {"nll_ms": tms, "value": 1e3 / tms, "unit": "VIF NLL evals/s",
+                      "kernel_ms": {nm: v[1] for nm, v in parts.items()},
+                      "u_gemm_roofline": {"bound": "tensor", "achieved": flops / (gemm_ms * 1e-3) / 1e12,
+                                          "peak": BF16_PEAK, "unit": "TFLOP/s",
+                                          "frac": flops / (gemm_ms * 1e-3) / 1e12 / BF16_PEAK,
+                                          "flops_per_launch": flops, "peak_note": "measured cuBLAS bf16 (burst)"}}
+    full["nll_mixed_ms"] = full["mixed"]["nll_ms"]
+    full["value"] = full["mixed"]["value"]
+    full["unit"] = "VIF NLL evals/s"
+    out["full"] = full
     del ws
     torch.cuda.empty_cache()
     return out

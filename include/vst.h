@@ -64,11 +64,18 @@ typedef enum {
 
 typedef enum {
   VST_FP64 = 0,   /* every step in FP64 */
-  VST_MIXED = 1   /* FP32 covariance + Cholesky, one refinement step of the
-                     solve with FP64 residuals, FP64 log-determinant and
-                     accumulation; rows whose local condition estimate exceeds
-                     the threshold, or whose FP32 Cholesky fails, are redone in
-                     FP64 */
+  VST_MIXED = 1,  /* FP32 covariance + Cholesky, one refinement step of the
+                     solve with double-float residuals, FP64 log-determinant
+                     and accumulation; rows whose local condition estimate
+                     exceeds the threshold, or whose FP32 Cholesky fails, are
+                     redone in FP64.  VIF: U = Sigma_nk L^{-T} on the tensor
+                     cores, each FP32 operand split into three BF16 parts,
+                     six products accumulated in FP32 (about FP32 accuracy) */
+  VST_MIXED_BF16X3 = 2  /* as VST_MIXED, but the VIF low-rank product splits
+                           each operand into two BF16 parts and keeps three
+                           products (16 significand bits, relative error
+                           ~1e-5 per entry of U); plain Vecchia: = VST_MIXED.
+                           Single-dataset entry points only. */
 } vst_precision;
 
 /* Native parameters of Eq. (2) plus the nugget of Eq. (1):
@@ -130,8 +137,12 @@ size_t vst_workspace_size(int64_t n, int m, int64_t k);
  * The search is exact: a space-time bucket grid is pruned only by a rigorous
  * upper bound of the correlation over each bucket.
  * Synchronises `stream` once (to size the bucket grid from the point cloud's
- * bounding box).  ind != NULL with k > 0 (VIF residual correlation) is not
- * available in this version and returns VST_EINVAL. */
+ * bounding box).
+ * VIF (ind != NULL, k > 0; Sect. 4.3 with the d_c metric of Sect. 4.4.1 on the
+ * residual): the correlation is that of the latent residual
+ * R = Sigma - U U^T (see vif_lowrank_u), |R_ij| / sqrt(R_ii R_jj), taken as 0
+ * when R_ii or R_jj is at most 1e-12 sigma1sq; FP64 brute force over all
+ * predecessors (O(n^2 k) work; for moderate n). */
 vst_status vif_build_neighbors(const vst_points* pts, const vst_theta* theta, int m,
                                const vst_inducing* ind, int32_t* nn, int32_t* nn_cnt,
                                int64_t* tie_rows, int64_t tie_cap, void* workspace,
@@ -140,7 +151,10 @@ vst_status vif_build_neighbors(const vst_points* pts, const vst_theta* theta, in
 /* Vecchia factor of the response covariance Sigma~ (Sect. 4.1 with the nugget
  * of Sect. 3.1 on the diagonal): A_i = Sigma~_{i,N(i)} Sigma~_{N(i)}^{-1},
  * D_i = Sigma~_ii - A_i Sigma~_{i,N(i)}^T, N(i) = nn[i][0..nn_cnt[i]).
- * Entries q >= nn_cnt[i] of A[i] are set to 0.  Requires nn[i][q] < i. */
+ * Entries q >= nn_cnt[i] of A[i] are set to 0.  Requires nn[i][q] < i.
+ * VIF (ind != NULL, k > 0): the factor of the residual R + nugget I
+ * (Sect. 4.3), R = Sigma - U U^T, so that
+ * Sigma~_VIF = U U^T + B^{-1} diag(D) B^{-T}. */
 vst_status vecchia_factor(const vst_points* pts, const vst_theta* theta, int m,
                           const vst_inducing* ind, const int32_t* nn, const int32_t* nn_cnt,
                           int precision, double* A, double* D, void* workspace,
@@ -150,7 +164,13 @@ vst_status vecchia_factor(const vst_points* pts, const vst_theta* theta, int m,
  * approximation of Sect. 4.1):
  *   nll = n/2 log(2 pi) + 1/2 sum_i log D_i + 1/2 sum_i (y_i - A_i y_N(i))^2 / D_i.
  * nll: one FP64 device scalar.  The sum is taken in a fixed order, so repeated
- * calls give the same bits. */
+ * calls give the same bits.
+ * VIF (ind != NULL, k > 0): -log N(y; 0, Sigma~_VIF) by the Woodbury identity
+ * (the complexity remark of Sect. 4.3): with W = D^{-1/2} B U,
+ * e = D^{-1/2} B y and M = I_k + W^T W,
+ *   nll = n/2 log(2 pi) + 1/2 (sum_i log D_i + log det M)
+ *         + 1/2 (e^T e - (W^T e)^T M^{-1} (W^T e)).
+ * m = 0 gives the FITC likelihood (Sect. 4.2). */
 vst_status vecchia_nll(const vst_points* pts, const vst_theta* theta, int m,
                        const vst_inducing* ind, const int32_t* nn, const int32_t* nn_cnt,
                        const double* y, int precision, double* nll, void* workspace,
@@ -159,11 +179,24 @@ vst_status vecchia_nll(const vst_points* pts, const vst_theta* theta, int m,
 /* NLL and its gradient with respect to the native parameters in the order
  * (sigma1sq, c, a, gamma, nugget); alpha, delta and nu are held fixed and the
  * neighbour sets are held fixed.  grad: 5 FP64 device values.  The factor is
- * recomputed, not stored. */
+ * recomputed, not stored.  Plain Vecchia only: ind with k > 0 returns
+ * VST_EINVAL. */
 vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m,
                             const vst_inducing* ind, const int32_t* nn, const int32_t* nn_cnt,
                             const double* y, int precision, double* nll, double* grad,
                             void* workspace, size_t ws_bytes, void* stream);
+
+/* VIF low-rank part (Sect. 4.3): Sigma_kk = L L^T (FP64 Cholesky of the
+ * inducing-point covariance), U = Sigma_nk L^{-T} and the residual variances
+ * r_i = sigma1sq - ||U_i||^2 (latent, no nugget).
+ * U: [n][k] row-major FP64 device output; r: [n] FP64 device output.
+ * precision: VST_FP64 (FP64 GEMM), VST_MIXED or VST_MIXED_BF16X3 (Sigma_nk
+ * in FP32, U by the split-BF16 tensor-core GEMM, see vst_precision; U is
+ * formed in FP32 and widened).  Workspace: vst_workspace_size(n, 0, k).
+ * Sigma_kk not positive definite: VST_ENOTSPD in vst_workspace_status. */
+vst_status vif_lowrank_u(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind,
+                         int precision, double* U, double* r, void* workspace, size_t ws_bytes,
+                         void* stream);
 
 /* Batched NLL and gradient of nsets independent datasets (one Vecchia model
  * each, Sect. 4.1 and 3.1) in one persistent launch.  Dataset d owns rows
@@ -236,7 +269,9 @@ vst_status vecchia_sample(const vst_points* pts, const vst_theta* theta, int m,
  * records a CUDA event pair on the launching stream around every launch of
  * its main kernels, by class: 0 = fused row kernel (NLL / gradient / factor),
  * 1 = FP64 fallback row kernel of the mixed form, 2 = neighbour query kernel,
- * 3 = Vecchia sampling kernel.  vst_profile_read() synchronises on the
+ * 3 = Vecchia sampling kernel, 4 = VIF low-rank GEMM U = Sigma_nk L^{-T},
+ * 5 = VIF per-row residual Gram, 6 = VIF [W e]^T [W e] product.
+ * vst_profile_read() synchronises on the
  * recorded events and returns the number of launches of that class and their
  * summed device time (ms) since the last vst_profile_enable(1).  At most 4096
  * launches are recorded; later ones are counted but not timed (returns 1 if

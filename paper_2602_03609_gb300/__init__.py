@@ -29,11 +29,12 @@ __all__ = [
     "vecchia_sample", "vst_workspace_status", "VecchiaNLL", "theta_tuple", "vst_profile_enable",
     "vst_profile_read", "vecchia_nll_grad_noalloc", "vst_noalloc_status", "NOALLOC_MAX_N",
     "BatchedWorkspace", "vecchia_nll_grad_batched", "BatchedGraph", "vst_autotune_nll_grad",
-    "vst_autotune_nll_grad_batched", "vst_autotune_clear",
+    "vst_autotune_nll_grad_batched", "vst_autotune_clear", "MIXED_BF16X3", "vif_lowrank_u",
 ]
 
 FP64 = 0
 MIXED = 1
+MIXED_BF16X3 = 2
 MAX_M = 31
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libvst.so")
@@ -103,6 +104,8 @@ def lib():
         L.vecchia_nll_grad.restype = ctypes.c_int
         L.vecchia_nll_grad.argtypes = [PT, TH, ctypes.c_int, IN, _P, _P, _P, ctypes.c_int, _P, _P, _P,
                                        ctypes.c_size_t, _P]
+        L.vif_lowrank_u.restype = ctypes.c_int
+        L.vif_lowrank_u.argtypes = [PT, TH, IN, ctypes.c_int, _P, _P, _P, ctypes.c_size_t, _P]
         L.vecchia_sample.restype = ctypes.c_int
         L.vecchia_sample.argtypes = [PT, TH, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]
         L.vst_profile_enable.restype = None
@@ -289,6 +292,23 @@ def vecchia_nll_grad(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, nll=None, g
     return nll, grad
 
 
+def vif_lowrank_u(xy, t, theta, inducing, precision=FP64, U=None, r=None, ws=None, stream=None):
+    """VIF low rank (Sect. 4.3): U = Sigma_nk L^{-T} [n, k] and the residual
+    variances r = sigma1sq - ||U_i||^2 [n]; CUDA float64 tensors."""
+    n = t.shape[0]
+    ind, k = _inducing(inducing)
+    if ind is None:
+        raise ValueError("vif_lowrank_u needs inducing=(xyk, tk) with k > 0")
+    U = U if U is not None else torch.empty((n, k), dtype=torch.float64, device=t.device)
+    r = r if r is not None else torch.empty(n, dtype=torch.float64, device=t.device)
+    ws = _ws(ws, n, 0, k)
+    pts = _points(xy, t)
+    _check(lib().vif_lowrank_u(ctypes.byref(pts), ctypes.byref(_th(theta)), ctypes.byref(ind), int(precision),
+                               _ptr(U, torch.float64, "U"), _ptr(r, torch.float64, "r"), ws.ptr, ws.nbytes,
+                               _stream(stream)))
+    return U, r
+
+
 class BatchedWorkspace(Workspace):
     """Workspace of the batched entry points."""
 
@@ -438,6 +458,7 @@ def vst_workspace_status(ws, stream=None, raise_on_error=True):
 
 
 PROF_ROWS, PROF_FALLBACK, PROF_KNN, PROF_SAMPLE = 0, 1, 2, 3
+PROF_VIF_GEMM, PROF_VIF_GRAM, PROF_VIF_SYRK = 4, 5, 6
 
 
 def vst_profile_enable(on=True):

@@ -329,15 +329,15 @@ vst_status vecchia_factor(const vst_points* pts, const vst_theta* theta, int m, 
   vst_status s = check_inducing(ind);
   if (s == VST_OK) s = check_common(pts, theta, m, nn, nn_cnt, ws, ws_bytes, k);
   if (s != VST_OK) return s;
-  if (precision != VST_FP64 && precision != VST_MIXED) return fail(VST_EINVAL, "bad precision %d", precision);
+  if (!valid_precision(precision)) return fail(VST_EINVAL, "bad precision %d", precision);
   if (pts->n > 0 && (!D || (m > 0 && !A))) return fail(VST_EINVAL, "A/D is NULL");
   if (k > 0) {
     const WsLayout L = ws_layout(pts->n, m, k);
     launch_init_header(reinterpret_cast<WsHeader*>(static_cast<char*>(ws) + L.hdr), (cudaStream_t)stream);
     return vif_factor(pts, theta, m, ind, nu_code(theta->nu), nn, nn_cnt, precision, A, D, ws, (cudaStream_t)stream);
   }
-  return run_rows(pts, theta, m, nn, nn_cnt, nullptr, precision, kModeFactor, nullptr, nullptr, A, D, ws,
-                  (cudaStream_t)stream);
+  return run_rows(pts, theta, m, nn, nn_cnt, nullptr, plain_precision(precision), kModeFactor, nullptr, nullptr, A,
+                  D, ws, (cudaStream_t)stream);
 }
 
 vst_status vecchia_nll(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind,
@@ -347,15 +347,15 @@ vst_status vecchia_nll(const vst_points* pts, const vst_theta* theta, int m, con
   vst_status s = check_inducing(ind);
   if (s == VST_OK) s = check_common(pts, theta, m, nn, nn_cnt, ws, ws_bytes, k);
   if (s != VST_OK) return s;
-  if (precision != VST_FP64 && precision != VST_MIXED) return fail(VST_EINVAL, "bad precision %d", precision);
+  if (!valid_precision(precision)) return fail(VST_EINVAL, "bad precision %d", precision);
   if (!nll || (pts->n > 0 && !y)) return fail(VST_EINVAL, "y/nll is NULL");
   if (k > 0) {
     const WsLayout L = ws_layout(pts->n, m, k);
     launch_init_header(reinterpret_cast<WsHeader*>(static_cast<char*>(ws) + L.hdr), (cudaStream_t)stream);
     return vif_nll(pts, theta, m, ind, nu_code(theta->nu), nn, nn_cnt, y, precision, nll, ws, (cudaStream_t)stream);
   }
-  return run_rows(pts, theta, m, nn, nn_cnt, y, precision, kModeNll, nll, nullptr, nullptr, nullptr, ws,
-                  (cudaStream_t)stream);
+  return run_rows(pts, theta, m, nn, nn_cnt, y, plain_precision(precision), kModeNll, nll, nullptr, nullptr,
+                  nullptr, ws, (cudaStream_t)stream);
 }
 
 vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind,
@@ -365,10 +365,10 @@ vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m
     return fail(VST_EINVAL, "the VIF gradient is not available in this version (vecchia_nll gives the VIF NLL)");
   vst_status s = check_common(pts, theta, m, nn, nn_cnt, ws, ws_bytes, 0);
   if (s != VST_OK) return s;
-  if (precision != VST_FP64 && precision != VST_MIXED) return fail(VST_EINVAL, "bad precision %d", precision);
+  if (!valid_precision(precision)) return fail(VST_EINVAL, "bad precision %d", precision);
   if (!nll || !grad || (pts->n > 0 && !y)) return fail(VST_EINVAL, "y/nll/grad is NULL");
-  return run_rows(pts, theta, m, nn, nn_cnt, y, precision, kModeNllGrad, nll, grad, nullptr, nullptr, ws,
-                  (cudaStream_t)stream);
+  return run_rows(pts, theta, m, nn, nn_cnt, y, plain_precision(precision), kModeNllGrad, nll, grad, nullptr,
+                  nullptr, ws, (cudaStream_t)stream);
 }
 
 vst_status vst_workspace_status(const void* ws, void* stream, vst_ws_info* info) {

@@ -40,6 +40,12 @@ __host__ __device__ inline void finish_dev_theta(DevTheta& d) {
   d.pf = (float)d.p;
 }
 
+// Precision codes accepted by the single-dataset entry points; the plain
+// Vecchia path has one mixed form (VST_MIXED_BF16X3 only changes the VIF
+// low-rank product).
+inline bool valid_precision(int p) { return p == VST_FP64 || p == VST_MIXED || p == VST_MIXED_BF16X3; }
+inline int plain_precision(int p) { return p == VST_MIXED_BF16X3 ? VST_MIXED : p; }
+
 // Per-point record read by the mixed-precision row kernel, written once per
 // call so that the per-row work has no FP64 arithmetic: coordinates and the
 // response as double-floats (hi + lo), the day index and whether the time is

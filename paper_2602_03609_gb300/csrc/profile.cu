@@ -9,15 +9,15 @@ namespace vst {
 
 namespace {
 constexpr int kMaxRecords = 4096;
-constexpr int kClasses = 4;
+constexpr int kClasses = kProfClasses;
 struct Rec {
   int cls;
   cudaEvent_t a, b;
 };
 bool g_on = false;
 std::vector<Rec> g_recs;
-int64_t g_count[kClasses] = {0, 0, 0, 0};
-int64_t g_dropped[kClasses] = {0, 0, 0, 0};
+int64_t g_count[kClasses] = {};
+int64_t g_dropped[kClasses] = {};
 
 void clear() {
   for (auto& r : g_recs) {

@@ -5,7 +5,16 @@
 
 namespace vst {
 
-enum ProfileClass { kProfRows = 0, kProfFallback = 1, kProfKnn = 2, kProfSample = 3 };
+enum ProfileClass {
+  kProfRows = 0,
+  kProfFallback = 1,
+  kProfKnn = 2,
+  kProfSample = 3,
+  kProfVifGemm = 4,  // VIF low-rank U GEMM (tensor-core or FP64)
+  kProfVifGram = 5,  // VIF per-row residual Gram
+  kProfVifSyrk = 6,  // VIF [W e]^T [W e]
+  kProfClasses = 7
+};
 
 class ProfileScope {
  public:

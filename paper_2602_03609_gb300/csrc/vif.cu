@@ -48,20 +48,6 @@ __device__ __forceinline__ double cov64(const DevTheta& th, double dx, double dy
   return f.P * matern_M<NU, double>(x, exp(-x));
 }
 
-// the same in FP32 for the mixed form (psi powers through log2/exp2)
-template <int NU>
-__device__ __forceinline__ float cov32(const DevTheta& th, float dx, float dy, float u) {
-  const float au = fabsf(u);
-  const float l2 = au > 0.f ? log2f(au) : -126.f;
-  const float psi = au > 0.f ? fmaf((float)th.a, exp2f(2.0f * (float)th.alpha * l2), 1.0f) : 1.0f;
-  const float lp = log2f(psi);
-  const float P = (float)th.sigma1sq * exp2f(-(float)th.p * lp);
-  const float G = (float)th.c * exp2f(-0.5f * (float)th.gamma * lp);
-  const float d2 = dx * dx + dy * dy;
-  const float x = G * (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f);
-  return P * matern_M<NU, float>(x, expf(-x));
-}
-
 // integer-day range of the data times: info[0] = min day, info[1] = number of
 // days, info[2] = 1 if every time is an integer and the span is tabulable
 __global__ void day_range_kernel(const double* t, int64_t n, int64_t* info) {
@@ -208,21 +194,19 @@ __global__ void trinv_kernel(const double* L, int k, double* X) {
 }
 
 // ---------------------------------------------------------------------------
-// U[i][c] = sum_{p <= c} S[i][p] X[c][p], S[i][p] = C(x_i, z_p), X = L^{-1}.
-// 64 x 64 output tile per block of 256 threads, 4 x 4 per thread, K step 16.
-template <typename T, int NU>
+// FP64 form: U[i][c] = sum_{p <= c} S[i][p] X[c][p], S[i][p] = C(x_i, z_p),
+// X = L^{-1}.  64 x 64 output tile per block of 256 threads, 4 x 4 per
+// thread, K step 16, Sigma_nk evaluated on the fly.  (The mixed form uses the
+// tensor-core GEMM of vif_tc.cu.)
+template <int NU>
 __global__ void __launch_bounds__(256) ugemm_kernel(const double* xy, const double* t, int64_t n,
                                                     const double* xyk, const double* tk, int k, DevTheta th,
-                                                    const double* X, T* U, const int64_t* dinfo,
-                                                    const float2* dtab) {
+                                                    const double* X, double* U) {
   constexpr int BM = 64, BN = 64, BK = 16;
-  __shared__ T As[BK][BM + 4];
-  __shared__ T Bs[BK][BN + 4];
+  __shared__ double As[BK][BM + 2];
+  __shared__ double Bs[BK][BN + 2];
   __shared__ double rx[BM], ry[BM], rt[BM];
   __shared__ double zx[BK], zy[BK], zt[BK];
-  __shared__ float4 rxy2[BM], zxy2[BK];  // (x_hi, x_lo, y_hi, y_lo) double-float coordinates
-  __shared__ int rday[BM];
-  const bool use_tab = std::is_same<T, float>::value && dinfo[2] != 0;
   const int64_t i0 = (int64_t)blockIdx.y * BM;
   const int c0 = blockIdx.x * BN;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -231,15 +215,12 @@ __global__ void __launch_bounds__(256) ugemm_kernel(const double* xy, const doub
     rx[tid] = i < n ? xy[2 * i] : 0.0;
     ry[tid] = i < n ? xy[2 * i + 1] : 0.0;
     rt[tid] = i < n ? t[i] : 0.0;
-    rday[tid] = (i < n && use_tab) ? (int)((int64_t)rt[tid] - dinfo[0]) : 0;
-    const float xh = (float)rx[tid], yh = (float)ry[tid];
-    rxy2[tid] = make_float4(xh, (float)(rx[tid] - (double)xh), yh, (float)(ry[tid] - (double)yh));
   }
-  T acc[4][4];
+  double acc[4][4];
 #pragma unroll
   for (int a = 0; a < 4; ++a)
 #pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = T(0);
+    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
   const int pend = k < c0 + BN ? k : c0 + BN;  // X[c][p] = 0 for p > c
   for (int p0 = 0; p0 < pend; p0 += BK) {
     __syncthreads();
@@ -248,44 +229,27 @@ __global__ void __launch_bounds__(256) ugemm_kernel(const double* xy, const doub
       zx[tid] = p < k ? xyk[2 * p] : 0.0;
       zy[tid] = p < k ? xyk[2 * p + 1] : 0.0;
       zt[tid] = p < k ? tk[p] : 0.0;
-      const float xh = (float)zx[tid], yh = (float)zy[tid];
-      zxy2[tid] = make_float4(xh, (float)(zx[tid] - (double)xh), yh, (float)(zy[tid] - (double)yh));
     }
     __syncthreads();
-    // S tile: 64 rows x 16 inducing points, 4 per thread
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int e = tid + q * 256;
       const int ii = e & (BM - 1), kk = e >> 6;
-      T v = T(0);
-      if (i0 + ii < n && p0 + kk < k) {
-        if constexpr (std::is_same<T, double>::value) {
-          v = cov64<NU>(th, rx[ii] - zx[kk], ry[ii] - zy[kk], rt[ii] - zt[kk]);
-        } else if (use_tab) {
-          const float2 pg = dtab[(int64_t)rday[ii] * k + p0 + kk];
-          // differences of double-float coordinates, all in FP32
-          const float4 a = rxy2[ii], b = zxy2[kk];
-          const float dx = (a.x - b.x) + (a.y - b.y), dy = (a.z - b.z) + (a.w - b.w);
-          const float x = pg.y * sqrtf(dx * dx + dy * dy);
-          v = pg.x * matern_M<NU, float>(x, expf(-x));
-        } else {
-          v = cov32<NU>(th, (float)(rx[ii] - zx[kk]), (float)(ry[ii] - zy[kk]), (float)(rt[ii] - zt[kk]));
-        }
-      }
+      double v = 0.0;
+      if (i0 + ii < n && p0 + kk < k) v = cov64<NU>(th, rx[ii] - zx[kk], ry[ii] - zy[kk], rt[ii] - zt[kk]);
       As[kk][ii] = v;
     }
-    // X tile: Bs[kk][cc] = X[c0 + cc][p0 + kk]
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int e = tid + q * 256;
       const int kk = e & (BK - 1), cc = e >> 4;
       const int c = c0 + cc, p = p0 + kk;
-      Bs[kk][cc] = (c < k && p < k && p <= c) ? (T)X[(int64_t)c * k + p] : T(0);
+      Bs[kk][cc] = (c < k && p < k && p <= c) ? X[(int64_t)c * k + p] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
-      T a[4], b[4];
+      double a[4], b[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         a[u] = As[kk][ty * 4 + u];
@@ -662,7 +626,7 @@ __global__ void final_kernel(const double* Lm, int k, const double* v, const dou
 
 template <typename T>
 static vst_status lowrank_T(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu,
-                            char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
+                            int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
   const int64_t n = pts->n;
   const int k = (int)ind->k;
   const DevTheta th = dev_theta_vif(theta);
@@ -686,29 +650,35 @@ static vst_status lowrank_T(const vst_points* pts, const vst_theta* theta, const
     float2* dtab = reinterpret_cast<float2*>(vbase + V.dtab);
     day_range_kernel<<<1, 256, 0, st>>>(pts->t, n, dinfo);
     day_lag_kernel<<<(int)((kVifMaxDays * (int64_t)k + 255) / 256), 256, 0, st>>>(ind->t, k, th, dinfo, dtab);
-    const dim3 grid((k + 63) / 64, (unsigned)((n + 63) / 64));
-    if (nu == 0)
-      ugemm_kernel<T, 0><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U, dinfo, dtab);
-    else if (nu == 1)
-      ugemm_kernel<T, 1><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U, dinfo, dtab);
-    else
-      ugemm_kernel<T, 2><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U, dinfo, dtab);
+    if constexpr (std::is_same<T, double>::value) {
+      const dim3 grid((k + 63) / 64, (unsigned)((n + 63) / 64));
+      ProfileScope ps(kProfVifGemm, st);
+      if (nu == 0) ugemm_kernel<0><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U);
+      else if (nu == 1) ugemm_kernel<1><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U);
+      else ugemm_kernel<2><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U);
+    } else {
+      (void)dtab;
+      s = lowrank_tc(pts, theta, ind, nu, split_terms, vbase, V, hdr, st);
+      if (s != VST_OK) return s;
+    }
     rdiag_kernel<T><<<(int)std::min<int64_t>((n + 7) / 8, 65535), 256, 0, st>>>(U, n, k, theta->sigma1sq, r);
   }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "VIF low-rank kernels");
 }
 
-vst_status vif_lowrank(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu, bool fp64,
-                       char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
-  return fp64 ? lowrank_T<double>(pts, theta, ind, nu, vbase, V, hdr, st)
-              : lowrank_T<float>(pts, theta, ind, nu, vbase, V, hdr, st);
+// U and r: FP64 SIMT GEMM (VST_FP64), or the split-BF16 tensor-core GEMM with
+// 6 products (VST_MIXED) or 3 products (VST_MIXED_BF16X3)
+vst_status vif_lowrank(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu,
+                       int precision, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
+  if (precision == VST_FP64) return lowrank_T<double>(pts, theta, ind, nu, 0, vbase, V, hdr, st);
+  return lowrank_T<float>(pts, theta, ind, nu, precision == VST_MIXED_BF16X3 ? 3 : 6, vbase, V, hdr, st);
 }
 
 vst_status vif_knn(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
                    int32_t* nn, int32_t* nn_cnt, int64_t* tie_rows, int64_t tie_cap, char* vbase,
                    const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
-  vst_status s = vif_lowrank(pts, theta, ind, nu, true, vbase, V, hdr, st);
+  vst_status s = vif_lowrank(pts, theta, ind, nu, VST_FP64, vbase, V, hdr, st);
   if (s != VST_OK) return s;
   VifKnnArgs A{};
   A.xy = pts->xy;
@@ -758,13 +728,16 @@ static vst_status vif_factor_T(const vst_points* pts, const vst_theta* theta, in
                                const int32_t* nn, const int32_t* nn_cnt, int precision, double* Aout, double* Dout,
                                char* base, const WsLayout& L, char* vbase, const VifLayout& V, cudaStream_t st) {
   WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
-  vst_status s = vif_lowrank(pts, theta, ind, nu, std::is_same<T, double>::value, vbase, V, hdr, st);
+  vst_status s = vif_lowrank(pts, theta, ind, nu, precision, vbase, V, hdr, st);
   if (s != VST_OK) return s;
   const int64_t n = pts->n;
   const int k = (int)ind->k;
   T* U = reinterpret_cast<T*>(vbase + V.U);
   T* gram = reinterpret_cast<T*>(vbase + V.gram);
-  if (n > 0) launch_gram<T>(m + 1, nn, nn_cnt, n, m, k, U, gram, st);
+  if (n > 0) {
+    ProfileScope ps(kProfVifGram, st);
+    launch_gram<T>(m + 1, nn, nn_cnt, n, m, k, U, gram, st);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "gram kernel");
   LagD* lagd = reinterpret_cast<LagD*>(base + L.lagd);
@@ -772,7 +745,7 @@ static vst_status vif_factor_T(const vst_points* pts, const vst_theta* theta, in
   uint8_t* flag = reinterpret_cast<uint8_t*>(base + L.flag);
   const DevTheta th = dev_theta_vif(theta);
   launch_lag_table(th, lagd, lagf, st);
-  const bool mixed = precision == VST_MIXED;
+  const bool mixed = precision != VST_FP64;
   PrepPt* prep = reinterpret_cast<PrepPt*>(base + L.prep);
   if (mixed) launch_prep_points(n, pts->xy, pts->t, nullptr, prep, flag, st);
   e = cudaGetLastError();
@@ -860,7 +833,10 @@ static vst_status vif_nll_T(const vst_points* pts, const vst_theta* theta, int m
   const int64_t chunk = std::max<int64_t>((n + kVifSyrkChunks - 1) / kVifSyrkChunks, 1);
   const int nchunk = (int)std::min<int64_t>(kVifSyrkChunks, (n + chunk - 1) / chunk);
   const int nb = (kk + 63) / 64;
-  if (n > 0) syrk_kernel<T><<<dim3(nb, nb, nchunk), 256, 0, st>>>(WE, n, kk, chunk, part);
+  if (n > 0) {
+    ProfileScope ps(kProfVifSyrk, st);
+    syrk_kernel<T><<<dim3(nb, nb, nchunk), 256, 0, st>>>(WE, n, kk, chunk, part);
+  }
   const int64_t kk2 = (int64_t)kk * kk;
   if (nchunk > 0) syrk_sum_kernel<<<(int)((kk2 + 255) / 256), 256, 0, st>>>(part, nchunk, kk, G);
   else cudaMemsetAsync(G, 0, sizeof(double) * kk2, st);
@@ -880,3 +856,54 @@ vst_status vif_nll(const vst_points* pts, const vst_theta* theta, int m, const v
 }
 
 }  // namespace vst
+
+namespace vst {
+vst_status check_theta(const vst_theta* th);
+vst_status check_inducing(const vst_inducing* ind);
+int nu_code(double nu);
+
+__global__ void widen_kernel(const float* src, int64_t count, double* dst) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x)
+    dst[q] = (double)src[q];
+}
+}  // namespace vst
+
+using namespace vst;
+
+extern "C" vst_status vif_lowrank_u(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind,
+                                    int precision, double* U, double* r, void* ws, size_t ws_bytes, void* stream) {
+  if (!pts) return fail(VST_EINVAL, "pts is NULL");
+  const int64_t n = pts->n;
+  if (n < 0 || n >= (int64_t(1) << 31)) return fail(VST_EINVAL, "n=%lld out of range", (long long)n);
+  vst_status s = check_theta(theta);
+  if (s != VST_OK) return s;
+  if (!ind || ind->k <= 0) return fail(VST_EINVAL, "vif_lowrank_u needs k > 0 inducing points");
+  s = check_inducing(ind);
+  if (s != VST_OK) return s;
+  if (!valid_precision(precision)) return fail(VST_EINVAL, "bad precision %d", precision);
+  if (n > 0 && (!pts->xy || !pts->t || !U || !r)) return fail(VST_EINVAL, "NULL array");
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256) return fail(VST_EINVAL, "workspace NULL or not 256-byte aligned");
+  const int64_t k = ind->k;
+  const WsLayout L = ws_layout(n, 0, k);
+  if (ws_bytes < L.total) return fail(VST_ENOMEM, "workspace has %zu bytes, %zu needed", ws_bytes, L.total);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* base = static_cast<char*>(ws);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
+  char* vbase = base + L.vif;
+  const VifLayout V = vif_layout(n, 0, k);
+  launch_init_header(hdr, st);
+  s = vif_lowrank(pts, theta, ind, nu_code(theta->nu), precision, vbase, V, hdr, st);
+  if (s != VST_OK) return s;
+  if (n == 0) return VST_OK;
+  const int64_t count = n * k;
+  cudaError_t e;
+  if (precision == VST_FP64) {
+    e = cudaMemcpyAsync(U, vbase + V.U, sizeof(double) * count, cudaMemcpyDeviceToDevice, st);
+  } else {
+    widen_kernel<<<(int)std::min<int64_t>((count + 255) / 256, 152 * 64), 256, 0, st>>>(
+        reinterpret_cast<const float*>(vbase + V.U), count, U);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(r, vbase + V.r, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+  return e == cudaSuccess ? VST_OK : cuda_fail(e, "vif_lowrank_u copies");
+}

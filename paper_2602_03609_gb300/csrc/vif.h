@@ -11,6 +11,26 @@ namespace vst {
 DevTheta dev_theta(const vst_theta* th);
 inline DevTheta dev_theta_vif(const vst_theta* th) { return dev_theta(th); }
 
+// the same in FP32 for the mixed form (psi powers through log2/exp2)
+template <int NU>
+__device__ __forceinline__ float cov32(const DevTheta& th, float dx, float dy, float u) {
+  const float au = fabsf(u);
+  const float l2 = au > 0.f ? log2f(au) : -126.f;
+  const float psi = au > 0.f ? fmaf((float)th.a, exp2f(2.0f * (float)th.alpha * l2), 1.0f) : 1.0f;
+  const float lp = log2f(psi);
+  const float P = (float)th.sigma1sq * exp2f(-(float)th.p * lp);
+  const float G = (float)th.c * exp2f(-0.5f * (float)th.gamma * lp);
+  const float d2 = dx * dx + dy * dy;
+  const float x = G * (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f);
+  return P * matern_M<NU, float>(x, expf(-x));
+}
+
+// U (FP32 [n][k]) of the mixed form by the split-BF16 tensor-core GEMM
+// (vif_tc.cu); split_terms = 3 or 6.  Needs X = L^{-1}, the day range and the
+// day lag table of the workspace already computed.
+vst_status lowrank_tc(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu,
+                      int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st);
+
 vst_status vif_knn(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
                    int32_t* nn, int32_t* nn_cnt, int64_t* tie_rows, int64_t tie_cap, char* vbase,
                    const VifLayout& V, WsHeader* hdr, cudaStream_t st);

@@ -1,0 +1,385 @@
+// VIF low rank on the tensor cores (mixed form): U = Sigma_nk L^{-T}
+// (Sect. 4.3) as a BF16 tcgen05 GEMM with split operands.
+//
+// Each FP32 operand value v is split into P BF16 parts, v ~ v_0 + v_1 + ...,
+// v_0 = bf16(v), v_j = bf16(v - v_0 - ... - v_{j-1}).  The product of two
+// split values keeps the terms whose part indices sum to at most P - 1:
+//   P = 2: a0 b0 + a0 b1 + a1 b0                       (3 products)
+//   P = 3: a0 b0 + a0 b1 + a1 b0 + a0 b2 + a1 b1 + a2 b0 (6 products)
+// all accumulated in one FP32 accumulator in tensor memory.  Two parts carry
+// 16 significand bits (relative error ~1e-5 per product), three parts carry
+// 24 (the FP32 level).
+//
+// Operands in HBM, K-major BF16 (K = inducing point index p, padded to kp):
+//   A parts [P][n][kp]   A[i][p] = Sigma(x_i, z_p), FP32 evaluation
+//   B parts [P][kp][kp]  B[c][p] = (L^{-1})[c][p]  (lower triangular)
+// so that U[i][c] = sum_p A[i][p] B[c][p]; tile columns c0..c0+BN-1 need only
+// p < c0 + BN.
+//
+// GEMM kernel: one CTA of 4 warps per 128 x BN output tile.  Warp 0 lane 0
+// issues the TMA loads of 64-wide K blocks (128-byte swizzle) into a ring of
+// STAGES shared-memory stages; warp 1 lane 0 issues tcgen05.mma (M = 128,
+// N = BN, K = 16 per instruction) into a TMEM accumulator of BN columns and
+// frees each stage with tcgen05.commit (the other lanes of both warps follow
+// their lane 0 through the waits); then all four warps read the
+// accumulator (warp w owns TMEM lanes 32w..32w+31 = tile rows) and store U.
+// Every wait is limited in time; a wait that runs out reports VST_ETIMEOUT and
+// the CTA still frees its tensor memory.
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "kernels.h"
+#include "profile.h"
+#include "umma.cuh"
+#include "vif.h"
+#include "workspace.h"
+
+namespace vst {
+
+vst_status fail(vst_status s, const char* fmt, ...);
+vst_status cuda_fail(cudaError_t e, const char* where);
+
+namespace {
+
+constexpr uint64_t kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+template <int P, int BN, int STAGES>
+struct TcShape {
+  static constexpr int BM = 128, BK = 64;
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = P * (A_BYTES + B_BYTES);
+  static constexpr int BAR_BYTES = 256;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + BAR_BYTES + 1024;  // + alignment slack
+  static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
+  static_assert(BN % 32 == 0 && BN >= 32 && BN <= 256, "N tile");
+};
+
+// BF16 parts of an FP64 value (residuals exact in FP64)
+template <int P>
+__device__ __forceinline__ void split_parts(double v, __nv_bfloat16 (&o)[P]) {
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    o[j] = __double2bfloat16(v);
+    v -= (double)__bfloat162float(o[j]);
+  }
+}
+// ... of an FP32 value (residuals exact in FP32)
+template <int P>
+__device__ __forceinline__ void split_parts(float v, __nv_bfloat16 (&o)[P]) {
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    o[j] = __float2bfloat16_rn(v);
+    v -= __bfloat162float(o[j]);
+  }
+}
+
+// B parts from X = L^{-1} (FP64, row-major k x k, lower): [P][kp][kp], zero
+// outside the lower triangle and the k x k block.
+template <int P>
+__global__ void split_x_kernel(const double* X, int k, int kp, __nv_bfloat16* B) {
+  const int64_t total = (int64_t)kp * kp;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(id / kp), p = (int)(id % kp);
+    const double v = (c < k && p <= c) ? X[(int64_t)c * k + p] : 0.0;
+    __nv_bfloat16 o[P];
+    split_parts<P>(v, o);
+#pragma unroll
+    for (int j = 0; j < P; ++j) B[(int64_t)j * total + id] = o[j];
+  }
+}
+
+// double-float coordinates of the inducing points
+__global__ void ind_coords_kernel(const double* xyk, int k, float4* zf) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= k) return;
+  const double x = xyk[2 * p], y = xyk[2 * p + 1];
+  const float xh = (float)x, yh = (float)y;
+  zf[p] = make_float4(xh, (float)(x - (double)xh), yh, (float)(y - (double)yh));
+}
+
+// A parts: one thread per (row i, 8 consecutive inducing points); the
+// covariance in FP32 as in the SIMT path (per-day lag factors rounded once
+// from FP64, double-float coordinate differences), then split.
+template <int NU, int P>
+__global__ void snk_split_kernel(const double* xy, const double* t, int64_t n, const double* xyk, const double* tk,
+                                 const float4* zf, int k, int kp, DevTheta th, const int64_t* dinfo,
+                                 const float2* dtab, __nv_bfloat16* A) {
+  const int groups = kp / 8;
+  const int64_t total = n * groups;
+  const bool use_tab = dinfo[2] != 0;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = id / groups;
+    const int p0 = (int)(id % groups) * 8;
+    const double xi = xy[2 * i], yi = xy[2 * i + 1], ti = t[i];
+    const float xh = (float)xi, yh = (float)yi;
+    const float4 a = make_float4(xh, (float)(xi - (double)xh), yh, (float)(yi - (double)yh));
+    const int64_t day = use_tab ? (int64_t)ti - dinfo[0] : 0;
+    __align__(16) __nv_bfloat16 o[P][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int p = p0 + q;
+      float v = 0.0f;
+      if (p < k) {
+        if (use_tab) {
+          const float2 pg = dtab[day * k + p];
+          const float4 b = zf[p];
+          const float dx = (a.x - b.x) + (a.y - b.y), dy = (a.z - b.z) + (a.w - b.w);
+          const float x = pg.y * sqrtf(dx * dx + dy * dy);
+          v = pg.x * matern_M<NU, float>(x, expf(-x));
+        } else {
+          v = cov32<NU>(th, (float)(xi - xyk[2 * p]), (float)(yi - xyk[2 * p + 1]), (float)(ti - tk[p]));
+        }
+      }
+      __nv_bfloat16 s[P];
+      split_parts<P>(v, s);
+#pragma unroll
+      for (int j = 0; j < P; ++j) o[j][q] = s[j];
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      *reinterpret_cast<uint4*>(A + ((int64_t)j * n + i) * kp + p0) = *reinterpret_cast<const uint4*>(o[j]);
+  }
+}
+
+// part index pairs (a, b) of the kept products, a + b <= P - 1
+template <int P>
+struct SplitTerms;
+template <>
+struct SplitTerms<2> {
+  static constexpr int N = 3;
+  static __device__ __forceinline__ int a(int t) { return t == 2 ? 1 : 0; }
+  static __device__ __forceinline__ int b(int t) { return t == 1 ? 1 : 0; }
+};
+template <>
+struct SplitTerms<3> {
+  static constexpr int N = 6;
+  // (0,0) (0,1) (1,0) (0,2) (1,1) (2,0)
+  static __device__ __forceinline__ int a(int t) { return t == 2 ? 1 : t == 4 ? 1 : t == 5 ? 2 : 0; }
+  static __device__ __forceinline__ int b(int t) { return t == 1 ? 1 : t == 3 ? 2 : t == 4 ? 1 : 0; }
+};
+
+template <int P, int BN, int STAGES>
+__global__ void __launch_bounds__(128, 1)
+    ugemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
+                    int k, int kp, float* U, WsHeader* hdr) {
+  using S = TcShape<P, BN, STAGES>;
+  extern __shared__ unsigned char tc_smem[];
+  const uint32_t raw = umma::smem_u32(tc_smem);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = tc_smem + (base - raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(gbase + STAGES * S::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t m0 = (int64_t)blockIdx.x * S::BM;
+  const int c0 = blockIdx.y * BN;
+  const int kend = kp < c0 + BN ? kp : c0 + BN;  // B[c][p] = 0 for p > c
+  const int nkb = (kend + S::BK - 1) / S::BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      umma::mbar_init(&full[s], 1);
+      umma::mbar_init(&empty[s], 1);
+    }
+    umma::mbar_init(accf, 1);
+    umma::fence_mbar_init();
+  }
+  if (warp == 0) {
+    umma::tmem_alloc(umma::smem_u32(tslot), BN);
+    umma::tmem_relinquish();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  bool ok = true;
+  // lane 0 waits, the warp takes its answer (the warps stay converged)
+  auto warp_wait = [&](uint64_t* bar, uint32_t parity) {
+    bool done = true;
+    if (lane == 0) done = umma::mbar_wait(bar, parity, kWaitLimitNs);
+    return __shfl_sync(0xffffffffu, done ? 1 : 0, 0) != 0;
+  };
+
+  if (warp == 0) {
+    // producer: TMA loads of the K blocks (lane 0 issues)
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t use = (uint32_t)(kb / STAGES);
+      if (use > 0 && !warp_wait(&empty[s], (use - 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      if (lane == 0) {
+        umma::mbar_arrive_expect_tx(&full[s], S::STAGE_BYTES);
+        const uint32_t sa = base + s * S::STAGE_BYTES, sb = sa + P * S::A_BYTES;
+#pragma unroll
+        for (int j = 0; j < P; ++j) {
+          umma::tma_load_2d(sa + j * S::A_BYTES, &tmA, kb * S::BK, (int)(j * n + m0), &full[s]);
+          umma::tma_load_2d(sb + j * S::B_BYTES, &tmB, kb * S::BK, j * kp + c0, &full[s]);
+        }
+      }
+      __syncwarp();
+    }
+  } else if (warp == 1) {
+    // MMA issuer (lane 0 issues)
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(S::BM, BN);
+    uint32_t acc = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t use = (uint32_t)(kb / STAGES);
+      if (!warp_wait(&full[s], use & 1u)) {
+        ok = false;
+        break;
+      }
+      umma::fence_after_sync();
+      if (lane == 0) {
+        const uint32_t sa = base + s * S::STAGE_BYTES, sb = sa + P * S::A_BYTES;
+#pragma unroll
+        for (int kk = 0; kk < S::BK / 16; ++kk) {
+#pragma unroll
+          for (int q = 0; q < SplitTerms<P>::N; ++q) {
+            const uint64_t ad = umma::desc_kmajor_sw128(sa + SplitTerms<P>::a(q) * S::A_BYTES + kk * 32);
+            const uint64_t bd = umma::desc_kmajor_sw128(sb + SplitTerms<P>::b(q) * S::B_BYTES + kk * 32);
+            umma::mma_bf16(tmem, ad, bd, idesc, acc);
+            acc = 1;
+          }
+        }
+        umma::mma_commit(&empty[s]);
+      }
+      __syncwarp();
+    }
+    if (lane == 0) umma::mma_commit(accf);
+    __syncwarp();
+  }
+
+  // epilogue: TMEM -> registers -> U (FP32, row-major [n][k])
+  if (!warp_wait(accf, 0)) ok = false;
+  umma::fence_after_sync();
+  const int64_t i = m0 + warp * 32 + lane;
+  const bool vec = (k & 3) == 0;
+#pragma unroll 1
+  for (int cb = 0; cb < BN; cb += 32) {
+    uint32_t v[32];
+    umma::tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+    umma::tmem_wait_ld();
+    const int cc = c0 + cb;
+    if (i < n && cc < k) {
+      float* dst = U + i * k + cc;
+      if (vec && cc + 32 <= k) {
+#pragma unroll
+        for (int q = 0; q < 32; q += 4)
+          *reinterpret_cast<float4*>(dst + q) = make_float4(__uint_as_float(v[q]), __uint_as_float(v[q + 1]),
+                                                            __uint_as_float(v[q + 2]), __uint_as_float(v[q + 3]));
+      } else {
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (cc + q < k) dst[q] = __uint_as_float(v[q]);
+      }
+    }
+  }
+  if (!ok) report_error(hdr, VST_ETIMEOUT, (int64_t)blockIdx.x);
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, BN);
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D BF16 tensor map: rows x cols (cols contiguous), box 64 x box_rows, 128-byte swizzle
+bool make_map(CUtensorMap* map, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[2] = {cols, rows};
+  const cuuint64_t strides[1] = {cols * 2};
+  const cuuint32_t box[2] = {64, box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int P, int BN, int STAGES>
+cudaError_t launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t n, int k, int kp, float* U,
+                        WsHeader* hdr, cudaStream_t st, bool* map_ok) {
+  using S = TcShape<P, BN, STAGES>;
+  CUtensorMap ta, tb;
+  *map_ok = make_map(&ta, A, (uint64_t)P * n, (uint64_t)kp, S::BM) &&
+            make_map(&tb, B, (uint64_t)P * kp, (uint64_t)kp, BN);
+  if (!*map_ok) return cudaSuccess;
+  auto kern = ugemm_tc_kernel<P, BN, STAGES>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+  if (e != cudaSuccess) return e;
+  const dim3 grid((unsigned)((n + S::BM - 1) / S::BM), (unsigned)(kp / BN));
+  ProfileScope ps(kProfVifGemm, st);
+  kern<<<grid, 128, S::SMEM, st>>>(ta, tb, n, k, kp, U, hdr);
+  return cudaGetLastError();
+}
+
+template <int P>
+vst_status lowrank_tc_P(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu,
+                        char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
+  const int64_t n = pts->n;
+  const int k = (int)ind->k, kp = vif_kp(k);
+  const DevTheta th = dev_theta_vif(theta);
+  const double* X = reinterpret_cast<const double*>(vbase + V.X);
+  const int64_t* dinfo = reinterpret_cast<const int64_t*>(vbase + V.dinfo);
+  const float2* dtab = reinterpret_cast<const float2*>(vbase + V.dtab);
+  __nv_bfloat16* Ap = reinterpret_cast<__nv_bfloat16*>(vbase + V.Ap);
+  __nv_bfloat16* Bp = reinterpret_cast<__nv_bfloat16*>(vbase + V.Bp);
+  float4* zf = reinterpret_cast<float4*>(vbase + V.zf);
+  float* U = reinterpret_cast<float*>(vbase + V.U);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, sms) * 8;
+  split_x_kernel<P><<<grid, 256, 0, st>>>(X, k, kp, Bp);
+  ind_coords_kernel<<<(k + 127) / 128, 128, 0, st>>>(ind->xy, k, zf);
+  if (nu == 0)
+    snk_split_kernel<0, P><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, zf, k, kp, th, dinfo, dtab, Ap);
+  else if (nu == 1)
+    snk_split_kernel<1, P><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, zf, k, kp, th, dinfo, dtab, Ap);
+  else
+    snk_split_kernel<2, P><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, zf, k, kp, th, dinfo, dtab, Ap);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "split kernels");
+  bool map_ok = true;
+  // two parts: 128 x 256 tiles; three parts: 128 x 128 tiles (two stages fit either way)
+  if constexpr (P == 2) e = launch_gemm<2, 256, 2>(Ap, Bp, n, k, kp, U, hdr, st, &map_ok);
+  else e = launch_gemm<3, 128, 2>(Ap, Bp, n, k, kp, U, hdr, st, &map_ok);
+  if (!map_ok) return fail(VST_ECUDA, "cuTensorMapEncodeTiled unavailable or rejected the operand layout");
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core U GEMM");
+  return VST_OK;
+}
+
+}  // namespace
+
+// U (FP32, [n][k]) of the mixed form on the tensor cores; split_terms = 3 or 6.
+// Needs X = L^{-1}, the day range and the day lag table already in place.
+vst_status lowrank_tc(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu,
+                      int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
+  if (pts->n <= 0) return VST_OK;
+  return split_terms == 3 ? lowrank_tc_P<2>(pts, theta, ind, nu, vbase, V, hdr, st)
+                          : lowrank_tc_P<3>(pts, theta, ind, nu, vbase, V, hdr, st);
+}
+
+}  // namespace vst

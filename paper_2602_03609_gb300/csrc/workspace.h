@@ -22,8 +22,14 @@ constexpr int64_t kVifMaxK = 4096;
 constexpr int64_t kVifMaxDays = 4096;  // data-day x inducing-point lag table
 
 struct VifLayout {
-  size_t S, X, U, r, gram, WE, logd, syrk, G, M, v, z, dinfo, dtab, total;
+  size_t S, X, U, r, gram, WE, logd, syrk, G, M, v, z, dinfo, dtab;
+  size_t Ap, Bp, zf;  // tensor-core low rank: BF16 operand parts, inducing coordinates
+  size_t total;
 };
+
+// inducing-point dimension padded for the tensor-core GEMM (N tiles of 256)
+inline int64_t vif_kp(int64_t k) { return (k + 255) / 256 * 256; }
+constexpr int kVifMaxParts = 3;  // BF16 parts per operand value
 
 inline size_t align256(size_t v);
 
@@ -52,6 +58,10 @@ inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
   L.z = take(sizeof(double) * (kk + 2));
   L.dinfo = take(sizeof(int64_t) * 4);
   L.dtab = take(sizeof(float) * 2 * kk * (size_t)kVifMaxDays);
+  const size_t kp = (size_t)vif_kp((int64_t)kk);
+  L.Ap = take(2 * (size_t)kVifMaxParts * nn * kp);
+  L.Bp = take(2 * (size_t)kVifMaxParts * kp * kp);
+  L.zf = take(16 * kk);
   L.total = off;
   return L;
 }

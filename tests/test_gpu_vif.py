@@ -70,3 +70,45 @@ def test_vif_m0_is_fitc(env):
     xy_d, t_d, y_d, xyk_d, tk_d, nn_d, cnt_d = dev(torch, xy, t, y, xyk, tk, nn, cnt)
     v = vst.vecchia_nll(xy_d, t_d, th, 0, nn_d, cnt_d, y_d, precision=vst.FP64, inducing=(xyk_d, tk_d))
     assert abs(v.item() - v_o) / n <= 1e-10
+
+
+@pytest.mark.parametrize("n_st,n_days,k", [(40, 8, 24), (60, 5, 257), (30, 12, 300)])
+def test_lowrank_u_parity(env, n_st, n_days, k):
+    """U = Sigma_nk L^{-T} and r = sigma1^2 - ||U_i||^2 against the oracle:
+    the FP64 GEMM, and the tensor-core GEMM with six and with three
+    split-BF16 products.  Cases span several 128-row tiles with a ragged tail,
+    k padded to the 256-wide tiles, and k % 4 != 0 (scalar stores).
+    Tolerances, relative to max |U| (r: to sigma1^2): FP64 1e-12; six
+    products 1e-5 (FP32 covariance entries, about 1e-7 relative, amplified by
+    the large entries of L^{-1} when k is close to n); three products 1e-4
+    (16 significand bits per operand, ~1e-5 per entry)."""
+    torch, vst = env
+    xy, t, th, xyk, tk, _ = problem(n_st, n_days, k, seed=k, order="random")
+    U_o, r_o = ovif.lowrank(xy, t, xyk, tk, th)
+    xy_d, t_d, xyk_d, tk_d = dev(torch, xy, t, xyk, tk)
+    scale = np.abs(U_o).max()
+    for prec, tol in ((vst.FP64, 1e-12), (vst.MIXED, 1e-5), (vst.MIXED_BF16X3, 1e-4)):
+        ws = vst.Workspace(t.shape[0], 0, k)
+        U, r = vst.vif_lowrank_u(xy_d, t_d, th, (xyk_d, tk_d), precision=prec, ws=ws)
+        vst.vst_workspace_status(ws)
+        assert np.abs(U.cpu().numpy() - U_o).max() <= tol * scale, prec
+        assert np.abs(r.cpu().numpy() - r_o).max() <= tol * th[0], prec
+
+
+def test_vif_nll_split_bf16_forms(env):
+    """VIF NLL with the tensor-core low rank, both split forms, against the
+    oracle's Woodbury NLL: |dNLL|/n <= 1e-6 (six products) and <= 1e-5
+    (three products)."""
+    torch, vst = env
+    k, m = 60, 10
+    xy, t, th, xyk, tk, y = problem(40, 10, k, seed=17, order="time")
+    n = t.shape[0]
+    U, r = ovif.lowrank(xy, t, xyk, tk, th)
+    nn_o, cnt_o, _, _ = ovif.knn(xy, t, th, U, r, m)
+    v_o = ovif.nll(xy, t, th, U, m, nn_o, cnt_o, y)
+    xy_d, t_d, y_d, xyk_d, tk_d, nn_d, cnt_d = dev(torch, xy, t, y, xyk, tk, nn_o, cnt_o)
+    ws = vst.Workspace(n, m, k)
+    for prec, tol in ((vst.MIXED, 1e-6), (vst.MIXED_BF16X3, 1e-5)):
+        v = vst.vecchia_nll(xy_d, t_d, th, m, nn_d, cnt_d, y_d, precision=prec, ws=ws, inducing=(xyk_d, tk_d))
+        vst.vst_workspace_status(ws)
+        assert abs(v.item() - v_o) / n <= tol, (prec, abs(v.item() - v_o) / n)
