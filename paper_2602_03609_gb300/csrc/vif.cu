@@ -17,7 +17,8 @@
 //   ugemm_kernel<T>      U = Sigma_nk L^{-T} (tiled; Sigma_nk evaluated on the fly)
 //   rdiag_kernel<T>      r_i = sigma1^2 - ||U_i||^2
 //   vif_knn_kernel       residual-correlation kNN, FP64 brute force
-//   gram_kernel<T>       per-row U_p . U_q over the local block (fed to the row kernel)
+//   gram64_kernel        FP64: per-row U_p . U_q over the local block (fed to the row kernel)
+//   gram_delta_kernel    mixed: per-row U_p . U_q, accumulated without cancellation
 //   wvec_kernel<T>       rows of [W e] and sum log D_i
 //   syrk_kernel<T>       partial [W e]^T [W e] over row chunks, then a fixed-order sum
 //   final_kernel         M = I + G, FP64 Cholesky, z = L_M^{-1} W^T e, the NLL
@@ -369,15 +370,29 @@ __global__ void __launch_bounds__(WARPS * 32) vif_knn_kernel(VifKnnArgs A) {
 }
 
 // ---------------------------------------------------------------------------
-// per-row Gram of the local block: gram[i][e] = U_{pos r} . U_{pos c}, pairs e
-// in the packed order of the row kernel (positions 0..cnt-1 neighbours,
-// PM-1 = row i, the rest unused)
-template <typename T, int PM>
-__global__ void __launch_bounds__(128) gram_kernel(const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k,
-                                                   const T* U, T* gram) {
+// Local blocks of the row kernel: positions 0..cnt-1 are the neighbours of
+// row i, position PM-1 is row i itself, the rest unused (index -1).
+template <int PM>
+__device__ __forceinline__ void block_indices(const int32_t* nn, const int32_t* nn_cnt, int64_t i, int m,
+                                              int (&idx)[PM]) {
+  const int cnt = min(max(nn_cnt[i], 0), min(m, PM - 1));
+#pragma unroll
+  for (int p = 0; p < PM; ++p) {
+    int v = -1;
+    if (p < cnt) v = nn[i * m + p];
+    if (p == PM - 1) v = (int)i;
+    idx[p] = (v >= 0 && v <= i) ? v : -1;
+  }
+}
+
+// FP64 form: gram[i][e] = U_{pos r} . U_{pos c} over the pairs e of the local
+// block in the packed order of the row kernel.  One warp per row.
+template <int PM>
+__global__ void __launch_bounds__(128) gram64_kernel(const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m,
+                                                     int k, const double* U, double* gram) {
   constexpr int NPAIR = PM * (PM + 1) / 2;
   constexpr int NPL = (NPAIR + 31) / 32;  // pairs per lane
-  __shared__ T Us[4][PM][33];
+  __shared__ double Us[4][PM][33];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t warp = (int64_t)blockIdx.x * 4 + wib;
   const int64_t total = (int64_t)gridDim.x * 4;
@@ -391,56 +406,214 @@ __global__ void __launch_bounds__(128) gram_kernel(const int32_t* nn, const int3
     pc[q] = c;
   }
   for (int64_t i = warp; i < n; i += total) {
-    const int cnt = min(max(nn_cnt[i], 0), min(m, PM - 1));
     int idx[PM];
+    block_indices<PM>(nn, nn_cnt, i, m, idx);
+    double acc[NPL];
 #pragma unroll
-    for (int p = 0; p < PM; ++p) {
-      int v = -1;
-      if (p < cnt) v = nn[i * m + p];
-      if (p == PM - 1) v = (int)i;
-      idx[p] = (v >= 0 && v <= i) ? v : -1;
-    }
-    // FP64: plain accumulation.  FP32: every product split exactly
-    // (FMA TwoProduct) and summed in double-float, then rounded once; plain
-    // FP32 accumulation over k terms leaves errors that are correlated
-    // across the nearly collinear rows of a neighbourhood and bias the NLL.
-    constexpr bool F = std::is_same<T, float>::value;
-    T acc[NPL];
-    df accd[F ? NPL : 1];
-#pragma unroll
-    for (int q = 0; q < NPL; ++q) acc[q] = T(0);
-#pragma unroll
-    for (int q = 0; q < (F ? NPL : 1); ++q) accd[q] = df{0.f, 0.f};
+    for (int q = 0; q < NPL; ++q) acc[q] = 0.0;
     for (int c0 = 0; c0 < k; c0 += 32) {
       const int c = c0 + lane;
 #pragma unroll
-      for (int p = 0; p < PM; ++p) Us[wib][p][lane] = (idx[p] >= 0 && c < k) ? U[(int64_t)idx[p] * k + c] : T(0);
+      for (int p = 0; p < PM; ++p) Us[wib][p][lane] = (idx[p] >= 0 && c < k) ? U[(int64_t)idx[p] * k + c] : 0.0;
       __syncwarp();
 #pragma unroll
       for (int q = 0; q < NPL; ++q) {
-        const T* a = Us[wib][pr[q]];
-        const T* b = Us[wib][pc[q]];
-        if constexpr (F) {
-          df sd = accd[q];
+        const double* a = Us[wib][pr[q]];
+        const double* b = Us[wib][pc[q]];
+        double s = 0.0;
 #pragma unroll 8
-          for (int u = 0; u < 32; ++u) df_fma_acc(sd, a[u], df{b[u], 0.f});
-          accd[q] = sd;
-        } else {
-          T s = T(0);
-#pragma unroll 8
-          for (int u = 0; u < 32; ++u) s = fma(a[u], b[u], s);
-          acc[q] += s;
-        }
+        for (int u = 0; u < 32; ++u) s = fma(a[u], b[u], s);
+        acc[q] += s;
       }
       __syncwarp();
     }
 #pragma unroll
     for (int q = 0; q < NPL; ++q) {
       const int e = lane + 32 * q;
-      if constexpr (F) acc[q] = accd[q].hi + accd[q].lo;
       if (e < NPAIR) gram[i * NPAIR + e] = acc[q];
     }
   }
+}
+
+// Mixed form: gram[i][e] = U_p . U_q for the pairs e of the local block,
+// accumulated without cancellation and rounded once to FP32.  With the row's
+// own vector as the reference, V_p = U_p - U_i and w_p = U_i . V_p:
+//   U_p . U_q = |U_i|^2 + w_p + w_q + V_p . V_q,   |U_i|^2 = sigma1^2 - r_i,
+// (U_p . U_i = |U_i|^2 + w_p) where the sums over k are of terms that are
+// small next to |U_i|^2 for the neighbours.  (Handing the row kernel
+// U_p . U_q - sigma1^2 instead, a value with a finer FP32 rounding, measured a
+// ~10x larger mixed-vs-FP64 NLL difference on the VIF benchmark rows, with D_i
+// biased upward; the row kernel therefore forms C - G as before.)  The Gram of the vectors {V_0, .., V_{PM-2}, U_i} is a small SYRK:
+// one warp per RW = 2 rows, the lower triangle in 4 x 4 tiles (NT per row),
+// lane jobs (row slot, tile) in rounds where the 32 lanes of a round share the
+// row slot, so that the 16-byte shared loads of a tile's four positions are
+// broadcasts.  Columns are staged 32 at a time: lane p loads U_p, the shuffled
+// U_i gives V_p, and the chunk is stored position-contiguous.  Each chunk's
+// 32 products are summed in FP32 (exact products in the FMA, a short chain)
+// and added to double-float running sums; a single FP32 sum over all k
+// columns (k ~ 1e3) loses enough to bias the NLL by ~1e-6 per point, since
+// the V_p are not small when k is large.
+template <int PM>
+struct GramTiles {
+  static constexpr int B = PM / 4;              // 4-position blocks
+  static constexpr int NT = B * (B + 1) / 2;    // lower-triangle tiles per row
+  static constexpr int RW = 2;                  // rows per warp
+  static constexpr int FULL = NT / 32;          // rounds with one row slot per round
+  static constexpr int LEFT = NT - FULL * 32;   // tiles per row left over
+  static constexpr int ROUNDS = FULL * RW + (LEFT * RW + 31) / 32;
+  static constexpr int SLOT = 32 * PM + 4;      // floats per row slot (+1 chunk against bank conflicts)
+};
+
+template <int PM>
+__global__ void __launch_bounds__(128) gram_delta_kernel(const int32_t* nn, const int32_t* nn_cnt, int64_t n,
+                                                         int m, int k, const float* U, const double* r, double s1,
+                                                         float* gram) {
+  using GT = GramTiles<PM>;
+  constexpr int NPAIR = PM * (PM + 1) / 2;
+  constexpr int L = PM - 1;
+  extern __shared__ __align__(16) float gsm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float* Vs = gsm + (size_t)wib * GT::RW * GT::SLOT;
+  const int64_t warp = (int64_t)blockIdx.x * (blockDim.x >> 5) + wib;
+  const int64_t nwarps = (int64_t)gridDim.x * (blockDim.x >> 5);
+  // this lane's jobs: row slot, and the tile's first rows (4 R) and columns (4 C)
+  int jrs[GT::ROUNDS], jr[GT::ROUNDS], jc[GT::ROUNDS];
+  bool jon[GT::ROUNDS];
+#pragma unroll
+  for (int q = 0; q < GT::ROUNDS; ++q) {
+    int rs = 0, t = 0;
+    bool on = true;
+    if (q < GT::FULL * GT::RW) {
+      rs = q / GT::FULL;
+      t = (q % GT::FULL) * 32 + lane;
+    } else {
+      const int j = (q - GT::FULL * GT::RW) * 32 + lane;
+      on = j < GT::LEFT * GT::RW;
+      rs = on ? j / GT::LEFT : 0;
+      t = on ? GT::FULL * 32 + j % GT::LEFT : 0;
+    }
+    int R = 0;
+    while ((R + 1) * (R + 2) / 2 <= t) ++R;
+    jrs[q] = rs;
+    jr[q] = 4 * R;
+    jc[q] = 4 * (t - R * (R + 1) / 2);
+    jon[q] = on;
+  }
+  const bool vec = (k & 3) == 0;
+  for (int64_t i0 = warp * GT::RW; i0 < n; i0 += nwarps * GT::RW) {
+    int idx[GT::RW];  // this lane's position in each row slot (-1: unused)
+#pragma unroll
+    for (int rs = 0; rs < GT::RW; ++rs) {
+      const int64_t i = i0 + rs;
+      int v = -1;
+      if (i < n && lane < PM) {
+        const int cnt = min(max(nn_cnt[i], 0), min(m, L));
+        if (lane < cnt) v = nn[i * m + lane];
+        if (lane == L) v = (int)i;
+        if (v < 0 || v > i) v = -1;
+      }
+      idx[rs] = v;
+    }
+    float acc[GT::ROUNDS][16], accl[GT::ROUNDS][16];  // double-float running sums
+#pragma unroll
+    for (int q = 0; q < GT::ROUNDS; ++q)
+#pragma unroll
+      for (int z = 0; z < 16; ++z) acc[q][z] = accl[q][z] = 0.f;
+    for (int c0 = 0; c0 < k; c0 += 32) {
+      __syncwarp();
+#pragma unroll
+      for (int rs = 0; rs < GT::RW; ++rs) {
+        float u[32];
+        const int64_t row = idx[rs];
+        if (row >= 0 && vec && c0 + 32 <= k) {
+          const float4* src = reinterpret_cast<const float4*>(U + row * k + c0);
+#pragma unroll
+          for (int z = 0; z < 8; ++z) {
+            const float4 f = __ldg(src + z);
+            u[4 * z] = f.x; u[4 * z + 1] = f.y; u[4 * z + 2] = f.z; u[4 * z + 3] = f.w;
+          }
+        } else {
+#pragma unroll
+          for (int z = 0; z < 32; ++z) u[z] = (row >= 0 && c0 + z < k) ? __ldg(U + row * k + c0 + z) : 0.f;
+        }
+        float* dst = Vs + rs * GT::SLOT;
+#pragma unroll
+        for (int z = 0; z < 32; ++z) {
+          const float ui = __shfl_sync(0xffffffffu, u[z], L);
+          // V_p = U_p - U_i for the neighbours, U_i itself at position L
+          const float v = lane == L ? ui : (idx[rs] >= 0 ? u[z] - ui : 0.f);
+          if (lane < PM) dst[z * PM + lane] = v;
+        }
+      }
+      __syncwarp();
+      // each chunk's 32 products summed apart, then added to the running sums
+      // (shorter FP32 accumulation chains than one sum over all k columns)
+#pragma unroll
+      for (int q = 0; q < GT::ROUNDS; ++q) {
+        if (!jon[q]) continue;
+        float part[16];
+#pragma unroll
+        for (int z = 0; z < 16; ++z) part[z] = 0.f;
+        const float* col = Vs + jrs[q] * GT::SLOT;
+#pragma unroll 4
+        for (int z = 0; z < 32; ++z) {
+          const float4 a = *reinterpret_cast<const float4*>(col + z * PM + jr[q]);
+          const float4 b = *reinterpret_cast<const float4*>(col + z * PM + jc[q]);
+          const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+          for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int y = 0; y < 4; ++y) part[4 * x + y] = fmaf(av[x], bv[y], part[4 * x + y]);
+        }
+#pragma unroll
+        for (int z = 0; z < 16; ++z) {
+          const df t = df_two_sum(acc[q][z], part[z]);
+          acc[q][z] = t.hi;
+          accl[q][z] += t.lo;
+        }
+      }
+    }
+    // S (lower triangle, PM x PM per row slot) to shared memory, then E
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < GT::ROUNDS; ++q) {
+      if (!jon[q]) continue;
+      float* S = Vs + jrs[q] * GT::SLOT;
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) S[(jr[q] + x) * PM + jc[q] + y] = acc[q][4 * x + y] + accl[q][4 * x + y];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int rs = 0; rs < GT::RW; ++rs) {
+      const int64_t i = i0 + rs;
+      if (i >= n) break;
+      const float* S = Vs + rs * GT::SLOT;
+      const df s1m = df_split(s1 - r[i]);  // |U_i|^2 = sigma1^2 - r_i
+      for (int e = lane; e < NPAIR; e += 32) {
+        int a, b;
+        pair_of<PM>(e, a, b);  // a >= b
+        // w_a + w_b + S_ab - r_i in double-float, rounded once
+        df v = {0.f, 0.f};
+        if (a != L) {
+          v = df_two_sum(S[L * PM + a], S[L * PM + b]);
+          const df t = df_two_sum(v.hi, S[a * PM + b]);
+          v = df{t.hi, v.lo + t.lo};
+        } else if (b != L) {
+          v = df{S[L * PM + b], 0.f};
+        }
+        // G = sigma1^2 - r_i + (w_a + w_b + S_ab), rounded once
+        const df t = df_two_sum(v.hi, s1m.hi);
+        gram[i * NPAIR + e] = t.hi + (t.lo + (v.lo + s1m.lo));
+      }
+    }
+  }
+}
+
+template <int PM>
+constexpr size_t gram_delta_smem(int warps) {
+  return sizeof(float) * (size_t)GramTiles<PM>::RW * GramTiles<PM>::SLOT * warps;
 }
 
 // rows of [W e]: W_i = (U_i - sum_q A_iq U_{nn(i,q)}) / sqrt(D_i), e_i likewise
@@ -713,13 +886,31 @@ vst_status vif_knn(const vst_points* pts, const vst_theta* theta, int m, const v
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "VIF knn kernel");
 }
 
-template <typename T>
-static void launch_gram(int pm, const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, const T* U, T* gram,
-                        cudaStream_t st) {
+// FP64: gram = U_p . U_q;  mixed: gram = U_p . U_q - sigma1^2 (see gram_delta_kernel)
+static void launch_gram(int pm, const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, const double* U,
+                        const double* r, double s1, double* gram, cudaStream_t st) {
+  (void)r;
+  (void)s1;
   const int blocks = (int)std::min<int64_t>((n + 3) / 4, 152 * 16);
-  if (pm <= 8) gram_kernel<T, 8><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
-  else if (pm <= 16) gram_kernel<T, 16><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
-  else gram_kernel<T, 32><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
+  if (pm <= 8) gram64_kernel<8><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
+  else if (pm <= 16) gram64_kernel<16><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
+  else gram64_kernel<32><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
+}
+static void launch_gram(int pm, const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, const float* U,
+                        const double* r, double s1, float* gram, cudaStream_t st) {
+  auto go = [&](auto kern, size_t smem) {
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 128, smem);
+    const int64_t need = (n + 4 * 2 - 1) / (4 * 2);
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::max(per, 1) * sms));
+    kern<<<blocks, 128, smem, st>>>(nn, nn_cnt, n, m, k, U, r, s1, gram);
+  };
+  if (pm <= 8) go(gram_delta_kernel<8>, gram_delta_smem<8>(4));
+  else if (pm <= 16) go(gram_delta_kernel<16>, gram_delta_smem<16>(4));
+  else go(gram_delta_kernel<32>, gram_delta_smem<32>(4));
 }
 
 // factor of the residual (A, D) with the fused row kernel fed the Gram
@@ -736,7 +927,8 @@ static vst_status vif_factor_T(const vst_points* pts, const vst_theta* theta, in
   T* gram = reinterpret_cast<T*>(vbase + V.gram);
   if (n > 0) {
     ProfileScope ps(kProfVifGram, st);
-    launch_gram<T>(m + 1, nn, nn_cnt, n, m, k, U, gram, st);
+    launch_gram(m + 1, nn, nn_cnt, n, m, k, U, reinterpret_cast<const double*>(vbase + V.r), theta->sigma1sq, gram,
+                st);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "gram kernel");

@@ -19,7 +19,11 @@
 // GEMM kernel: one CTA of 4 warps per 128 x BN output tile.  Warp 0 lane 0
 // issues the TMA loads of 64-wide K blocks (128-byte swizzle) into a ring of
 // STAGES shared-memory stages; warp 1 lane 0 issues tcgen05.mma (M = 128,
-// N = BN, K = 16 per instruction) into a TMEM accumulator of BN columns and
+// N = BN, K = 16 per instruction) into two TMEM accumulators of BN columns,
+// one for the leading product a0 b0 and one for the smaller correction
+// products (the tensor core's FP32 accumulation is not round-to-nearest, and
+// a separate accumulator keeps the corrections from adding rounding steps to
+// the large sum; the two are added once in the epilogue), and
 // frees each stage with tcgen05.commit (the other lanes of both warps follow
 // their lane 0 through the waits); then all four warps read the
 // accumulator (warp w owns TMEM lanes 32w..32w+31 = tile rows) and store U.
@@ -193,7 +197,7 @@ __global__ void __launch_bounds__(128, 1)
     umma::fence_mbar_init();
   }
   if (warp == 0) {
-    umma::tmem_alloc(umma::smem_u32(tslot), BN);
+    umma::tmem_alloc(umma::smem_u32(tslot), 2 * BN);
     umma::tmem_relinquish();
   }
   umma::fence_before_sync();
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(128, 1)
   } else if (warp == 1) {
     // MMA issuer (lane 0 issues)
     constexpr uint32_t idesc = umma::idesc_bf16_f32(S::BM, BN);
-    uint32_t acc = 0;
+    uint32_t acc_main = 0, acc_corr = 0;
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % STAGES;
       const uint32_t use = (uint32_t)(kb / STAGES);
@@ -248,8 +252,13 @@ __global__ void __launch_bounds__(128, 1)
           for (int q = 0; q < SplitTerms<P>::N; ++q) {
             const uint64_t ad = umma::desc_kmajor_sw128(sa + SplitTerms<P>::a(q) * S::A_BYTES + kk * 32);
             const uint64_t bd = umma::desc_kmajor_sw128(sb + SplitTerms<P>::b(q) * S::B_BYTES + kk * 32);
-            umma::mma_bf16(tmem, ad, bd, idesc, acc);
-            acc = 1;
+            if (q == 0) {
+              umma::mma_bf16(tmem, ad, bd, idesc, acc_main);
+              acc_main = 1;
+            } else {
+              umma::mma_bf16(tmem + BN, ad, bd, idesc, acc_corr);
+              acc_corr = 1;
+            }
           }
         }
         umma::mma_commit(&empty[s]);
@@ -267,9 +276,13 @@ __global__ void __launch_bounds__(128, 1)
   const bool vec = (k & 3) == 0;
 #pragma unroll 1
   for (int cb = 0; cb < BN; cb += 32) {
-    uint32_t v[32];
-    umma::tmem_ld_32x32b_x32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb, v);
+    uint32_t v[32], w[32];
+    const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)cb;
+    umma::tmem_ld_32x32b_x32(ta, v);
+    umma::tmem_ld_32x32b_x32(ta + BN, w);
     umma::tmem_wait_ld();
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
     const int cc = c0 + cb;
     if (i < n && cc < k) {
       float* dst = U + i * k + cc;
@@ -288,7 +301,7 @@ __global__ void __launch_bounds__(128, 1)
   if (!ok) report_error(hdr, VST_ETIMEOUT, (int64_t)blockIdx.x);
   umma::fence_before_sync();
   __syncthreads();
-  if (warp == 0) umma::tmem_dealloc(tmem, BN);
+  if (warp == 0) umma::tmem_dealloc(tmem, 2 * BN);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
