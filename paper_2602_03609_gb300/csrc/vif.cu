@@ -12,7 +12,9 @@
 //
 // Kernels (T = double for the FP64 form, float for the mixed form):
 //   kk_kernel            Sigma_kk in FP64
-//   chol_panel/syrk_trail blocked FP64 Cholesky (in place, lower)
+//   chol_diag/trsm/trail blocked FP64 Cholesky (in place, lower): 32 x 32 diagonal
+//                        block in one warp, panel rows by forward substitution,
+//                        tiled trailing update
 //   trinv_kernel         L^{-1}, FP64, one warp per column
 //   ugemm_kernel<T>      U = Sigma_nk L^{-T} (tiled; Sigma_nk evaluated on the fly)
 //   rdiag_kernel<T>      r_i = sigma1^2 - ||U_i||^2
@@ -107,31 +109,55 @@ __global__ void kk_kernel(const double* xyk, const double* tk, int k, DevTheta t
 // blocked Cholesky, FP64, lower, in place (A row-major k x k)
 constexpr int kPanel = 32;
 
-__global__ void chol_panel_kernel(double* A, int k, int j0, int jb, WsHeader* hdr, int err_code) {
-  __shared__ double inv;
-  for (int c = j0; c < j0 + jb; ++c) {
-    if (threadIdx.x == 0) {
-      double d = A[(int64_t)c * k + c];
-      if (!(d > 0.0)) {
-        report_error(hdr, err_code, c);
-        d = 1.0;
-      }
-      d = sqrt(d);
-      A[(int64_t)c * k + c] = d;
-      inv = 1.0 / d;
+// diagonal block of the panel, jb x jb (jb <= 32), factored in shared memory
+// by one warp: lane r holds row r; a non-positive pivot is reported and
+// replaced by 1 so that the factorisation finishes
+__global__ void chol_diag_kernel(double* A, int k, int j0, int jb, WsHeader* hdr, int err_code) {
+  __shared__ double a[32][33];
+  const int lane = threadIdx.x;
+  for (int q = 0; q < jb; ++q) a[lane][q] = (lane < jb) ? A[(int64_t)(j0 + lane) * k + j0 + q] : 0.0;
+  __syncwarp();
+  for (int c = 0; c < jb; ++c) {
+    double d = a[c][c];
+    if (!(d > 0.0)) {
+      if (lane == 0) report_error(hdr, err_code, j0 + c);
+      d = 1.0;
     }
-    __syncthreads();
-    for (int r = c + 1 + threadIdx.x; r < k; r += blockDim.x) A[(int64_t)r * k + c] *= inv;
-    __syncthreads();
-    const int w = j0 + jb - (c + 1);  // remaining panel columns
-    if (w > 0) {
-      const int64_t cnt = (int64_t)(k - c - 1) * w;
-      for (int64_t q = threadIdx.x; q < cnt; q += blockDim.x) {
-        const int r = c + 1 + (int)(q / w), c2 = c + 1 + (int)(q % w);
-        if (c2 <= r) A[(int64_t)r * k + c2] -= A[(int64_t)r * k + c] * A[(int64_t)c2 * k + c];
-      }
+    d = sqrt(d);
+    __syncwarp();
+    if (lane == c) a[c][c] = d;
+    if (lane > c && lane < jb) a[lane][c] /= d;
+    __syncwarp();
+    if (lane > c && lane < jb)
+      for (int c2 = c + 1; c2 <= lane; ++c2) a[lane][c2] -= a[lane][c] * a[c2][c];
+    __syncwarp();
+  }
+  if (lane < jb)
+    for (int q = 0; q <= lane; ++q) A[(int64_t)(j0 + lane) * k + j0 + q] = a[lane][q];
+}
+
+// panel rows below the diagonal block: L21 = A21 L11^{-T}, one thread per row
+// (forward substitution with the factored block in shared memory)
+__global__ void chol_trsm_kernel(double* A, int k, int j0, int jb) {
+  __shared__ double l[32][33];
+  for (int q = threadIdx.x; q < jb * jb; q += blockDim.x) {
+    const int r = q / jb, c = q % jb;
+    l[r][c] = (c <= r) ? A[(int64_t)(j0 + r) * k + j0 + c] : 0.0;
+  }
+  __syncthreads();
+  const int r = j0 + jb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k) return;
+  double x[32];
+  double* row = A + (int64_t)r * k + j0;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    if (c < jb) {
+      double v = row[c];
+#pragma unroll
+      for (int p = 0; p < c; ++p) v -= x[p] * l[c][p];
+      x[c] = v / l[c][c];
+      row[c] = x[c];
     }
-    __syncthreads();
   }
 }
 
@@ -161,9 +187,10 @@ __global__ void chol_trail_kernel(double* A, int k, int j0, int jb) {
 vst_status chol64(double* A, int k, WsHeader* hdr, int err_code, cudaStream_t st) {
   for (int j0 = 0; j0 < k; j0 += kPanel) {
     const int jb = std::min(kPanel, k - j0);
-    chol_panel_kernel<<<1, 256, 0, st>>>(A, k, j0, jb, hdr, err_code);
+    chol_diag_kernel<<<1, 32, 0, st>>>(A, k, j0, jb, hdr, err_code);
     const int rest = k - (j0 + jb);
     if (rest > 0) {
+      chol_trsm_kernel<<<(rest + 127) / 128, 128, 0, st>>>(A, k, j0, jb);
       const int nb = (rest + 31) / 32;
       chol_trail_kernel<<<dim3(nb, nb), 256, 0, st>>>(A, k, j0, jb);
     }

@@ -183,8 +183,11 @@ __global__ void __launch_bounds__(128, 1)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(accf + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t m0 = (int64_t)blockIdx.x * S::BM;
-  const int c0 = blockIdx.y * BN;
+  // consecutive CTAs share the A tile (N tile fastest), so that its reads
+  // across the kp / BN column tiles come from L2
+  const int ntile = kp / BN;
+  const int64_t m0 = (int64_t)(blockIdx.x / ntile) * S::BM;
+  const int c0 = (int)(blockIdx.x % ntile) * BN;
   const int kend = kp < c0 + BN ? kp : c0 + BN;  // B[c][p] = 0 for p > c
   const int nkb = (kend + S::BK - 1) / S::BK;
 
@@ -298,7 +301,7 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
   }
-  if (!ok) report_error(hdr, VST_ETIMEOUT, (int64_t)blockIdx.x);
+  if (!ok) report_error(hdr, VST_ETIMEOUT, m0);
   umma::fence_before_sync();
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tmem, 2 * BN);
@@ -342,7 +345,9 @@ cudaError_t launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t 
   auto kern = ugemm_tc_kernel<P, BN, STAGES>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
   if (e != cudaSuccess) return e;
-  const dim3 grid((unsigned)((n + S::BM - 1) / S::BM), (unsigned)(kp / BN));
+  const int64_t tiles = (n + S::BM - 1) / S::BM * (kp / BN);
+  if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
+  const dim3 grid((unsigned)tiles);
   ProfileScope ps(kProfVifGemm, st);
   kern<<<grid, 128, S::SMEM, st>>>(ta, tb, n, k, kp, U, hdr);
   return cudaGetLastError();
