@@ -51,18 +51,59 @@ __device__ __forceinline__ double cov64(const DevTheta& th, double dx, double dy
   return f.P * matern_M<NU, double>(x, exp(-x));
 }
 
+// 16-byte read-only vector load of VEC consecutive values
+template <typename T, int VEC>
+__device__ __forceinline__ void ldg_vec(T (&v)[VEC], const T* p) {
+  if constexpr (sizeof(T) == 4) {
+    const float4 f = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+  } else {
+    const double2 d = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = d.x; v[1] = d.y;
+  }
+}
+
 // integer-day range of the data times: info[0] = min day, info[1] = number of
-// days, info[2] = 1 if every time is an integer and the span is tabulable
-__global__ void day_range_kernel(const double* t, int64_t n, int64_t* info) {
+// days, info[2] = 1 if every time is an integer and the span is tabulable.
+// Two stages: per-block (min, max, all-integer) partials, then one block.
+__global__ void day_partial_kernel(const double* t, int64_t n, double* part) {
   __shared__ double smin[256], smax[256];
   __shared__ int sint[256];
   double lo = DBL_MAX, hi = -DBL_MAX;
   int allint = 1;
-  for (int64_t i = threadIdx.x; i < n; i += 256) {
+  for (int64_t i = blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) {
     const double v = t[i];
     lo = fmin(lo, v);
     hi = fmax(hi, v);
     allint &= (v == floor(v)) && fabs(v) < 1.0e9;
+  }
+  smin[threadIdx.x] = lo;
+  smax[threadIdx.x] = hi;
+  sint[threadIdx.x] = allint;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + w]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + w]);
+      sint[threadIdx.x] &= sint[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    part[3 * blockIdx.x] = smin[0];
+    part[3 * blockIdx.x + 1] = smax[0];
+    part[3 * blockIdx.x + 2] = sint[0];
+  }
+}
+__global__ void day_range_kernel(const double* part, int nparts, int64_t n, int64_t* info) {
+  __shared__ double smin[256], smax[256];
+  __shared__ int sint[256];
+  double lo = DBL_MAX, hi = -DBL_MAX;
+  int allint = 1;
+  for (int b = threadIdx.x; b < nparts; b += 256) {
+    lo = fmin(lo, part[3 * b]);
+    hi = fmax(hi, part[3 * b + 1]);
+    allint &= part[3 * b + 2] != 0.0;
   }
   smin[threadIdx.x] = lo;
   smax[threadIdx.x] = hi;
@@ -645,42 +686,68 @@ constexpr size_t gram_delta_smem(int warps) {
 
 // rows of [W e]: W_i = (U_i - sum_q A_iq U_{nn(i,q)}) / sqrt(D_i), e_i likewise
 // with y; writes WE[i][0..k) = W_i and WE[i][k] = e_i; per-warp partial sums
-// of log D_i into part[warp]
+// of log D_i into part[warp].  One warp per row: the neighbours' indices and
+// coefficients staged once in shared memory, U rows read 16 bytes per lane.
 template <typename T>
-__global__ void wvec_kernel(const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, const T* U,
-                            const double* y, const double* A, const double* D, T* WE, double* part) {
-  const int lane = threadIdx.x & 31;
+__global__ void __launch_bounds__(256) wvec_kernel(const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m,
+                                                   int k, const T* U, const double* y, const double* A,
+                                                   const double* D, T* WE, double* part) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  __shared__ int sj[8][32];
+  __shared__ T sa[8][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool vec = (k % VEC) == 0;
   double slog = 0.0;
   for (int64_t i = warp; i < n; i += nw) {
-    const int cnt = min(max(nn_cnt[i], 0), m);
+    const int cnt0 = min(max(nn_cnt[i], 0), min(m, 32));
     const double Di = D[i];
     const double s = 1.0 / sqrt(Di);
     int myj = -1;
     double mya = 0.0;
-    if (lane < cnt) {
+    if (lane < cnt0) {
       myj = nn[i * m + lane];
       mya = A[i * m + lane];
       if (myj < 0 || myj >= i) { myj = -1; mya = 0.0; }
     }
-    double ey = (lane < cnt && myj >= 0) ? mya * y[myj] : 0.0;
+    double ey = (myj >= 0) ? mya * y[myj] : 0.0;
     ey = warp_sum(ey);
+    // compact the used neighbours (a skipped one has coefficient 0)
+    __syncwarp();
+    sj[wib][lane] = myj >= 0 ? myj : (int)i;
+    sa[wib][lane] = (T)mya;
+    __syncwarp();
+    const int cnt = cnt0;
     const T sT = (T)s;
-    const T myaT = (T)mya;
-    for (int c0 = 0; c0 < k + 1; c0 += 32) {
-      const int c = c0 + lane;
-      T v = T(0);
-      if (c < k) v = U[i * k + c];
-      for (int q = 0; q < cnt; ++q) {
-        const int j = __shfl_sync(kFull, myj, q);
-        const T aq = __shfl_sync(kFull, myaT, q);
-        if (c < k && j >= 0) v = fma(-aq, U[(int64_t)j * k + c], v);
+    const T* Ui = U + i * k;
+    T* Wi = WE + i * (k + 1);
+    if (vec) {
+      for (int c = lane * VEC; c < k; c += 32 * VEC) {
+        T v[VEC];
+        ldg_vec<T, VEC>(v, Ui + c);
+#pragma unroll 4
+        for (int q = 0; q < cnt; ++q) {
+          T u[VEC];
+          ldg_vec<T, VEC>(u, U + (int64_t)sj[wib][q] * k + c);
+          const T aq = sa[wib][q];
+#pragma unroll
+          for (int z = 0; z < VEC; ++z) v[z] = fma(-aq, u[z], v[z]);
+        }
+#pragma unroll
+        for (int z = 0; z < VEC; ++z) Wi[c + z] = v[z] * sT;
       }
-      if (c < k) WE[i * (k + 1) + c] = v * sT;
-      if (c == k) WE[i * (k + 1) + c] = (T)((y[i] - ey) * s);
+    } else {
+      for (int c = lane; c < k; c += 32) {
+        T v = Ui[c];
+        for (int q = 0; q < cnt; ++q) v = fma(-sa[wib][q], U[(int64_t)sj[wib][q] * k + c], v);
+        Wi[c] = v * sT;
+      }
     }
-    if (lane == 0) slog += log(Di);
+    if (lane == 0) {
+      Wi[k] = (T)((y[i] - ey) * s);
+      slog += log(Di);
+    }
   }
   slog = warp_sum(slog);
   if (lane == 0) part[warp] = slog;
@@ -848,7 +915,10 @@ static vst_status lowrank_T(const vst_points* pts, const vst_theta* theta, const
   if (n > 0) {
     int64_t* dinfo = reinterpret_cast<int64_t*>(vbase + V.dinfo);
     float2* dtab = reinterpret_cast<float2*>(vbase + V.dtab);
-    day_range_kernel<<<1, 256, 0, st>>>(pts->t, n, dinfo);
+    double* dpart = reinterpret_cast<double*>(vbase + V.dpart);
+    const int dblocks = (int)std::min<int64_t>(kVifDayBlocks, (n + 255) / 256);
+    day_partial_kernel<<<dblocks, 256, 0, st>>>(pts->t, n, dpart);
+    day_range_kernel<<<1, 256, 0, st>>>(dpart, dblocks, n, dinfo);
     day_lag_kernel<<<(int)((kVifMaxDays * (int64_t)k + 255) / 256), 256, 0, st>>>(ind->t, k, th, dinfo, dtab);
     if constexpr (std::is_same<T, double>::value) {
       const dim3 grid((k + 63) / 64, (unsigned)((n + 63) / 64));
@@ -861,7 +931,9 @@ static vst_status lowrank_T(const vst_points* pts, const vst_theta* theta, const
       s = lowrank_tc(pts, theta, ind, nu, split_terms, vbase, V, hdr, st);
       if (s != VST_OK) return s;
     }
-    rdiag_kernel<T><<<(int)std::min<int64_t>((n + 7) / 8, 65535), 256, 0, st>>>(U, n, k, theta->sigma1sq, r);
+    // (the tensor-core path forms r from its GEMM epilogue)
+    if constexpr (std::is_same<T, double>::value)
+      rdiag_kernel<T><<<(int)std::min<int64_t>((n + 7) / 8, 65535), 256, 0, st>>>(U, n, k, theta->sigma1sq, r);
   }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "VIF low-rank kernels");

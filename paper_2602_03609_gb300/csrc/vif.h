@@ -27,7 +27,8 @@ __device__ __forceinline__ float cov32(const DevTheta& th, float dx, float dy, f
 
 // U (FP32 [n][k]) of the mixed form by the split-BF16 tensor-core GEMM
 // (vif_tc.cu); split_terms = 3 or 6.  Needs X = L^{-1}, the day range and the
-// day lag table of the workspace already computed.
+// day lag table of the workspace already computed.  Also forms the residual
+// variances r_i = sigma1^2 - ||U_i||^2 (workspace r) from the GEMM epilogue.
 vst_status lowrank_tc(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu,
                       int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st);
 

@@ -171,7 +171,7 @@ struct SplitTerms<3> {
 template <int P, int BN, int STAGES>
 __global__ void __launch_bounds__(128, 1)
     ugemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
-                    int k, int kp, float* U, WsHeader* hdr) {
+                    int k, int kp, float* U, double* rpart, WsHeader* hdr) {
   using S = TcShape<P, BN, STAGES>;
   extern __shared__ unsigned char tc_smem[];
   const uint32_t raw = umma::smem_u32(tc_smem);
@@ -277,6 +277,7 @@ __global__ void __launch_bounds__(128, 1)
   umma::fence_after_sync();
   const int64_t i = m0 + warp * 32 + lane;
   const bool vec = (k & 3) == 0;
+  df sq = {0.f, 0.f};  // this row's sum of U_ic^2 over the tile, double-float
 #pragma unroll 1
   for (int cb = 0; cb < BN; cb += 32) {
     uint32_t v[32], w[32];
@@ -287,6 +288,11 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
     for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
     const int cc = c0 + cb;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const float u = __uint_as_float(v[q]);
+      if (cc + q < k) df_fma_acc(sq, u, df{u, 0.f});
+    }
     if (i < n && cc < k) {
       float* dst = U + i * k + cc;
       if (vec && cc + 32 <= k) {
@@ -301,6 +307,7 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
   }
+  if (i < n) rpart[i * ntile + c0 / BN] = df_to_double(sq);
   if (!ok) report_error(hdr, VST_ETIMEOUT, m0);
   umma::fence_before_sync();
   __syncthreads();
@@ -334,9 +341,18 @@ bool make_map(CUtensorMap* map, const void* ptr, uint64_t rows, uint64_t cols, u
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// r_i = sigma1^2 - sum_t part[i][t] over the GEMM's column tiles, in a fixed order
+__global__ void rsum_kernel(const double* part, int64_t n, int nt, double s1, double* r) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nt; ++q) s += part[i * nt + q];
+    r[i] = s1 - s;
+  }
+}
+
 template <int P, int BN, int STAGES>
 cudaError_t launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t n, int k, int kp, float* U,
-                        WsHeader* hdr, cudaStream_t st, bool* map_ok) {
+                        double* rpart, double s1, double* r, WsHeader* hdr, cudaStream_t st, bool* map_ok) {
   using S = TcShape<P, BN, STAGES>;
   CUtensorMap ta, tb;
   *map_ok = make_map(&ta, A, (uint64_t)P * n, (uint64_t)kp, S::BM) &&
@@ -348,8 +364,11 @@ cudaError_t launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t 
   const int64_t tiles = (n + S::BM - 1) / S::BM * (kp / BN);
   if (tiles > 0x7fffffff) return cudaErrorInvalidConfiguration;
   const dim3 grid((unsigned)tiles);
-  ProfileScope ps(kProfVifGemm, st);
-  kern<<<grid, 128, S::SMEM, st>>>(ta, tb, n, k, kp, U, hdr);
+  {
+    ProfileScope ps(kProfVifGemm, st);
+    kern<<<grid, 128, S::SMEM, st>>>(ta, tb, n, k, kp, U, rpart, hdr);
+  }
+  rsum_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 65535), 256, 0, st>>>(rpart, n, kp / BN, s1, r);
   return cudaGetLastError();
 }
 
@@ -366,6 +385,8 @@ vst_status lowrank_tc_P(const vst_points* pts, const vst_theta* theta, const vst
   __nv_bfloat16* Bp = reinterpret_cast<__nv_bfloat16*>(vbase + V.Bp);
   float4* zf = reinterpret_cast<float4*>(vbase + V.zf);
   float* U = reinterpret_cast<float*>(vbase + V.U);
+  double* rpart = reinterpret_cast<double*>(vbase + V.rpart);
+  double* r = reinterpret_cast<double*>(vbase + V.r);
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -382,8 +403,8 @@ vst_status lowrank_tc_P(const vst_points* pts, const vst_theta* theta, const vst
   if (e != cudaSuccess) return cuda_fail(e, "split kernels");
   bool map_ok = true;
   // two parts: 128 x 256 tiles; three parts: 128 x 128 tiles (two stages fit either way)
-  if constexpr (P == 2) e = launch_gemm<2, 256, 2>(Ap, Bp, n, k, kp, U, hdr, st, &map_ok);
-  else e = launch_gemm<3, 128, 2>(Ap, Bp, n, k, kp, U, hdr, st, &map_ok);
+  if constexpr (P == 2) e = launch_gemm<2, 256, 2>(Ap, Bp, n, k, kp, U, rpart, theta->sigma1sq, r, hdr, st, &map_ok);
+  else e = launch_gemm<3, 128, 2>(Ap, Bp, n, k, kp, U, rpart, theta->sigma1sq, r, hdr, st, &map_ok);
   if (!map_ok) return fail(VST_ECUDA, "cuTensorMapEncodeTiled unavailable or rejected the operand layout");
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core U GEMM");
   return VST_OK;

@@ -20,10 +20,13 @@ constexpr int64_t kVifMaxWarps = 1 << 16;
 constexpr int kVifSyrkChunks = 16;
 constexpr int64_t kVifMaxK = 4096;
 constexpr int64_t kVifMaxDays = 4096;  // data-day x inducing-point lag table
+constexpr int kVifDayBlocks = 256;     // day-range reduction blocks
 
 struct VifLayout {
   size_t S, X, U, r, gram, WE, logd, syrk, G, M, v, z, dinfo, dtab;
   size_t Ap, Bp, zf;  // tensor-core low rank: BF16 operand parts, inducing coordinates
+  size_t rpart;       // per (row, column tile) sums of U_ic^2 from the GEMM epilogue
+  size_t dpart;       // day-range partials
   size_t total;
 };
 
@@ -62,6 +65,8 @@ inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
   L.Ap = take(2 * (size_t)kVifMaxParts * nn * kp);
   L.Bp = take(2 * (size_t)kVifMaxParts * kp * kp);
   L.zf = take(16 * kk);
+  L.rpart = take(sizeof(double) * nn * (kp / 128));
+  L.dpart = take(sizeof(double) * 3 * kVifDayBlocks);
   L.total = off;
   return L;
 }
