@@ -51,6 +51,11 @@ def _measured_peak(key, fallback):
         return fallback
 
 
+# DRAM bytes (read + write) of one launch of the mixed row kernel on the
+# continental workload, from one ncu capture of the current kernel
+# (dram__bytes_read.sum + dram__bytes_write.sum): the inputs, read once
+ROWS_TRAFFIC_BYTES = 173265408 + 3952384
+
 # dense BF16 tensor peak (a cuBLAS GEMM timed alone on this part), for the
 # VIF low-rank GEMM
 BF16_PEAK = _measured_peak("bf16_tflops", 1900.0)
@@ -514,7 +519,7 @@ def run_ours(args):
         "config": dict(describe(w), precision="mixed (FP32 covariance + Cholesky, double-float refinement, "
                                               "FP64 accumulation)"),
         "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                     "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ROWS_TRAFFIC_BYTES,
                      "kernel": "rows_kernel<float, nu=1.5, 32, nll_grad>",
                      "flops_per_launch": F, "avg_launch_ms": rows_ms_avg,
                      "peak_note": "FP32 peak from unit counts and clocks (152 x 128 x 2 x 2.07 GHz)"},
