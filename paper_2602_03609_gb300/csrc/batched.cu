@@ -45,7 +45,7 @@ void apply_launch_shape(RowArgs& g, int batched, int precision, int nu, int pm) 
   g.row_chunk = 1;
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
-    auto it = g_tuned.find(std::make_tuple(batched, precision, nu, pm <= 8 ? 8 : pm <= 16 ? 16 : 32));
+    auto it = g_tuned.find(std::make_tuple(batched, precision, nu, padded_pm(pm)));
     if (it != g_tuned.end()) {
       g.blocks_per_sm = it->second.first;
       g.row_chunk = it->second.second;
@@ -58,7 +58,7 @@ void apply_launch_shape(RowArgs& g, int batched, int precision, int nu, int pm) 
 
 static void tuned_store(int batched, int precision, int nu, int pm, int bps, int chunk) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  g_tuned[std::make_tuple(batched, precision, nu, pm <= 8 ? 8 : pm <= 16 ? 16 : 32)] = {bps, chunk};
+  g_tuned[std::make_tuple(batched, precision, nu, padded_pm(pm))] = {bps, chunk};
 }
 
 // ---------------------------------------------------------------------------

@@ -40,6 +40,10 @@ __host__ __device__ inline void finish_dev_theta(DevTheta& d) {
   d.pf = (float)d.p;
 }
 
+// Padded size of the local (m+1) x (m+1) block: the row kernels are
+// instantiated for PM = 8, 16, 24, 32 (multiples of the 16-byte FP32 row loads)
+__host__ __device__ constexpr int padded_pm(int p) { return p <= 8 ? 8 : p <= 16 ? 16 : p <= 24 ? 24 : 32; }
+
 // Precision codes accepted by the single-dataset entry points; the plain
 // Vecchia path has one mixed form (VST_MIXED_BF16X3 only changes the VIF
 // low-rank product).

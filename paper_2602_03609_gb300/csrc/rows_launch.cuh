@@ -47,9 +47,12 @@ static cudaError_t launch_pm(int mode, const RowArgs& g, cudaStream_t st, int64_
 
 template <typename T, int NU>
 cudaError_t launch_rows_tn(int pm, int mode, const RowArgs& g, cudaStream_t st, int64_t* w) {
-  if (pm <= 8) return launch_pm<T, NU, 8>(mode, g, st, w);
-  if (pm <= 16) return launch_pm<T, NU, 16>(mode, g, st, w);
-  return launch_pm<T, NU, 32>(mode, g, st, w);
+  switch (padded_pm(pm)) {
+    case 8: return launch_pm<T, NU, 8>(mode, g, st, w);
+    case 16: return launch_pm<T, NU, 16>(mode, g, st, w);
+    case 24: return launch_pm<T, NU, 24>(mode, g, st, w);
+    default: return launch_pm<T, NU, 32>(mode, g, st, w);
+  }
 }
 
 }  // namespace vst

@@ -991,9 +991,12 @@ static void launch_gram(int pm, const int32_t* nn, const int32_t* nn_cnt, int64_
   (void)r;
   (void)s1;
   const int blocks = (int)std::min<int64_t>((n + 3) / 4, 152 * 16);
-  if (pm <= 8) gram64_kernel<8><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
-  else if (pm <= 16) gram64_kernel<16><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
-  else gram64_kernel<32><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
+  switch (padded_pm(pm)) {
+    case 8: gram64_kernel<8><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram); break;
+    case 16: gram64_kernel<16><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram); break;
+    case 24: gram64_kernel<24><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram); break;
+    default: gram64_kernel<32><<<blocks, 128, 0, st>>>(nn, nn_cnt, n, m, k, U, gram);
+  }
 }
 static void launch_gram(int pm, const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, const float* U,
                         const double* r, double s1, float* gram, cudaStream_t st) {
@@ -1007,9 +1010,12 @@ static void launch_gram(int pm, const int32_t* nn, const int32_t* nn_cnt, int64_
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::max(per, 1) * sms));
     kern<<<blocks, 128, smem, st>>>(nn, nn_cnt, n, m, k, U, r, s1, gram);
   };
-  if (pm <= 8) go(gram_delta_kernel<8>, gram_delta_smem<8>(4));
-  else if (pm <= 16) go(gram_delta_kernel<16>, gram_delta_smem<16>(4));
-  else go(gram_delta_kernel<32>, gram_delta_smem<32>(4));
+  switch (padded_pm(pm)) {
+    case 8: go(gram_delta_kernel<8>, gram_delta_smem<8>(4)); break;
+    case 16: go(gram_delta_kernel<16>, gram_delta_smem<16>(4)); break;
+    case 24: go(gram_delta_kernel<24>, gram_delta_smem<24>(4)); break;
+    default: go(gram_delta_kernel<32>, gram_delta_smem<32>(4));
+  }
 }
 
 // factor of the residual (A, D) with the fused row kernel fed the Gram

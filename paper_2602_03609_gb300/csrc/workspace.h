@@ -45,7 +45,7 @@ inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
     return at;
   };
   const size_t nn = n > 0 ? (size_t)n : 1, kk = k > 0 ? (size_t)k : 1;
-  const int pm = m + 1 <= 8 ? 8 : m + 1 <= 16 ? 16 : 32;
+  const int pm = padded_pm(m + 1);
   const size_t npair = (size_t)pm * (pm + 1) / 2;
   L.S = take(sizeof(double) * kk * kk);
   L.X = take(sizeof(double) * kk * kk);
