@@ -39,6 +39,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "dfmath.cuh"
 
 namespace vst {
 
@@ -75,6 +76,9 @@ struct RowArgs {
   // subtracted from the covariance; at most one of the two is set
   const double* gram_d;
   const float* gram_f;
+  // VIF, mixed form: per integer lag, the amplitude P and scale G of Eq. (2)
+  // as double-floats {P_hi, P_lo, G_hi, G_lo}
+  const float4* lagdf;
   // mixed form: per-point records (row0-relative like xy, t, y); required
   const PrepPt* prep;
 };
@@ -301,15 +305,25 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
         if (CAN_VIF && vif) {
           // VIF: the residual C - U U^T is a small difference, which
           // amplifies any systematic FP32 error in C (a rounded lag factor,
-          // an approximate exp): C is evaluated in FP64 and C - G rounded once
-          double P64, G64, Q64, L64;
-          lag_lookup<double>(th, lagd, lagf, (const LagD*)nullptr, allint, pr.td, pc.td, s.tt[r], s.tt[c], P64,
-                             G64, Q64, L64);
-          const double ddx = (double)pr.ox - (double)pc.ox, ddy = (double)pr.oy - (double)pc.oy;
-          const double x = G64 * sqrt(ddx * ddx + ddy * ddy);
-          const double c64 = P64 * matern_M<NU, double>(x, exp(-x));
-          const double gv = g.gram_f ? (double)g.gram_f[gi * NPAIR + e] : 0.0;
-          v = (float)(c64 - gv);
+          // an approximate exp): C is evaluated in double-float arithmetic
+          // (~48 bits, FP32 pipe) and C - G rounded once
+          df P2, G2;
+          const int lag = abs(pr.td - pc.td);
+          if (allint && lag < kLagTab && g.lagdf != nullptr) {
+            const float4 f = __ldg(g.lagdf + lag);
+            P2 = df{f.x, f.y};
+            G2 = df{f.z, f.w};
+          } else {
+            const LagD f = lag_factors(th, allint ? (double)lag : s.tt[r] - s.tt[c]);
+            P2 = df_split(f.P);
+            G2 = df_split(f.G);
+          }
+          const df dx = df_two_sum(pr.ox, -pc.ox), dy = df_two_sum(pr.oy, -pc.oy);
+          const df xx = dfm_mul(G2, dfm_sqrt(dfm_add(dfm_mul(dx, dx), dfm_mul(dy, dy))));
+          const df cc = dfm_mul(P2, dfm_matern<NU>(xx, dfm_exp_neg(xx)));
+          const float gv = g.gram_f ? g.gram_f[gi * NPAIR + e] : 0.f;
+          const df t = df_two_sum(cc.hi, -gv);
+          v = t.hi + (t.lo + cc.lo);
         } else {
           const float x = G * h;
           const float E = __expf(-x);

@@ -138,6 +138,15 @@ __global__ void day_lag_kernel(const double* tk, int k, DevTheta th, const int64
   tab[id] = make_float2((float)f.P, (float)f.G);
 }
 
+// per integer lag u < kLagTab: P and G of Eq. (2) as double-floats
+__global__ void lag_df_kernel(DevTheta th, float4* out) {
+  const int u = blockIdx.x * blockDim.x + threadIdx.x;
+  if (u >= kLagTab) return;
+  const LagD f = lag_factors(th, (double)u);
+  const float ph = (float)f.P, gh = (float)f.G;
+  out[u] = make_float4(ph, (float)(f.P - (double)ph), gh, (float)(f.G - (double)gh));
+}
+
 template <int NU>
 __global__ void kk_kernel(const double* xyk, const double* tk, int k, DevTheta th, double* S) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1042,6 +1051,8 @@ static vst_status vif_factor_T(const vst_points* pts, const vst_theta* theta, in
   uint8_t* flag = reinterpret_cast<uint8_t*>(base + L.flag);
   const DevTheta th = dev_theta_vif(theta);
   launch_lag_table(th, lagd, lagf, st);
+  float4* lagdf = reinterpret_cast<float4*>(vbase + V.lagdf);
+  lag_df_kernel<<<(kLagTab + 127) / 128, 128, 0, st>>>(th, lagdf);
   const bool mixed = precision != VST_FP64;
   PrepPt* prep = reinterpret_cast<PrepPt*>(base + L.prep);
   if (mixed) launch_prep_points(n, pts->xy, pts->t, nullptr, prep, flag, st);
@@ -1064,6 +1075,7 @@ static vst_status vif_factor_T(const vst_points* pts, const vst_theta* theta, in
   g.tau = 1.0e4f;
   g.partial = reinterpret_cast<double*>(base + L.partial);
   g.prep = prep;
+  g.lagdf = lagdf;
   if constexpr (std::is_same<T, double>::value) g.gram_d = gram;
   else g.gram_f = gram;
   apply_launch_shape(g, 0, precision, nu, m + 1);

@@ -27,6 +27,7 @@ struct VifLayout {
   size_t Ap, Bp, zf;  // tensor-core low rank: BF16 operand parts, inducing coordinates
   size_t rpart;       // per (row, column tile) sums of U_ic^2 from the GEMM epilogue
   size_t dpart;       // day-range partials
+  size_t lagdf;       // per-lag (P, G) as double-floats (mixed residual covariance)
   size_t total;
 };
 
@@ -67,6 +68,7 @@ inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
   L.zf = take(16 * kk);
   L.rpart = take(sizeof(double) * nn * (kp / 128));
   L.dpart = take(sizeof(double) * 3 * kVifDayBlocks);
+  L.lagdf = take(16 * (size_t)kLagTab);
   L.total = off;
   return L;
 }
