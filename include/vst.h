@@ -186,6 +186,27 @@ vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m
                             const double* y, int precision, double* nll, double* grad,
                             void* workspace, size_t ws_bytes, void* stream);
 
+/* Vecchia prediction at n_pred new points (the predictive distribution of
+ * Sect. 3.1 under the Vecchia approximation of Sect. 4.1 with the
+ * correlation-based neighbours of Sect. 4.4.1): every prediction point p
+ * conditions on the min(m, n_train) training points of largest correlation
+ * (all training points are candidates; ties to the smaller index), and
+ *   mean[p] = A_p y_N(p),   var[p] = Sigma~_pp - A_p Sigma~_{N(p),p}
+ * with A_p = Sigma~_{p,N(p)} Sigma~_{N(p)}^{-1}: the marginal predictive mean
+ * and variance of the response (latent = 0) or, with latent != 0, of the
+ * latent process (the nugget left out of var).  Prediction points do not
+ * condition on one another.
+ * train: n_train points (any order), y: their n_train responses; pred: n_pred
+ * points; mean, var: n_pred FP64 device outputs; nn_out (may be NULL):
+ * [n_pred][m] int32 training indices of the neighbours (-1 padded).
+ * precision: VST_FP64 or VST_MIXED (VST_MIXED_BF16X3 = VST_MIXED here).
+ * Workspace: vst_workspace_size_predict(n_train, n_pred, m) bytes.
+ * Synchronises `stream` once (bounding box of the neighbour search). */
+size_t vst_workspace_size_predict(int64_t n_train, int64_t n_pred, int m);
+vst_status vecchia_predict(const vst_points* train, const vst_theta* theta, int m, const double* y,
+                           const vst_points* pred, int precision, int latent, double* mean, double* var,
+                           int32_t* nn_out, void* workspace, size_t ws_bytes, void* stream);
+
 /* VIF low-rank part (Sect. 4.3): Sigma_kk = L L^T (FP64 Cholesky of the
  * inducing-point covariance), U = Sigma_nk L^{-T} and the residual variances
  * r_i = sigma1sq - ||U_i||^2 (latent, no nugget).

@@ -30,6 +30,7 @@ __all__ = [
     "vst_profile_read", "vecchia_nll_grad_noalloc", "vst_noalloc_status", "NOALLOC_MAX_N",
     "BatchedWorkspace", "vecchia_nll_grad_batched", "BatchedGraph", "vst_autotune_nll_grad",
     "vst_autotune_nll_grad_batched", "vst_autotune_clear", "MIXED_BF16X3", "vif_lowrank_u",
+    "vecchia_predict", "vst_workspace_size_predict", "PredictWorkspace",
 ]
 
 FP64 = 0
@@ -104,6 +105,11 @@ def lib():
         L.vecchia_nll_grad.restype = ctypes.c_int
         L.vecchia_nll_grad.argtypes = [PT, TH, ctypes.c_int, IN, _P, _P, _P, ctypes.c_int, _P, _P, _P,
                                        ctypes.c_size_t, _P]
+        L.vst_workspace_size_predict.restype = ctypes.c_size_t
+        L.vst_workspace_size_predict.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
+        L.vecchia_predict.restype = ctypes.c_int
+        L.vecchia_predict.argtypes = [PT, TH, ctypes.c_int, _P, PT, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P,
+                                      ctypes.c_size_t, _P]
         L.vif_lowrank_u.restype = ctypes.c_int
         L.vif_lowrank_u.argtypes = [PT, TH, IN, ctypes.c_int, _P, _P, _P, ctypes.c_size_t, _P]
         L.vecchia_sample.restype = ctypes.c_int
@@ -307,6 +313,46 @@ def vif_lowrank_u(xy, t, theta, inducing, precision=FP64, U=None, r=None, ws=Non
                                _ptr(U, torch.float64, "U"), _ptr(r, torch.float64, "r"), ws.ptr, ws.nbytes,
                                _stream(stream)))
     return U, r
+
+
+def vst_workspace_size_predict(n_train, n_pred, m) -> int:
+    return int(lib().vst_workspace_size_predict(int(n_train), int(n_pred), int(m)))
+
+
+class PredictWorkspace(Workspace):
+    """Workspace of vecchia_predict."""
+
+    def __init__(self, n_train, n_pred, m, device=None):
+        self.nbytes = vst_workspace_size_predict(n_train, n_pred, m)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+        self.ptr = (self.buf.data_ptr() + 255) // 256 * 256
+
+    def fits(self, n_train, n_pred, m):
+        return self.nbytes >= vst_workspace_size_predict(n_train, n_pred, m)
+
+
+def vecchia_predict(xy, t, y, theta, m, xy_pred, t_pred, precision=FP64, latent=False, mean=None, var=None,
+                    nn=None, ws=None, stream=None):
+    """Vecchia predictive mean and variance at new points (each conditioned on
+    its m most correlated training points).  Returns (mean, var), or
+    (mean, var, nn) when nn=True (the neighbour indices, [n_pred, m] int32)."""
+    n, npred = t.shape[0], t_pred.shape[0]
+    mean = mean if mean is not None else torch.empty(npred, dtype=torch.float64, device=t_pred.device)
+    var = var if var is not None else torch.empty(npred, dtype=torch.float64, device=t_pred.device)
+    want_nn = nn is True
+    if want_nn:
+        nn = torch.empty((npred, m), dtype=torch.int32, device=t_pred.device)
+    if ws is None:
+        ws = PredictWorkspace(n, npred, m, device=t_pred.device)
+    if not ws.fits(n, npred, m):
+        raise ValueError("workspace too small")
+    tr, pr = _points(xy, t), _points(xy_pred, t_pred)
+    _check(lib().vecchia_predict(ctypes.byref(tr), ctypes.byref(_th(theta)), int(m), _ptr(y, torch.float64, "y"),
+                                 ctypes.byref(pr), int(precision), 1 if latent else 0,
+                                 _ptr(mean, torch.float64, "mean"), _ptr(var, torch.float64, "var"),
+                                 _ptr(nn, torch.int32, "nn") if want_nn else None, ws.ptr, ws.nbytes,
+                                 _stream(stream)))
+    return (mean, var, nn) if want_nn else (mean, var)
 
 
 class BatchedWorkspace(Workspace):

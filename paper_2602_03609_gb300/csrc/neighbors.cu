@@ -225,6 +225,10 @@ struct KnnArgs {
   int64_t* tie_rows;
   int64_t tie_cap;
   WsHeader* hdr;
+  // candidates of query row i are the rows j < min(i, n_cand); queries are the
+  // rows row0..n-1, written to nn / nn_cnt at (i - row0)
+  int64_t n_cand;
+  int64_t row0;
 };
 
 template <int NU>
@@ -257,7 +261,8 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
 
   __shared__ int sq_all[WARPS][64];
   int* sq = sq_all[threadIdx.x >> 5];
-  for (int64_t i = warp; i < A.n; i += total) {
+  for (int64_t i = A.row0 + warp; i < A.n; i += total) {
+    const int64_t lim = i < A.n_cand ? i : A.n_cand;  // candidates j < lim
     const double xi = A.xy[2 * i], yi = A.xy[2 * i + 1], ti = A.t[i];
     const float xif = (float)(xi - g.xmin), yif = (float)(yi - g.ymin);
     const int qb = time_bin(g, ti), qcx = cell_x(g, xi), qcy = cell_y(g, yi);
@@ -327,7 +332,7 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
         lag_rho(A, ulo, Pl, Gl);
         if (Pl + (double)g.margin < thr) break;
       }
-      bool vb = bin >= 0 && bin < g.nt && A.binmin[bin] < i;
+      bool vb = bin >= 0 && bin < g.nt && A.binmin[bin] < lim;
       double ulo = 0.0, uhi = 0.0;
       if (vb) {
         if (g.int_times) {
@@ -408,11 +413,11 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
                 const int b = cbin * g.ncell + cy * g.ncx + cx;
                 s = A.offsets[b];
                 int en = A.offsets[b + 1];
-                if (en > s && A.sidx[en - 1] >= i) {  // keep the predecessors of i only
+                if (en > s && A.sidx[en - 1] >= lim) {  // keep the candidates j < lim only
                   int lo = s, hi = en;
                   while (lo < hi) {
                     const int mid = (lo + hi) >> 1;
-                    if (A.sidx[mid] < i) lo = mid + 1; else hi = mid;
+                    if (A.sidx[mid] < lim) lo = mid + 1; else hi = mid;
                   }
                   en = lo;
                 }
@@ -484,11 +489,12 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
 
     while (qn > 0) flush(qn < 32 ? qn : 32);
     // write the sorted neighbour list
-    const int want = (int)(i < (int64_t)A.m ? i : (int64_t)A.m);
+    const int want = (int)(lim < (int64_t)A.m ? lim : (int64_t)A.m);
     const int cnt = min(count, A.m);
-    if (lane < A.m) A.nn[i * A.m + lane] = lane < cnt ? lid : -1;
+    const int64_t oi = i - A.row0;
+    if (lane < A.m) A.nn[oi * A.m + lane] = lane < cnt ? lid : -1;
     if (lane == 0) {
-      A.nn_cnt[i] = cnt;
+      A.nn_cnt[oi] = cnt;
       if (cnt != want) report_error(A.hdr, VST_EINTERNAL, i);
     }
     if (count == K) {
@@ -496,7 +502,7 @@ __global__ void __launch_bounds__(WARPS * 32) knn_kernel(KnnArgs A) {
       const double rm1 = __shfl_sync(kFull, lr, A.m);
       if (lane == 0 && (rm - rm1) <= 1e-12 * fabs(rm)) {
         const unsigned long long slot = atomicAdd(&A.hdr->n_tie, 1ull);
-        if (A.tie_rows && (int64_t)slot < A.tie_cap) A.tie_rows[slot] = i;
+        if (A.tie_rows && (int64_t)slot < A.tie_cap) A.tie_rows[slot] = oi;
       }
     }
   }
@@ -519,42 +525,12 @@ static cudaError_t launch_knn(const KnnArgs& A, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-}  // namespace vst
-
-using namespace vst;
-
-extern "C" vst_status vif_build_neighbors(const vst_points* pts, const vst_theta* theta, int m,
-                                          const vst_inducing* ind, int32_t* nn, int32_t* nn_cnt,
-                                          int64_t* tie_rows, int64_t tie_cap, void* ws, size_t ws_bytes,
-                                          void* stream) {
-  if (!pts) return fail(VST_EINVAL, "pts is NULL");
-  const int64_t n = pts->n;
-  if (n < 0 || n >= (int64_t(1) << 30)) return fail(VST_EINVAL, "n out of range [0, 2^30)");
-  if (m < 0 || m > VST_MAX_M) return fail(VST_EINVAL, "m=%d out of range [0, %d]", m, VST_MAX_M);
-  vst_status s = check_theta(theta);
-  if (s != VST_OK) return s;
-  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256) return fail(VST_EINVAL, "workspace NULL or not 256-byte aligned");
-  const int64_t kind = (ind && ind->k > 0) ? ind->k : 0;
-  s = check_inducing(ind);
-  if (s != VST_OK) return s;
-  if (ws_bytes < vst_workspace_size(n, m, kind)) return fail(VST_ENOMEM, "workspace too small");
-  if (n > 0 && (!pts->xy || !pts->t || !nn_cnt || (m > 0 && !nn))) return fail(VST_EINVAL, "NULL array");
-  if (tie_cap < 0) return fail(VST_EINVAL, "tie_cap < 0");
-  cudaStream_t st = (cudaStream_t)stream;
-  const WsLayout L = ws_layout(n, m, 0);
-  char* base = static_cast<char*>(ws);
-  WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
-  launch_init_header(hdr, st);
-  if (n == 0) return VST_OK;
-  if (m == 0) {
-    cudaError_t e = cudaMemsetAsync(nn_cnt, 0, sizeof(int32_t) * n, st);
-    return e == cudaSuccess ? VST_OK : cuda_fail(e, "memset");
-  }
-  if (kind > 0) {
-    const WsLayout LV = ws_layout(n, m, kind);
-    return vif_knn(pts, theta, m, ind, nu_code(theta->nu), nn, nn_cnt, tie_rows, tie_cap, base + LV.vif,
-                   vif_layout(n, m, kind), hdr, st);
-  }
+// Bucket grid over the n points and the exact search for query rows
+// row0..n-1 among the rows j < min(i, n_cand) (n_cand = n, row0 = 0: the
+// Vecchia predecessors of every row).  Synchronises st once (bounding box).
+vst_status plain_knn(const double* xy, const double* t, int64_t n, const vst_theta* theta, int m, int32_t* nn,
+                     int32_t* nn_cnt, int64_t* tie_rows, int64_t tie_cap, char* base, const WsLayout& L,
+                     WsHeader* hdr, int64_t n_cand, int64_t row0, cudaStream_t st) {
   const DevTheta th = dev_theta(theta);
   LagD* lagd = reinterpret_cast<LagD*>(base + L.lagd);
   LagF* lagf = reinterpret_cast<LagF*>(base + L.lagf);
@@ -564,7 +540,7 @@ extern "C" vst_status vif_build_neighbors(const vst_points* pts, const vst_theta
   double* bpart = reinterpret_cast<double*>(base + L.bbox_part);
   double* bbox = reinterpret_cast<double*>(base + L.bbox);
   const int nbb = (int)std::min<int64_t>(kBBoxBlocks, (n + 255) / 256);
-  bbox_partial_kernel<<<nbb, 256, 0, st>>>(pts->xy, pts->t, n, bpart);
+  bbox_partial_kernel<<<nbb, 256, 0, st>>>(xy, t, n, bpart);
   bbox_final_kernel<<<1, 32, 0, st>>>(bpart, nbb, bbox);
   double hb[7];
   cudaError_t e = cudaMemcpyAsync(hb, bbox, sizeof(hb), cudaMemcpyDeviceToHost, st);
@@ -630,7 +606,7 @@ extern "C" vst_status vif_build_neighbors(const vst_points* pts, const vst_theta
   if (e == cudaSuccess) e = cudaMemsetAsync(binmin, 0x7f, sizeof(int32_t) * g.nt, st);
   if (e != cudaSuccess) return cuda_fail(e, "memset");
   const int gridn = (int)std::min<int64_t>((n + 255) / 256, 4096);
-  key_kernel<<<gridn, 256, 0, st>>>(pts->xy, pts->t, n, g, pb, cursor, binmin);
+  key_kernel<<<gridn, 256, 0, st>>>(xy, t, n, g, pb, cursor, binmin);
   const int nblk = (int)((nb + 1023) / 1024);
   scan_blocks_kernel<<<nblk, 1024, 0, st>>>(cursor, nb, offsets, bsums);
   scan_sums_kernel<<<1, 1024, 0, st>>>(bsums, nblk);
@@ -639,15 +615,15 @@ extern "C" vst_status vif_build_neighbors(const vst_points* pts, const vst_theta
   if (e != cudaSuccess) return cuda_fail(e, "memset");
   scatter_kernel<<<gridn, 256, 0, st>>>(n, pb, offsets, cursor, sidx);
   const int gridb = (int)std::min<int64_t>((nb + 255) / 256, 8192);
-  sort_buckets_kernel<<<gridb, 256, 0, st>>>(nb, offsets, sidx, pts->xy, g, sx, sy);
+  sort_buckets_kernel<<<gridb, 256, 0, st>>>(nb, offsets, sidx, xy, g, sx, sy);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "bucketing kernels");
 
   KnnArgs A{};
   A.inv_s1 = 1.0 / theta->sigma1sq;
   A.inv_s1f = (float)A.inv_s1;
-  A.xy = pts->xy;
-  A.t = pts->t;
+  A.xy = xy;
+  A.t = t;
   A.n = n;
   A.m = m;
   A.th = th;
@@ -664,6 +640,8 @@ extern "C" vst_status vif_build_neighbors(const vst_points* pts, const vst_theta
   A.tie_rows = tie_rows;
   A.tie_cap = tie_rows ? tie_cap : 0;
   A.hdr = hdr;
+  A.n_cand = n_cand;
+  A.row0 = row0;
   const int nu = nu_code(theta->nu);
   {
     ProfileScope ps(kProfKnn, st);
@@ -672,3 +650,43 @@ extern "C" vst_status vif_build_neighbors(const vst_points* pts, const vst_theta
   if (e != cudaSuccess) return cuda_fail(e, "knn kernel");
   return VST_OK;
 }
+
+}  // namespace vst
+
+using namespace vst;
+
+extern "C" vst_status vif_build_neighbors(const vst_points* pts, const vst_theta* theta, int m,
+                                          const vst_inducing* ind, int32_t* nn, int32_t* nn_cnt,
+                                          int64_t* tie_rows, int64_t tie_cap, void* ws, size_t ws_bytes,
+                                          void* stream) {
+  if (!pts) return fail(VST_EINVAL, "pts is NULL");
+  const int64_t n = pts->n;
+  if (n < 0 || n >= (int64_t(1) << 30)) return fail(VST_EINVAL, "n out of range [0, 2^30)");
+  if (m < 0 || m > VST_MAX_M) return fail(VST_EINVAL, "m=%d out of range [0, %d]", m, VST_MAX_M);
+  vst_status s = check_theta(theta);
+  if (s != VST_OK) return s;
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256) return fail(VST_EINVAL, "workspace NULL or not 256-byte aligned");
+  const int64_t kind = (ind && ind->k > 0) ? ind->k : 0;
+  s = check_inducing(ind);
+  if (s != VST_OK) return s;
+  if (ws_bytes < vst_workspace_size(n, m, kind)) return fail(VST_ENOMEM, "workspace too small");
+  if (n > 0 && (!pts->xy || !pts->t || !nn_cnt || (m > 0 && !nn))) return fail(VST_EINVAL, "NULL array");
+  if (tie_cap < 0) return fail(VST_EINVAL, "tie_cap < 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  const WsLayout L = ws_layout(n, m, 0);
+  char* base = static_cast<char*>(ws);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
+  launch_init_header(hdr, st);
+  if (n == 0) return VST_OK;
+  if (m == 0) {
+    cudaError_t e = cudaMemsetAsync(nn_cnt, 0, sizeof(int32_t) * n, st);
+    return e == cudaSuccess ? VST_OK : cuda_fail(e, "memset");
+  }
+  if (kind > 0) {
+    const WsLayout LV = ws_layout(n, m, kind);
+    return vif_knn(pts, theta, m, ind, nu_code(theta->nu), nn, nn_cnt, tie_rows, tie_cap, base + LV.vif,
+                   vif_layout(n, m, kind), hdr, st);
+  }
+  return plain_knn(pts->xy, pts->t, n, theta, m, nn, nn_cnt, tie_rows, tie_cap, base, L, hdr, n, 0, st);
+}
+

@@ -81,6 +81,9 @@ struct RowArgs {
   const float4* lagdf;
   // mixed form: per-point records (row0-relative like xy, t, y); required
   const PrepPt* prep;
+  // single-dataset form: rows out0..n-1 are processed and their per-row
+  // arrays (nn, nn_cnt, flag, A, D) hold row i at index i - out0 (0: all rows)
+  int64_t out0;
 };
 
 // Per-position record of the local block: offsets from row i, integer day
@@ -207,7 +210,8 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   constexpr int NPAIR = WarpSm<T, PM>::NPAIR;
   const int m = g.m;
   const int64_t gi = row0 + i;  // global row (batched form); nn indices are local
-  const int cnt = g.nn_cnt[gi];
+  const int64_t ri = gi - g.out0;  // index into the per-row arrays
+  const int cnt = g.nn_cnt[ri];
   if (cnt < 0 || cnt > m || cnt > LAST || (int64_t)cnt > i) {
     if (lane == 0) report_error(g.hdr, VST_EINVAL, gi);
     return;
@@ -215,7 +219,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   int idx = -1;
   bool bad = false;
   if (lane < cnt) {
-    idx = g.nn[gi * m + lane];
+    idx = g.nn[ri * m + lane];
     bad = (idx < 0) || ((int64_t)idx >= i);
   }
   if (__any_sync(kFull, bad)) {
@@ -405,7 +409,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     const float ratio = mx / mn;
     if (!ok || !(ratio * ratio <= g.tau)) {
       if (lane == 0) {
-        g.flag[gi] = 1;
+        g.flag[ri] = 1;
         atomicAdd(&g.hdr->n_fallback, 1ull);
       }
       return;
@@ -535,7 +539,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     rt = rs.hi + rs.lo;
     if (!(Dt > 0.0f) || !(rt == rt)) {  // lost to FP32 rounding: redo in FP64
       if (lane == 0) {
-        g.flag[gi] = 1;
+        g.flag[ri] = 1;
         atomicAdd(&g.hdr->n_fallback, 1ull);
       }
       return;
@@ -564,9 +568,9 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     if (lane < m) {
       double v = 0.0;
       if (lane < cnt) v = MIXED ? df_to_double(a_ref) : (double)aj;
-      g.A[gi * m + lane] = v;
+      g.A[ri * m + lane] = v;
     }
-    if (lane == 0) g.D[gi] = Dd;
+    if (lane == 0) g.D[ri] = Dd;
     return;
   }
 
@@ -666,10 +670,10 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) rows_kernel(RowArgs g)
     if (g.fallback_only) any = g.hdr->n_fallback != 0ull;
     if (any) {
       const int64_t chunk = g.row_chunk > 0 ? g.row_chunk : 1;
-      for (int64_t base = warp * chunk; base < n; base += total * chunk) {
+      for (int64_t base = g.out0 + warp * chunk; base < n; base += total * chunk) {
         const int64_t end = base + chunk < n ? base + chunk : n;
         for (int64_t i = base; i < end; ++i) {
-          if (g.fallback_only && g.flag[i] == 0) continue;
+          if (g.fallback_only && g.flag[i - g.out0] == 0) continue;
           row_body<T, NU, PM, MODE>(g, g.th, g.lagd, g.lagf, bsc, true, s, i, 0, lane, acc);
         }
       }
