@@ -83,8 +83,8 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true", help="skip the CPU-baseline leg")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-datasets leg")
     ap.add_argument("--no-vif", action="store_true", help="skip the VIF leg")
-    ap.add_argument("--legs", default="main,batched,vif,baseline",
-                    help="comma list of legs to run: main, batched, vif, baseline")
+    ap.add_argument("--legs", default="main,batched,predict,vif,baseline",
+                    help="comma list of legs to run: main, batched, predict, vif, baseline")
     ap.add_argument("--vif-n", type=int, default=30000, help="rows of the exact-search VIF leg")
     ap.add_argument("--vif-full", type=int, default=1, help="1: also time the full-size VIF NLL")
     return ap.parse_args()
@@ -296,6 +296,45 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
     return out
 
 
+def predict_leg(vst, torch, dev, w):
+    """Vecchia prediction (mean and variance) from the bench workload's
+    training points: (a) the next day at every station of the last day
+    (the forecasting case), (b) one million points of a regular 1000 x 1000
+    grid over the domain on the next day.  Each call includes the bucket grid
+    over all points, the exact neighbour search of the prediction points among
+    the training points, and their factor rows."""
+    th = vst.vst_theta_from_ranges(*w.theta.astuple())
+    xy, t, y = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (w.xy, w.t, w.z))
+    last = float(w.t.max())
+    st_xy = np.unique(w.xy[w.t == last], axis=0)
+    lo, hi = w.xy.min(0), w.xy.max(0)
+    gx, gy = np.meshgrid(np.linspace(lo[0], hi[0], 1000), np.linspace(lo[1], hi[1], 1000))
+    cases = {"next_day_stations": st_xy, "grid_1e6": np.stack([gx.ravel(), gy.ravel()], 1)}
+    out = {}
+    for name, pxy in cases.items():
+        xp = torch.from_numpy(np.ascontiguousarray(pxy)).to(dev)
+        tp = torch.full((pxy.shape[0],), last + 1.0, dtype=torch.float64, device=dev)
+        ws = vst.PredictWorkspace(w.n, pxy.shape[0], w.m, device=dev)
+        res = {"n_pred": int(pxy.shape[0])}
+        for pname, prec in (("mixed", vst.MIXED), ("fp64", vst.FP64)):
+            f = (lambda p=prec: vst.vecchia_predict(xy, t, y, th, w.m, xp, tp, precision=p, ws=ws))
+            f()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = 3
+            a.record()
+            for _ in range(reps):
+                f()
+            b.record()
+            torch.cuda.synchronize()
+            ms = a.elapsed_time(b) / reps
+            res[pname] = {"ms": ms, "value": pxy.shape[0] / (ms * 1e-3), "unit": "predictions/s"}
+        vst.vst_workspace_status(ws)
+        out[name] = res
+        del ws
+    return out
+
+
 def cpu_baseline(w, th, seconds_hint=True):
     """The oracle as it stands, on the host cores, on a bounded sample: NLL +
     gradient terms of the first S rows (each with m = 30 neighbours found by
@@ -398,6 +437,8 @@ def run_ours(args):
             out["vif"] = vif_leg(vst, torch, dev, w, args.vif_n, args.vif_full != 0)
         if "batched" in legs:
             out["batched"] = batched_leg(vst, torch, dev, args.steps)
+        if "predict" in legs:
+            out["predict"] = predict_leg(vst, torch, dev, w)
         if rank == 0:
             print(json.dumps(out), flush=True)
         return 0
@@ -546,6 +587,8 @@ def run_ours(args):
     }
     if not args.no_batched and "batched" in legs:
         line["batched"] = batched_leg(vst, torch, dev, args.steps)
+    if "predict" in legs:
+        line["predict"] = predict_leg(vst, torch, dev, w)
     if not args.no_vif and "vif" in legs:
         del ws
         torch.cuda.empty_cache()
