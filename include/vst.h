@@ -207,6 +207,26 @@ vst_status vecchia_predict(const vst_points* train, const vst_theta* theta, int 
                            const vst_points* pred, int precision, int latent, double* mean, double* var,
                            int32_t* nn_out, void* workspace, size_t ws_bytes, void* stream);
 
+/* Space-time separated kMeans++ inducing points (Algorithm 3, Sect. 4.4.2):
+ * m_s = round(sqrt(m n / |T|^2)) centres among the unique locations and
+ * m_t = round(sqrt(m |T|^2 / n)) among the unique times (round = floor(x +
+ * 1/2); clamped to [1, |S|], [1, |T|]), each by kMeans++ (first centre
+ * uniform, then D^2 sampling) followed by lloyd_iters Lloyd steps; the k =
+ * m_s m_t inducing points are the Cartesian product, point a m_t + b =
+ * (location centre a, time centre b).  Draws: SplitMix64 from `seed` (times)
+ * and seed ^ 0xD1B54A32D192ED03 (locations), u_j = (mix(x0 + (j+1) gamma)
+ * >> 11) 2^-53.  D^2 weights and Lloyd sums are exact 64-bit integers
+ * (2^32-scaled), so the result is deterministic and order-independent.
+ * Unique locations are sorted lexicographically, unique times ascending.
+ * xyk: [k_cap][2], tk: [k_cap] FP64 device outputs; k_out, ms_out, mt_out:
+ * host outputs (ms_out, mt_out may be NULL).  VST_EINVAL if k > k_cap.
+ * Synchronises `stream` several times.  Workspace:
+ * vst_workspace_size_kmeans(n) bytes. */
+size_t vst_workspace_size_kmeans(int64_t n);
+vst_status vst_sts_kmeanspp(const vst_points* pts, int64_t m, uint64_t seed, int lloyd_iters, double* xyk,
+                            double* tk, int64_t k_cap, int64_t* k_out, int64_t* ms_out, int64_t* mt_out,
+                            void* workspace, size_t ws_bytes, void* stream);
+
 /* VIF low-rank part (Sect. 4.3): Sigma_kk = L L^T (FP64 Cholesky of the
  * inducing-point covariance), U = Sigma_nk L^{-T} and the residual variances
  * r_i = sigma1sq - ||U_i||^2 (latent, no nugget).

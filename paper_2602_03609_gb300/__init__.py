@@ -30,7 +30,7 @@ __all__ = [
     "vst_profile_read", "vecchia_nll_grad_noalloc", "vst_noalloc_status", "NOALLOC_MAX_N",
     "BatchedWorkspace", "vecchia_nll_grad_batched", "BatchedGraph", "vst_autotune_nll_grad",
     "vst_autotune_nll_grad_batched", "vst_autotune_clear", "MIXED_BF16X3", "vif_lowrank_u",
-    "vecchia_predict", "vst_workspace_size_predict", "PredictWorkspace",
+    "vecchia_predict", "vst_workspace_size_predict", "PredictWorkspace", "sts_kmeanspp",
 ]
 
 FP64 = 0
@@ -105,6 +105,12 @@ def lib():
         L.vecchia_nll_grad.restype = ctypes.c_int
         L.vecchia_nll_grad.argtypes = [PT, TH, ctypes.c_int, IN, _P, _P, _P, ctypes.c_int, _P, _P, _P,
                                        ctypes.c_size_t, _P]
+        L.vst_workspace_size_kmeans.restype = ctypes.c_size_t
+        L.vst_workspace_size_kmeans.argtypes = [ctypes.c_int64]
+        L.vst_sts_kmeanspp.restype = ctypes.c_int
+        L.vst_sts_kmeanspp.argtypes = [PT, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int, _P, _P, ctypes.c_int64,
+                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                       ctypes.POINTER(ctypes.c_int64), _P, ctypes.c_size_t, _P]
         L.vst_workspace_size_predict.restype = ctypes.c_size_t
         L.vst_workspace_size_predict.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_int]
         L.vecchia_predict.restype = ctypes.c_int
@@ -353,6 +359,24 @@ def vecchia_predict(xy, t, y, theta, m, xy_pred, t_pred, precision=FP64, latent=
                                  _ptr(nn, torch.int32, "nn") if want_nn else None, ws.ptr, ws.nbytes,
                                  _stream(stream)))
     return (mean, var, nn) if want_nn else (mean, var)
+
+
+def sts_kmeanspp(xy, t, m, seed=0, lloyd_iters=10, k_cap=None, stream=None):
+    """Space-time separated kMeans++ inducing points (Algorithm 3).  Returns
+    (xyk [k, 2], tk [k]) CUDA float64 tensors and (m_s, m_t)."""
+    n = t.shape[0]
+    k_cap = int(k_cap if k_cap is not None else 4 * m + 16)
+    xyk = torch.empty((k_cap, 2), dtype=torch.float64, device=t.device)
+    tk = torch.empty(k_cap, dtype=torch.float64, device=t.device)
+    nbytes = int(lib().vst_workspace_size_kmeans(int(n)))
+    buf = torch.empty(nbytes + 256, dtype=torch.uint8, device=t.device)
+    ptr = (buf.data_ptr() + 255) // 256 * 256
+    k, ms, mt = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int64(0)
+    pts = _points(xy, t)
+    _check(lib().vst_sts_kmeanspp(ctypes.byref(pts), int(m), ctypes.c_uint64(seed & (2**64 - 1)), int(lloyd_iters),
+                                  xyk.data_ptr(), tk.data_ptr(), k_cap, ctypes.byref(k), ctypes.byref(ms),
+                                  ctypes.byref(mt), ptr, nbytes, _stream(stream)))
+    return xyk[:k.value], tk[:k.value], (ms.value, mt.value)
 
 
 class BatchedWorkspace(Workspace):
