@@ -235,6 +235,18 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
         return a.elapsed_time(b) / reps
 
     k = 1000
+    # space-time separated kMeans++ selection (Algorithm 3) on the full
+    # workload, timed on its own (the legs below use the seeded inducing sets
+    # of the input generator)
+    xyf, tf = torch.from_numpy(w.xy).to(dev), torch.from_numpy(w.t).to(dev)
+    vst.sts_kmeanspp(xyf, tf, k, seed=11, lloyd_iters=10)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, (ms_c, mt_c) = vst.sts_kmeanspp(xyf, tf, k, seed=11, lloyd_iters=10)
+    torch.cuda.synchronize()
+    out["sts_kmeanspp"] = {"ms": (time.perf_counter() - t0) * 1e3, "m_s": ms_c, "m_t": mt_c, "k": ms_c * mt_c,
+                           "lloyd_iters": 10, "n": w.n}
+    del xyf, tf
     sub = type(w)(name="sub", xy=w.xy[:nv], t=w.t[:nv], z=w.z[:nv], theta=w.theta, m=w.m, order=None)
     xyk, tk = si.inducing_points(sub, k, seed=11, lloyd_iters=10)
     ind = (torch.from_numpy(xyk).to(dev), torch.from_numpy(tk).to(dev))
