@@ -25,13 +25,21 @@ at the end of Sect. 4.3):
 Pinned by (tests/test_oracle_vif.py): m = n-1 gives the exact GP likelihood
 for any k; k = 0 gives plain Vecchia; m = 0 gives the dense FITC likelihood
 (Sect. 4.2); the Woodbury value equals the dense Sigma~_VIF likelihood.
+
+The gradient (nll_grad) is the derivative of that NLL with the neighbour sets
+and inducing points held fixed, taken in forward mode on dense matrices: one
+derivative of every intermediate (Sigma_kk, L_kk, U, R~, A_i, D_i, B^{-1},
+Sigma~_VIF) per parameter, then 1/2 tr(Sigma~^{-1} dSigma~) - 1/2 alpha^T
+dSigma~ alpha.  Pinned by (tests/test_oracle_vif.py): central differences of
+nll; k = 0 gives the plain Vecchia gradient; m = n-1 gives the exact GP
+gradient for any k.
 """
 from __future__ import annotations
 
 import numpy as np
 import scipy.linalg as sla
 
-from . import cov_matrix
+from . import cov_grad, cov_matrix
 
 
 def lowrank(xy, t, xyk, tk, theta):
@@ -134,3 +142,94 @@ def dense_sigma(xy, t, theta, U, m, nn, cnt, A=None, D=None):
         B[i, nn[i, :cnt[i]]] = -A[i, :cnt[i]]
     Binv = sla.solve_triangular(B, np.eye(n), lower=True)
     return U @ U.T + Binv @ np.diag(D) @ Binv.T
+
+
+def _dcov(xy1, t1, xy2, t2, theta):
+    """d Sigma(x1, x2) / d(sigma1^2, c, a, gamma) as [4, n1, n2] (no nugget)."""
+    n1, n2 = t1.shape[0], t2.shape[0]
+    out = np.zeros((4, n1, n2))
+    for i in range(n1):
+        for j in range(n2):
+            h = float(np.hypot(xy1[i, 0] - xy2[j, 0], xy1[i, 1] - xy2[j, 1]))
+            out[:, i, j] = cov_grad(theta, h, float(t1[i] - t2[j]))
+    return out
+
+
+def nll_grad(xy, t, theta, xyk, tk, m, nn, cnt, y):
+    """VIF NLL and its gradient w.r.t. (sigma1^2, c, a, gamma, nugget), the
+    neighbour sets and inducing points held fixed (forward mode, dense; small n)."""
+    xy, t, y = np.asarray(xy, float), np.asarray(t, float), np.asarray(y, float)
+    n = t.shape[0]
+    k = 0 if tk is None else tk.shape[0]
+    theta = np.asarray(theta, float)
+    # low rank and its derivatives: U L^T = Sigma_nk, dL = L Phi(L^{-1} dSigma_kk L^{-T})
+    if k:
+        Skk = cov_matrix(xyk, tk, xyk, tk, theta)
+        Snk = cov_matrix(xy, t, xyk, tk, theta)
+        L = np.linalg.cholesky(Skk)
+        Linv = sla.solve_triangular(L, np.eye(k), lower=True)
+        U = Snk @ Linv.T
+        dSkk = _dcov(xyk, tk, xyk, tk, theta)
+        dSnk = _dcov(xy, t, xyk, tk, theta)
+    else:
+        U = np.zeros((n, 0))
+    dU = np.zeros((5, n, k))
+    for j in range(4):
+        if not k:
+            break
+        Z = Linv @ dSkk[j] @ Linv.T
+        Phi = np.tril(Z) - 0.5 * np.diag(np.diag(Z))
+        dL = L @ Phi
+        dU[j] = (dSnk[j] - U @ dL.T) @ Linv.T
+    # residual plus nugget and its derivatives
+    C = cov_matrix(xy, t, xy, t, theta)
+    dC = _dcov(xy, t, xy, t, theta)
+    Rt = C - U @ U.T + theta[4] * np.eye(n)
+    dRt = np.zeros((5, n, n))
+    for j in range(5):
+        if j < 4:
+            dRt[j] = dC[j] - dU[j] @ U.T - U @ dU[j].T
+        else:
+            dRt[j] = np.eye(n)
+    # residual Vecchia factor and its derivatives, row by row
+    A = np.zeros((n, m))
+    D = np.zeros(n)
+    dA = np.zeros((5, n, m))
+    dD = np.zeros((5, n))
+    for i in range(n):
+        N = nn[i, :cnt[i]].astype(np.int64)
+        c = N.size
+        if c == 0:
+            D[i] = Rt[i, i]
+            dD[:, i] = dRt[:, i, i]
+            continue
+        KN = Rt[np.ix_(N, N)]
+        kv = Rt[N, i]
+        a = np.linalg.solve(KN, kv)
+        A[i, :c] = a
+        D[i] = Rt[i, i] - kv @ a
+        for j in range(5):
+            dKN = dRt[j][np.ix_(N, N)]
+            dk = dRt[j][N, i]
+            dA[j, i, :c] = np.linalg.solve(KN, dk - dKN @ a)
+            dD[j, i] = dRt[j][i, i] - 2.0 * dk @ a + a @ dKN @ a
+    B = np.eye(n)
+    for i in range(n):
+        B[i, nn[i, :cnt[i]]] = -A[i, :cnt[i]]
+    Binv = sla.solve_triangular(B, np.eye(n), lower=True)
+    S = Binv @ np.diag(D) @ Binv.T
+    Sig = U @ U.T + S
+    Lf = np.linalg.cholesky(Sig)
+    alpha = sla.cho_solve((Lf, True), y)
+    Sinv = sla.cho_solve((Lf, True), np.eye(n))
+    value = 0.5 * n * np.log(2 * np.pi) + np.log(np.diag(Lf)).sum() + 0.5 * y @ alpha
+    grad = np.zeros(5)
+    for j in range(5):
+        dAm = np.zeros((n, n))
+        for i in range(n):
+            dAm[i, nn[i, :cnt[i]]] = dA[j, i, :cnt[i]]
+        dBinv = Binv @ dAm @ Binv  # B = I - A
+        dS = dBinv @ np.diag(D) @ Binv.T + Binv @ np.diag(dD[j]) @ Binv.T + Binv @ np.diag(D) @ dBinv.T
+        dSig = dU[j] @ U.T + U @ dU[j].T + dS
+        grad[j] = 0.5 * np.sum(Sinv * dSig) - 0.5 * alpha @ dSig @ alpha
+    return value, grad

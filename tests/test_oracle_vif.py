@@ -91,3 +91,45 @@ def test_residual_neighbours_match_python_sort():
     d = np.sqrt(np.diag(R)[keep])
     assert np.all(np.abs(R[np.ix_(keep, keep)] / d[:, None] / d[None, :]) <= 1 + 1e-9)
     assert np.all(r >= -1e-12)
+
+
+def _vif_nll_at(xy, t, th, xyk, tk, m, nn, cnt, y):
+    U, _ = vif.lowrank(xy, t, xyk, tk, th)
+    return vif.nll(xy, t, th, U, m, nn, cnt, y)
+
+
+def test_gradient_matches_central_differences():
+    # d NLL / d theta_j against (NLL(theta + h e_j) - NLL(theta - h e_j)) / 2h,
+    # h relative 1e-5: the truncation error is O(h^2) ~ 1e-10 relative
+    xy, t, th, xyk, tk, y = setup(n_st=16, n_days=4, k=10, order="random")
+    U, r = vif.lowrank(xy, t, xyk, tk, th)
+    nn, cnt, _, _ = vif.knn(xy, t, th, U, r, 5)
+    v, g = vif.nll_grad(xy, t, th, xyk, tk, 5, nn, cnt, y)
+    assert v == pytest.approx(vif.nll(xy, t, th, U, 5, nn, cnt, y), rel=1e-12)
+    for j in range(5):
+        h = 1e-5 * th[j]
+        tp, tm = th.copy(), th.copy()
+        tp[j] += h
+        tm[j] -= h
+        fd = (_vif_nll_at(xy, t, tp, xyk, tk, 5, nn, cnt, y) - _vif_nll_at(xy, t, tm, xyk, tk, 5, nn, cnt, y)) / (2 * h)
+        assert g[j] == pytest.approx(fd, rel=1e-6, abs=1e-6 * np.abs(g).max()), j
+
+
+def test_gradient_k0_is_plain_vecchia_gradient():
+    xy, t, th, xyk, tk, y = setup(n_st=16, n_days=4, k=0)
+    nn, cnt, _, _ = oracle.knn(xy, t, th, 6)
+    v, g = vif.nll_grad(xy, t, th, None, None, 6, nn, cnt, y)
+    v0, g0 = oracle.nll_grad(xy, t, th, 6, nn, cnt, y)
+    assert v == pytest.approx(v0, rel=1e-12)
+    np.testing.assert_allclose(g, g0, rtol=1e-9, atol=1e-10 * np.abs(g0).max())
+
+
+def test_gradient_all_predecessors_is_exact_gp_gradient():
+    # m = n-1: Sigma~_VIF = Sigma + sigma^2 I for every theta, so the gradient
+    # is the exact GP gradient whatever the inducing points
+    xy, t, th, xyk, tk, y = setup(n_st=12, n_days=4, k=9)
+    m, nn, cnt = oracle.all_predecessors(t.shape[0])
+    v, g = vif.nll_grad(xy, t, th, xyk, tk, m, nn, cnt, y)
+    v0, g0 = oracle.dense_nll(xy, t, th, y, grad=True)
+    assert v == pytest.approx(v0, rel=1e-11)
+    np.testing.assert_allclose(g, g0, rtol=1e-8, atol=1e-9 * np.abs(g0).max())
