@@ -263,10 +263,19 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
                                        inducing=ind), 3)
     v3 = vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED_BF16X3, ws=ws, inducing=ind).item()
     vst.vst_workspace_status(ws)
+    # the VIF NLL and gradient (FP64, adjoint pass), its own larger workspace
+    del ws
+    wsg = vst.Workspace(nv, w.m, k, device=dev, vif_grad=True)
+    tg = timed(lambda: vst.vecchia_nll_grad(xy, t, th, w.m, nn, cnt, y, precision=vst.FP64, ws=wsg,
+                                            inducing=ind), 2)
+    vg, gg = vst.vecchia_nll_grad(xy, t, th, w.m, nn, cnt, y, precision=vst.FP64, ws=wsg, inducing=ind)
+    vst.vst_workspace_status(wsg)
     out["sub"] = {"n": nv, "k": k, "m": w.m, "knn_ms": knn_ms, "knn_queries_per_s": nv / (knn_ms * 1e-3),
                   "nll_fp64_ms": t64, "nll_mixed_ms": tmx, "dnll_per_n": abs(vmx - v64) / nv,
-                  "nll_mixed_bf16x3_ms": t3, "dnll_per_n_bf16x3": abs(v3 - v64) / nv}
-    del ws, nn, cnt
+                  "nll_mixed_bf16x3_ms": t3, "dnll_per_n_bf16x3": abs(v3 - v64) / nv,
+                  "nll_grad_fp64_ms": tg, "nll_grad_fp64_evals_per_s": 1e3 / tg,
+                  "grad_nll_equals_nll": vg.item() == v64, "grad": [float(v) for v in gg.cpu()]}
+    del wsg, nn, cnt
     if not full:
         return out
     # full size, mixed

@@ -124,6 +124,8 @@ vst_status vst_theta_from_ranges(double sigma1sq, double range_s, double range_t
 /* Host-only.  Workspace bytes needed by any entry point below for n points,
  * m neighbours and k inducing points (k = 0: plain Vecchia). */
 size_t vst_workspace_size(int64_t n, int m, int64_t k);
+/* Workspace of vecchia_nll_grad with k > 0 inducing points (VIF). */
+size_t vst_workspace_size_vif_grad(int64_t n, int m, int64_t k);
 
 /* Correlation-based Vecchia neighbour selection (Sect. 4.4.1).
  * For every row i: the min(i, m) predecessors j < i with the largest
@@ -179,8 +181,13 @@ vst_status vecchia_nll(const vst_points* pts, const vst_theta* theta, int m,
 /* NLL and its gradient with respect to the native parameters in the order
  * (sigma1sq, c, a, gamma, nugget); alpha, delta and nu are held fixed and the
  * neighbour sets are held fixed.  grad: 5 FP64 device values.  The factor is
- * recomputed, not stored.  Plain Vecchia only: ind with k > 0 returns
- * VST_EINVAL. */
+ * recomputed, not stored.
+ * VIF (ind != NULL, k > 0; the likelihood of Sect. 4.3 as in vecchia_nll,
+ * inducing points held fixed): FP64 only (precision VST_FP64, else
+ * VST_EINVAL); workspace vst_workspace_size_vif_grad(n, m, k) bytes.  The
+ * gradient is the exact derivative of the VIF NLL that vecchia_nll returns,
+ * by an adjoint pass through the Woodbury terms, the residual blocks and the
+ * low-rank part U = Sigma_nk L^{-T} (L L^T = Sigma_kk). */
 vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m,
                             const vst_inducing* ind, const int32_t* nn, const int32_t* nn_cnt,
                             const double* y, int precision, double* nll, double* grad,

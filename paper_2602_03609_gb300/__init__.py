@@ -25,6 +25,7 @@ import torch
 
 __all__ = [
     "FP64", "MIXED", "MAX_M", "VstError", "lib", "vst_theta_from_ranges", "vst_workspace_size",
+    "vst_workspace_size_vif_grad",
     "Workspace", "vif_build_neighbors", "vecchia_factor", "vecchia_nll", "vecchia_nll_grad",
     "vecchia_sample", "vst_workspace_status", "VecchiaNLL", "theta_tuple", "vst_profile_enable",
     "vst_profile_read", "vecchia_nll_grad_noalloc", "vst_noalloc_status", "NOALLOC_MAX_N",
@@ -93,6 +94,8 @@ def lib():
         L.vst_theta_from_ranges.argtypes = [ctypes.c_double] * 8 + [ctypes.POINTER(_Theta)]
         L.vst_workspace_size.restype = ctypes.c_size_t
         L.vst_workspace_size.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int64]
+        L.vst_workspace_size_vif_grad.restype = ctypes.c_size_t
+        L.vst_workspace_size_vif_grad.argtypes = [ctypes.c_int64, ctypes.c_int, ctypes.c_int64]
         PT, TH, IN = ctypes.POINTER(_Points), ctypes.POINTER(_Theta), ctypes.POINTER(_Inducing)
         L.vif_build_neighbors.restype = ctypes.c_int
         L.vif_build_neighbors.argtypes = [PT, TH, ctypes.c_int, IN, _P, _P, _P, ctypes.c_int64, _P,
@@ -185,16 +188,22 @@ def vst_workspace_size(n, m, k=0) -> int:
     return int(lib().vst_workspace_size(int(n), int(m), int(k)))
 
 
-class Workspace:
-    """Caller-owned scratch memory (a CUDA uint8 tensor, 256-byte aligned)."""
+def vst_workspace_size_vif_grad(n, m, k) -> int:
+    return int(lib().vst_workspace_size_vif_grad(int(n), int(m), int(k)))
 
-    def __init__(self, n, m, k=0, device=None):
-        self.nbytes = vst_workspace_size(n, m, k)
+
+class Workspace:
+    """Caller-owned scratch memory (a CUDA uint8 tensor, 256-byte aligned).
+    vif_grad=True sizes it for the VIF gradient (k > 0)."""
+
+    def __init__(self, n, m, k=0, device=None, vif_grad=False):
+        self.nbytes = vst_workspace_size_vif_grad(n, m, k) if (vif_grad and k > 0) else vst_workspace_size(n, m, k)
         self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device or "cuda")
         self.ptr = (self.buf.data_ptr() + 255) // 256 * 256
 
-    def fits(self, n, m, k=0):
-        return self.nbytes >= vst_workspace_size(n, m, k)
+    def fits(self, n, m, k=0, vif_grad=False):
+        need = vst_workspace_size_vif_grad(n, m, k) if (vif_grad and k > 0) else vst_workspace_size(n, m, k)
+        return self.nbytes >= need
 
 
 def _ptr(x, dtype, name):
@@ -221,10 +230,10 @@ def _points(xy, t):
     return _Points(_ptr(xy, torch.float64, "xy"), _ptr(t, torch.float64, "t"), n)
 
 
-def _ws(ws, n, m, k=0):
+def _ws(ws, n, m, k=0, vif_grad=False):
     if ws is None:
-        ws = Workspace(n, m, k)
-    if not ws.fits(n, m, k):
+        ws = Workspace(n, m, k, vif_grad=vif_grad)
+    if not ws.fits(n, m, k, vif_grad=vif_grad):
         raise ValueError("workspace too small")
     return ws
 
@@ -290,14 +299,18 @@ def vecchia_nll(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, out=None, ws=Non
     return out
 
 
-def vecchia_nll_grad(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, nll=None, grad=None, ws=None, stream=None):
-    """NLL and its gradient w.r.t. (sigma1sq, c, a, gamma, nugget); CUDA tensors."""
+def vecchia_nll_grad(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, nll=None, grad=None, ws=None, stream=None,
+                     inducing=None):
+    """NLL and its gradient w.r.t. (sigma1sq, c, a, gamma, nugget); CUDA tensors.
+    With inducing=(xyk, tk): the VIF likelihood (Sect. 4.3), FP64 only."""
     n = t.shape[0]
+    ind, k = _inducing(inducing)
     nll = nll if nll is not None else torch.empty(1, dtype=torch.float64, device=t.device)
     grad = grad if grad is not None else torch.empty(5, dtype=torch.float64, device=t.device)
-    ws = _ws(ws, n, m)
+    ws = _ws(ws, n, m, k, vif_grad=True)
     pts = _points(xy, t)
-    _check(lib().vecchia_nll_grad(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), None,
+    _check(lib().vecchia_nll_grad(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m),
+                                  ctypes.byref(ind) if ind else None,
                                   _ptr(nn, torch.int32, "nn"), _ptr(nn_cnt, torch.int32, "nn_cnt"),
                                   _ptr(y, torch.float64, "y"), int(precision), _ptr(nll, torch.float64, "nll"),
                                   _ptr(grad, torch.float64, "grad"), ws.ptr, ws.nbytes, _stream(stream)))

@@ -322,6 +322,10 @@ vst_status vst_theta_from_ranges(double sigma1sq, double range_s, double range_t
 
 size_t vst_workspace_size(int64_t n, int m, int64_t k) { return ws_layout(n, m, k).total; }
 
+size_t vst_workspace_size_vif_grad(int64_t n, int m, int64_t k) {
+  return ws_layout(n, m, k).total + vif_grad_extra_bytes(n, m, k);
+}
+
 vst_status vecchia_factor(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind,
                           const int32_t* nn, const int32_t* nn_cnt, int precision, double* A, double* D,
                           void* ws, size_t ws_bytes, void* stream) {
@@ -361,12 +365,21 @@ vst_status vecchia_nll(const vst_points* pts, const vst_theta* theta, int m, con
 vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind,
                             const int32_t* nn, const int32_t* nn_cnt, const double* y, int precision, double* nll,
                             double* grad, void* ws, size_t ws_bytes, void* stream) {
-  if (ind && ind->k > 0)
-    return fail(VST_EINVAL, "the VIF gradient is not available in this version (vecchia_nll gives the VIF NLL)");
-  vst_status s = check_common(pts, theta, m, nn, nn_cnt, ws, ws_bytes, 0);
+  const int64_t k = (ind && ind->k > 0) ? ind->k : 0;
+  vst_status s = check_inducing(ind);
+  if (s == VST_OK) s = check_common(pts, theta, m, nn, nn_cnt, ws, ws_bytes, k);
   if (s != VST_OK) return s;
   if (!valid_precision(precision)) return fail(VST_EINVAL, "bad precision %d", precision);
   if (!nll || !grad || (pts->n > 0 && !y)) return fail(VST_EINVAL, "y/nll/grad is NULL");
+  if (k > 0) {
+    if (precision != VST_FP64) return fail(VST_EINVAL, "the VIF gradient is computed in FP64 only (precision 0)");
+    const size_t need = vst_workspace_size_vif_grad(pts->n, m, k);
+    if (ws_bytes < need) return fail(VST_ENOMEM, "workspace has %zu bytes, %zu needed", ws_bytes, need);
+    const WsLayout L = ws_layout(pts->n, m, k);
+    launch_init_header(reinterpret_cast<WsHeader*>(static_cast<char*>(ws) + L.hdr), (cudaStream_t)stream);
+    return vif_nll_grad64(pts, theta, m, ind, nu_code(theta->nu), nn, nn_cnt, y, nll, grad, ws,
+                          (cudaStream_t)stream);
+  }
   return run_rows(pts, theta, m, nn, nn_cnt, y, plain_precision(precision), kModeNllGrad, nll, grad, nullptr,
                   nullptr, ws, (cudaStream_t)stream);
 }

@@ -43,7 +43,9 @@
 
 namespace vst {
 
-enum RowMode { kModeNll = 0, kModeNllGrad = 1, kModeFactor = 2 };
+// kModeVifAdj (FP64 only): the VIF gradient's pass over the residual blocks,
+// with the per-row adjoints of A_i and D_i given (abar, dbar)
+enum RowMode { kModeNll = 0, kModeNllGrad = 1, kModeFactor = 2, kModeVifAdj = 3 };
 
 struct RowArgs {
   const double* xy;
@@ -81,6 +83,11 @@ struct RowArgs {
   const float4* lagdf;
   // mixed form: per-point records (row0-relative like xy, t, y); required
   const PrepPt* prep;
+  // kModeVifAdj: adjoints dNLL/dA_i [n][m] and dNLL/dD_i [n]; out: the
+  // block's symmetric adjoint weights W_pq per packed pair [n][NPAIR]
+  const double* abar;
+  const double* dbar;
+  double* wblk;
   // single-dataset form: rows out0..n-1 are processed and their per-row
   // arrays (nn, nn_cnt, flag, A, D) hold row i at index i - out0 (0: all rows)
   int64_t out0;
@@ -260,7 +267,8 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       xj = xy[2 * (int64_t)idx];
       yj = xy[2 * (int64_t)idx + 1];
       tj = tv[idx];
-      if (MODE != kModeFactor) rj = g.y[row0 + idx];
+      if (MODE == kModeVifAdj) rj = (lane < cnt) ? g.abar[ri * m + lane] : 0.0;
+      else if (MODE != kModeFactor) rj = g.y[row0 + idx];
     }
     const bool tint = (tj == floor(tj)) && fabs(tj) < 1.0e9;
     allint = __all_sync(kFull, tint);
@@ -281,7 +289,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   const T diag = MIXED ? (T)th.dg_hi : (T)(th.sigma1sq + th.nugget);
   // a Gram (VIF) is only ever passed to the factor mode; the NLL and
   // gradient instantiations compile without the VIF code
-  constexpr bool CAN_VIF = (MODE == kModeFactor);
+  constexpr bool CAN_VIF = (MODE == kModeFactor || MODE == kModeVifAdj);
   const bool vif = CAN_VIF && (g.gram_d != nullptr || g.gram_f != nullptr);
   (void)vif;
   const auto* lags = lag_smem ? bs->lag : nullptr;
@@ -351,7 +359,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     }
     s.K[r][c] = v;
     s.K[c][r] = v;
-    if (MODE == kModeNllGrad) {
+    if (MODE == kModeNllGrad || MODE == kModeVifAdj) {
       if constexpr (MIXED) {
         s.q1[e] = q1;
       } else {
@@ -450,7 +458,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   }
 
   // backward solves with L_N^T: aj = (L_N^{-T} w)_j, bj = (L_N^{-T} z_N)_j
-  const bool need_b = (MODE == kModeNllGrad);
+  const bool need_b = (MODE == kModeNllGrad) || (MODE == kModeVifAdj);
   const bool need_a = MIXED || MODE != kModeNll;
   T aj = T(0), bj = T(0);
   if (need_a) {
@@ -561,7 +569,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       if (lane == 0) report_error(g.hdr, VST_ENOTSPD, gi);
       return;
     }
-    if (MODE != kModeFactor && lane == 0) acc.add(0, log(Ll) + 0.5 * zl * zl);
+    if (MODE != kModeFactor && MODE != kModeVifAdj && lane == 0) acc.add(0, log(Ll) + 0.5 * zl * zl);
   }
 
   if (MODE == kModeFactor) {
@@ -575,9 +583,11 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   }
 
   // ---- 5. adjoint: sum over pairs of W_pq dSigma~_pq / dtheta
-  if (MODE == kModeNllGrad) {
-    const T c2 = rt / Dt;
-    const T c1 = T(0.5) * (T(1) / Dt - c2 * c2);
+  // (kModeVifAdj: W = Dbar a~ a~^T + (a~ b~^T + b~ a~^T) / 2 with
+  // b~ = (K_N^{-1} Abar, 0), i.e. c1 = Dbar, c2 = -1)
+  if (MODE == kModeNllGrad || MODE == kModeVifAdj) {
+    const T c2 = MODE == kModeVifAdj ? T(-1) : rt / Dt;
+    const T c1 = MODE == kModeVifAdj ? (T)g.dbar[ri] : T(0.5) * (T(1) / Dt - c2 * c2);
     __syncwarp();
     if (lane < PM) {
       const T at = (lane < cnt) ? -aj : (lane == LAST ? T(1) : T(0));
@@ -595,9 +605,13 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       const int rc = bs->pairs[e];
       const int r = rc & 0xff, c = rc >> 8;
       const Pos<T> pr = s.pos[r], pc = s.pos[c];
-      if (!pr.valid || !pc.valid) continue;
+      if (!pr.valid || !pc.valid) {
+        if (MODE == kModeVifAdj) g.wblk[ri * NPAIR + e] = 0.0;
+        continue;
+      }
       const T ar = s.ab[r][0], br = s.ab[r][1], ac = s.ab[c][0], bc = s.ab[c][1];
       const T w = ar * (c1 * ac - hc2 * bc) - hc2 * br * ac;
+      if (MODE == kModeVifAdj) g.wblk[ri * NPAIR + e] = (double)w;
       if (r == c) {
         gd += w;  // dC(0,0)/dsigma1^2 = 1 and d/dnugget = 1
       } else {

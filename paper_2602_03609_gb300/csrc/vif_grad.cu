@@ -1,0 +1,639 @@
+// Gradient of the VIF negative log-likelihood (Sect. 4.3) with respect to
+// (sigma1^2, c, a, gamma, nugget), FP64, by an adjoint through the Woodbury
+// terms and the residual blocks.
+//
+// With Sigma_VIF = U U^T + S, S = B^{-1} D B^{-T} the Vecchia factor of the
+// residual R~ = C - U U^T + nugget I, U = Sigma_nk L^{-T}, L L^T = Sigma_kk,
+// alpha = Sigma_VIF^{-1} y and Q = Sigma_VIF^{-1} - alpha alpha^T:
+//   dNLL = 1/2 <Q, dU U^T + U dU^T> + 1/2 <Q, dS>.
+// In terms of what the NLL already computes (W = D^{-1/2} B U, e =
+// D^{-1/2} B y, M = I + W^T W, v = W^T e) and Y = W M^{-1}:
+//   eps = e - Y v,  beta = y - U M^{-1} v,  s = W^T eps,
+//   Q U = B^T F,  F = D^{-1/2} (Y - eps s^T),
+//   1/2 <Q, dS> = sum_i Abar_i . dA_i + Dbar_i dD_i,
+//     Abar_iq = -(Y_i . U_nn(i,q) + eps_i beta_nn(i,q)) / sqrt(D_i),
+//     Dbar_i  = (1 - Y_i . W_i - eps_i^2) / (2 D_i),
+// and through each residual block (A_i = K_N^{-1} k, D_i = K_ii - k.A_i)
+//   Abar . dA + Dbar dD = sum_pq Wb_pq dK_pq,
+//   Wb = Dbar a~ a~^T + (a~ b~^T + b~ a~^T) / 2,  a~ = (-A_i, 1),
+//   b~ = (K_N^{-1} Abar_i, 0).
+// dK = dC + dnugget I - (dU_p . U_q + U_p . dU_q): the first part is the
+// fused row kernel's adjoint pass (kModeVifAdj); the second adds -2 Z U to
+// the gradient with respect to U, Z = sum_i (block i's Wb placed at its
+// rows), gathered per row through the reverse neighbour index.  With
+// G_U = B^T F - 2 Z U, H = G_U L^{-1} and J = H^T U,
+//   <G_U, dU> = <H, dSigma_nk> - <J, dL>,  dL = L Phi(L^{-1} dSigma_kk L^{-T})
+// (Phi: lower triangle, halved diagonal), and <J, dL> = <Omega, dSigma_kk>,
+// Omega = L^{-T} Psi L^{-1}, Psi the symmetric part of L^T J with the strict
+// lower triangle halved on each side and the diagonal halved.
+#include <algorithm>
+#include <cmath>
+
+#include "kernels.h"
+#include "profile.h"
+#include "vif.h"
+#include "workspace.h"
+
+namespace vst {
+
+vst_status fail(vst_status s, const char* fmt, ...);
+vst_status cuda_fail(cudaError_t e, const char* where);
+vst_status chol64(double* A, int k, WsHeader* hdr, int err_code, cudaStream_t st);
+__global__ void trinv_kernel(const double* L, int k, double* X);
+void launch_lag_table(const DevTheta& th, LagD* d, LagF* f, cudaStream_t st);
+void launch_reduce_partials(const double* p0, int64_t w0, const double* p1, int64_t w1, double nll_const,
+                            double* nll, double* grad, cudaStream_t st);
+void apply_launch_shape(RowArgs& g, int batched, int precision, int nu, int pm);
+
+namespace {
+
+constexpr int kChunks = 32;  // row chunks of the deterministic column reductions
+
+struct GradLayout {
+  size_t LinvM, Minv, Y, GU, H, abar, dbar, eps, beta, qd, wv, svec, spart, wblk, roff, rcur, rent, bsum,
+      t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, total;
+};
+
+GradLayout grad_layout(int64_t n, int m, int64_t k) {
+  GradLayout G{};
+  size_t off = 0;
+  auto take = [&off](size_t b) {
+    const size_t at = off;
+    off = (off + b + 255) & ~size_t(255);
+    return at;
+  };
+  const size_t nn = (size_t)std::max<int64_t>(n, 1), kk = (size_t)std::max<int64_t>(k, 1);
+  const size_t mm = (size_t)std::max(m, 1);
+  const int pm = padded_pm(m + 1);
+  const size_t npair = (size_t)pm * (pm + 1) / 2;
+  G.LinvM = take(8 * kk * kk);
+  G.Minv = take(8 * kk * kk);
+  G.Y = take(8 * nn * kk);
+  G.GU = take(8 * nn * kk);
+  G.H = take(8 * nn * kk);
+  G.abar = take(8 * nn * mm);
+  G.dbar = take(8 * nn);
+  G.eps = take(8 * nn);
+  G.beta = take(8 * nn);
+  G.qd = take(8 * nn);
+  G.wv = take(8 * kk);
+  G.svec = take(8 * kk);
+  G.spart = take(8 * kk * kChunks);
+  G.wblk = take(8 * nn * npair);
+  G.roff = take(8 * (nn + 1));
+  G.rcur = take(4 * nn);
+  G.rent = take(8 * nn * (mm + 1));
+  G.bsum = take(8 * (nn / 1024 + 2));
+  G.t1part = take(8 * 4 * 4096);
+  G.Jpart = take(8 * kk * kk * kChunks);
+  G.J = take(8 * kk * kk);
+  G.Kp = take(8 * kk * kk);
+  G.Psi = take(8 * kk * kk);
+  G.T1 = take(8 * kk * kk);
+  G.Omega = take(8 * kk * kk);
+  G.t2part = take(8 * 4 * 4096);
+  G.grows = take(8 * 8);
+  G.total = off;
+  return G;
+}
+
+// ---- dense FP64 GEMMs, 64 x 64 output tiles, 4 x 4 per thread, K step 16
+// C[M][N] = A[M][K] B[K][N]; b_lower: B[a][b] = 0 for a < b (rows below the
+// column tile's first column skipped)
+__global__ void __launch_bounds__(256) gemm_nn_kernel(const double* A, int64_t lda, const double* B, int64_t ldb,
+                                                      double* C, int64_t ldc, int64_t M, int N, int K, int b_lower) {
+  constexpr int BT = 64, BK = 16;
+  __shared__ double As[BK][BT + 2], Bs[BK][BT + 2];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int64_t i0 = (int64_t)blockIdx.y * BT;
+  const int j0 = blockIdx.x * BT;
+  double acc[4][4] = {};
+  const int kbeg = b_lower ? (j0 / BK) * BK : 0;
+  for (int k0 = kbeg; k0 < K; k0 += BK) {
+    __syncthreads();
+    for (int q = tid; q < BK * BT; q += 256) {
+      const int kk = q & (BK - 1), ii = q >> 4;
+      As[kk][ii] = (i0 + ii < M && k0 + kk < K) ? A[(i0 + ii) * lda + k0 + kk] : 0.0;
+      const int kb = q / BT, jj = q % BT;
+      Bs[kb][jj] = (k0 + kb < K && j0 + jj < N) ? B[(int64_t)(k0 + kb) * ldb + j0 + jj] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[kk][ty * 4 + u];
+        b[u] = Bs[kk][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t i = i0 + ty * 4 + u;
+    if (i >= M) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int j = j0 + tx * 4 + v;
+      if (j < N) C[i * ldc + j] = acc[u][v];
+    }
+  }
+}
+
+// partial C[a][b] = sum over rows i of the chunk of A[i][a] B[i][b]
+// (A: rows x Na, B: rows x Nb); a_lower: A[i][a] = 0 for i < a
+__global__ void __launch_bounds__(256) gemm_tn_kernel(const double* A, int64_t lda, const double* B, int64_t ldb,
+                                                      int64_t rows, int Na, int Nb, int64_t chunk, int a_lower,
+                                                      double* part) {
+  constexpr int BT = 64, BK = 16;
+  __shared__ double As[BK][BT + 2], Bs[BK][BT + 2];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int a0 = blockIdx.y * BT, b0 = blockIdx.x * BT;
+  int64_t r0 = (int64_t)blockIdx.z * chunk;
+  const int64_t r1 = rows < r0 + chunk ? rows : r0 + chunk;
+  if (a_lower && r0 < a0) r0 = r1 < (int64_t)a0 ? r1 : (int64_t)a0;
+  double acc[4][4] = {};
+  for (int64_t k0 = r0; k0 < r1; k0 += BK) {
+    __syncthreads();
+    for (int q = tid; q < BK * BT; q += 256) {
+      const int kk = q / BT, jj = q % BT;
+      const int64_t r = k0 + kk;
+      As[kk][jj] = (r < r1 && a0 + jj < Na && (!a_lower || r >= a0 + jj)) ? A[r * lda + a0 + jj] : 0.0;
+      Bs[kk][jj] = (r < r1 && b0 + jj < Nb) ? B[r * ldb + b0 + jj] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        a[u] = As[kk][ty * 4 + u];
+        b[u] = Bs[kk][tx * 4 + u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
+    }
+  }
+  double* P = part + (int64_t)blockIdx.z * Na * Nb;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int a = a0 + ty * 4 + u;
+    if (a >= Na) continue;
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int b = b0 + tx * 4 + v;
+      if (b < Nb) P[(int64_t)a * Nb + b] = acc[u][v];
+    }
+  }
+}
+
+__global__ void sum_parts_kernel(const double* part, int nparts, int64_t count, double* out) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int c = 0; c < nparts; ++c) s += part[(int64_t)c * count + q];
+    out[q] = s;
+  }
+}
+
+// y = A x for a k x k row-major A
+__global__ void gemv_kernel(const double* A, const double* x, int k, double* y) {
+  const int lane = threadIdx.x & 31;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= k) return;
+  double s = 0.0;
+  for (int c = lane; c < k; c += 32) s += A[(int64_t)r * k + c] * x[c];
+  s = warp_sum(s);
+  if (lane == 0) y[r] = s;
+}
+
+// per row: eps = e - Y v, beta = y - U wv, qd = Y . W
+__global__ void rowvec_kernel(int64_t n, int k, const double* Y, const double* WE, const double* U, const double* v,
+                              const double* wv, const double* y, double* eps, double* beta, double* qd) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w; i < n; i += nw) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    const double* Yi = Y + i * k;
+    const double* Wi = WE + i * (int64_t)(k + 1);
+    const double* Ui = U + i * k;
+    for (int p = lane; p < k; p += 32) {
+      a = fma(Yi[p], v[p], a);
+      b = fma(Ui[p], wv[p], b);
+      c = fma(Yi[p], Wi[p], c);
+    }
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    if (lane == 0) {
+      eps[i] = Wi[k] - a;
+      beta[i] = y[i] - b;
+      qd[i] = c;
+    }
+  }
+}
+
+// s = W^T eps: per row chunk, partial column sums
+__global__ void wteps_kernel(int64_t n, int k, const double* WE, const double* eps, int64_t chunk, double* part) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= k) return;
+  const int64_t r0 = (int64_t)blockIdx.y * chunk, r1 = n < r0 + chunk ? n : r0 + chunk;
+  double s = 0.0;
+  for (int64_t i = r0; i < r1; ++i) s = fma(WE[i * (int64_t)(k + 1) + c], eps[i], s);
+  part[(int64_t)blockIdx.y * k + c] = s;
+}
+
+// Abar and Dbar per row
+__global__ void adj_kernel(int64_t n, int m, int k, const int32_t* nn, const int32_t* nn_cnt, const double* Y,
+                           const double* U, const double* D, const double* eps, const double* beta,
+                           const double* qd, double* abar, double* dbar) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w; i < n; i += nw) {
+    const int cnt = min(max(nn_cnt[i], 0), m);
+    const double Di = D[i], sd = 1.0 / sqrt(Di);
+    const double* Yi = Y + i * k;
+    for (int q = 0; q < m; ++q) {
+      double val = 0.0;
+      if (q < cnt) {
+        const int j = nn[i * m + q];
+        if (j >= 0 && j < i) {
+          double s = 0.0;
+          const double* Uj = U + (int64_t)j * k;
+          for (int p = lane; p < k; p += 32) s = fma(Yi[p], Uj[p], s);
+          s = warp_sum(s);
+          val = -(s + eps[i] * beta[j]) * sd;
+        }
+      }
+      if (lane == 0) abar[i * m + q] = val;
+    }
+    if (lane == 0) dbar[i] = 0.5 * (1.0 - qd[i] - eps[i] * eps[i]) / Di;
+  }
+}
+
+// ---- reverse index: for every row r the (block row i, position p) pairs of
+// the residual blocks that contain r (p < cnt_i: neighbour slot, p = PM - 1:
+// r = i itself), in increasing (i, p)
+__global__ void rcount_kernel(int64_t n, int m, const int32_t* nn, const int32_t* nn_cnt, int64_t* cnt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[i + 1]), 1ull);
+    const int c = min(max(nn_cnt[i], 0), m);
+    for (int q = 0; q < c; ++q) {
+      const int j = nn[i * m + q];
+      if (j >= 0 && j < i) atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[j + 1]), 1ull);
+    }
+  }
+}
+// inclusive scan of cnt[1..n] in place (three passes)
+__global__ void rscan_blocks_kernel(int64_t* a, int64_t n, int64_t* bsum) {
+  __shared__ int64_t s[1024];
+  const int64_t i = blockIdx.x * 1024 + threadIdx.x;
+  s[threadIdx.x] = i < n ? a[i] : 0;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int64_t add = threadIdx.x >= o ? s[threadIdx.x - o] : 0;
+    __syncthreads();
+    s[threadIdx.x] += add;
+    __syncthreads();
+  }
+  if (i < n) a[i] = s[threadIdx.x];
+  if (threadIdx.x == 1023) bsum[blockIdx.x] = s[1023];
+}
+__global__ void rscan_sums_kernel(int64_t* bsum, int nb) {
+  if (threadIdx.x == 0 && blockIdx.x == 0)
+    for (int b = 1; b < nb; ++b) bsum[b] += bsum[b - 1];
+}
+__global__ void rscan_add_kernel(int64_t* a, int64_t n, const int64_t* bsum) {
+  const int64_t i = blockIdx.x * 1024 + threadIdx.x;
+  if (i < n && blockIdx.x > 0) a[i] += bsum[blockIdx.x - 1];
+}
+__global__ void rfill_kernel(int64_t n, int m, int last, const int32_t* nn, const int32_t* nn_cnt, const int64_t* off,
+                             int32_t* cur, int2* ent) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    ent[off[i] + atomicAdd(&cur[i], 1)] = make_int2((int)i, last);
+    const int c = min(max(nn_cnt[i], 0), m);
+    for (int q = 0; q < c; ++q) {
+      const int j = nn[i * m + q];
+      if (j >= 0 && j < i) ent[off[j] + atomicAdd(&cur[j], 1)] = make_int2((int)i, q);
+    }
+  }
+}
+__global__ void rsort_kernel(int64_t n, const int64_t* off, int2* ent) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t a = off[r], b = off[r + 1];
+    for (int64_t x = a + 1; x < b; ++x) {
+      const int2 v = ent[x];
+      int64_t y = x - 1;
+      while (y >= a && (ent[y].x > v.x || (ent[y].x == v.x && ent[y].y > v.y))) {
+        ent[y + 1] = ent[y];
+        --y;
+      }
+      ent[y + 1] = v;
+    }
+  }
+}
+
+template <int PM>
+__device__ __forceinline__ int pair_index(int r, int c) {  // r >= c, inverse of pair_of
+  if (r < PM / 2) return r * (PM + 1) + c;
+  const int pr = PM - 1 - r;
+  return pr * (PM + 1) + pr + 1 + c;
+}
+
+// G_U[r] = F_r - sum_{(i,p): p < last} A_ip F_i - 2 sum_{(i,p)} sum_q Wb^(i)_pq U_(block i, q),
+// F_i = (Y_i - eps_i s) / sqrt(D_i).  One warp per row, 32 columns at a time.
+template <int PM>
+__global__ void __launch_bounds__(128) gu_kernel(int64_t n, int m, int k, const int32_t* nn, const int32_t* nn_cnt,
+                                                 const int64_t* off, const int2* ent, const double* A,
+                                                 const double* D, const double* Y, const double* eps,
+                                                 const double* svec, const double* U, const double* wblk,
+                                                 double* GU) {
+  constexpr int NPAIR = PM * (PM + 1) / 2, L = PM - 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = w; r < n; r += nw) {
+    const int64_t a = off[r], b = off[r + 1];
+    const double sr = 1.0 / sqrt(D[r]), er = eps[r];
+    for (int c0 = 0; c0 < k; c0 += 32) {
+      const int c = c0 + lane;
+      const bool on = c < k;
+      const double sc = on ? svec[c] : 0.0;
+      double acc = on ? (Y[r * k + c] - er * sc) * sr : 0.0;
+      for (int64_t x = a; x < b; ++x) {
+        const int2 en = ent[x];
+        const int64_t i = en.x;
+        const int p = en.y;
+        const int cnt = min(max(nn_cnt[i], 0), min(m, L));
+        if (p < L) {  // B^T F: r is neighbour p of row i
+          const double Aip = A[i * m + p];
+          if (on) acc = fma(-Aip, (Y[i * k + c] - eps[i] * sc) / sqrt(D[i]), acc);
+        }
+        // -2 Z U: block i's weights of position p against every position q
+        const double* Wi = wblk + i * NPAIR;
+        for (int q = 0; q < PM; ++q) {
+          int row;
+          if (q == L) row = (int)i;
+          else if (q < cnt) row = nn[i * m + q];
+          else continue;
+          if (row < 0 || row > i) continue;  // invalid lists are reported by the row kernel
+          const double wpq = Wi[p >= q ? pair_index<PM>(p, q) : pair_index<PM>(q, p)];
+          if (on) acc = fma(-2.0 * wpq, U[(int64_t)row * k + c], acc);
+        }
+      }
+      if (on) GU[r * k + c] = acc;
+    }
+  }
+}
+
+// covariance of Eq. (2) and its derivatives with respect to (sigma1^2, c, a, gamma)
+template <int NU>
+__device__ __forceinline__ void cov_derivs(const DevTheta& th, double dx, double dy, double u, double (&d)[4]) {
+  const LagD f = lag_factors(th, u);
+  const double x = f.G * sqrt(dx * dx + dy * dy);
+  const double E = exp(-x);
+  const double C = f.P * matern_M<NU, double>(x, E);
+  const double X = f.P * matern_xdM<NU, double>(x, E);  // P x M'(x)
+  d[0] = C / th.sigma1sq;
+  d[1] = X / th.c;
+  d[2] = f.Qa * (-th.p * C - 0.5 * th.gamma * X);
+  d[3] = -f.L * (C + 0.5 * X);
+}
+
+// sum over (i, p) of H[i][p] dSigma_nk[i][p]/dtheta, per block partials
+template <int NU>
+__global__ void term1_kernel(int64_t n, int k, const double* xy, const double* t, const double* xyk,
+                             const double* tk, DevTheta th, const double* H, double* part) {
+  __shared__ double sh[4][256];
+  double acc[4] = {0, 0, 0, 0};
+  const int64_t total = n * k;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = q / k;
+    const int p = (int)(q % k);
+    double d[4];
+    cov_derivs<NU>(th, xy[2 * i] - xyk[2 * p], xy[2 * i + 1] - xyk[2 * p + 1], t[i] - tk[p], d);
+    const double h = H[q];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = fma(h, d[j], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sh[j][threadIdx.x] = acc[j];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 4; ++j) part[(int64_t)blockIdx.x * 4 + j] = sh[j][0];
+}
+
+// sum over (a, b) of Omega[a][b] dSigma_kk[a][b]/dtheta
+template <int NU>
+__global__ void term2_kernel(int k, const double* xyk, const double* tk, DevTheta th, const double* Om,
+                             double* part) {
+  __shared__ double sh[4][256];
+  double acc[4] = {0, 0, 0, 0};
+  const int64_t total = (int64_t)k * k;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(q / k), b = (int)(q % k);
+    double d[4];
+    cov_derivs<NU>(th, xyk[2 * a] - xyk[2 * b], xyk[2 * a + 1] - xyk[2 * b + 1], tk[a] - tk[b], d);
+    const double o = Om[q];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = fma(o, d[j], acc[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) sh[j][threadIdx.x] = acc[j];
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) sh[j][threadIdx.x] += sh[j][threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+    for (int j = 0; j < 4; ++j) part[(int64_t)blockIdx.x * 4 + j] = sh[j][0];
+}
+
+// Psi from K' = L^T J: strict lower part halved onto both triangles, diagonal halved
+__global__ void psi_kernel(int k, const double* Kp, double* Psi) {
+  const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (q >= (int64_t)k * k) return;
+  const int a = (int)(q / k), b = (int)(q % k);
+  Psi[q] = a > b ? 0.5 * Kp[q] : (a < b ? 0.5 * Kp[(int64_t)b * k + a] : 0.5 * Kp[q]);
+}
+
+// grad = row-kernel sums + term1 - term2 (first four), nugget from the rows
+__global__ void combine_kernel(const double* grows, const double* t1, int n1, const double* t2, int n2,
+                               double* grad) {
+  const int j = threadIdx.x;
+  if (j >= 5) return;
+  double v = grows[j];
+  if (j < 4) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < n1; ++q) a += t1[q * 4 + j];
+    for (int q = 0; q < n2; ++q) b += t2[q * 4 + j];
+    v += a - b;
+  }
+  grad[j] = v;
+}
+
+void gemm_nn(const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int64_t M, int N,
+             int K, bool b_lower, cudaStream_t st) {
+  constexpr int64_t kRowsPerLaunch = 65535 * 64;  // grid.y limit
+  for (int64_t r0 = 0; r0 < M; r0 += kRowsPerLaunch) {
+    const int64_t rows = std::min(kRowsPerLaunch, M - r0);
+    const dim3 grid((unsigned)((N + 63) / 64), (unsigned)((rows + 63) / 64));
+    gemm_nn_kernel<<<grid, 256, 0, st>>>(A + r0 * lda, lda, B, ldb, C + r0 * ldc, ldc, rows, N, K, b_lower ? 1 : 0);
+  }
+}
+// C[Na][Nb] = A^T B over `rows` rows, deterministic: kChunks row chunks then a fixed-order sum
+void gemm_tn(const double* A, int64_t lda, const double* B, int64_t ldb, int64_t rows, int Na, int Nb, bool a_lower,
+             double* part, double* C, cudaStream_t st) {
+  const int64_t chunk = std::max<int64_t>((rows + kChunks - 1) / kChunks, 16);
+  const int nch = (int)std::max<int64_t>(1, (rows + chunk - 1) / chunk);
+  const dim3 grid((unsigned)((Nb + 63) / 64), (unsigned)((Na + 63) / 64), (unsigned)nch);
+  gemm_tn_kernel<<<grid, 256, 0, st>>>(A, lda, B, ldb, rows, Na, Nb, chunk, a_lower ? 1 : 0, part);
+  const int64_t count = (int64_t)Na * Nb;
+  sum_parts_kernel<<<(unsigned)std::min<int64_t>((count + 255) / 256, 4096), 256, 0, st>>>(part, nch, count, C);
+}
+
+}  // namespace
+
+size_t vif_grad_extra_bytes(int64_t n, int m, int64_t k) { return grad_layout(n, m, k).total; }
+
+// VIF NLL and gradient, FP64.  The workspace is ws_layout(n, m, k) followed by
+// the gradient scratch (vif_grad_extra_bytes).
+vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
+                          const int32_t* nn, const int32_t* nn_cnt, const double* y, double* nll, double* grad,
+                          void* ws, cudaStream_t st) {
+  const int64_t n = pts->n;
+  const int k = (int)ind->k;
+  vst_status s = vif_nll(pts, theta, m, ind, nu, nn, nn_cnt, y, VST_FP64, nll, ws, st);
+  if (s != VST_OK) return s;
+  if (n == 0) return cudaMemsetAsync(grad, 0, 5 * sizeof(double), st) == cudaSuccess ? VST_OK : VST_ECUDA;
+  char* base = static_cast<char*>(ws);
+  const WsLayout L = ws_layout(n, m, k);
+  char* vb = base + L.vif;
+  const VifLayout V = vif_layout(n, m, k);
+  char* gb = base + L.total;
+  const GradLayout G = grad_layout(n, m, k);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
+  auto P = [&](size_t o) { return reinterpret_cast<double*>(gb + o); };
+  const double* A = reinterpret_cast<const double*>(base + L.sA);
+  const double* D = reinterpret_cast<const double*>(base + L.sD);
+  const double* U = reinterpret_cast<const double*>(vb + V.U);
+  const double* X = reinterpret_cast<const double*>(vb + V.X);   // L^{-1}
+  const double* Lkk = reinterpret_cast<const double*>(vb + V.S);  // L (lower, in place)
+  const double* WE = reinterpret_cast<const double*>(vb + V.WE);
+  const double* LM = reinterpret_cast<const double*>(vb + V.M);   // Cholesky factor of M
+  const double* v = reinterpret_cast<const double*>(vb + V.v);    // W^T e
+  const DevTheta th = dev_theta_vif(theta);
+  const int pm = padded_pm(m + 1);
+  const int64_t gridw = std::min<int64_t>((n + 7) / 8, 65535);  // 8 warps per block of 256
+
+  // M^{-1} = L_M^{-T} L_M^{-1}
+  {
+    const int wpb = 4;
+    const size_t smem = sizeof(double) * k * wpb;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(trinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    trinv_kernel<<<(k + wpb - 1) / wpb, 32 * wpb, smem, st>>>(LM, k, P(G.LinvM));
+    gemm_tn(P(G.LinvM), k, P(G.LinvM), k, k, k, k, false, P(G.Jpart), P(G.Minv), st);
+  }
+  // Y = W M^{-1}; wv = M^{-1} v
+  gemm_nn(WE, k + 1, P(G.Minv), k, P(G.Y), k, n, k, k, false, st);
+  gemv_kernel<<<(k * 32 + 255) / 256, 256, 0, st>>>(P(G.Minv), v, k, P(G.wv));
+  rowvec_kernel<<<(unsigned)gridw, 256, 0, st>>>(n, k, P(G.Y), WE, U, v, P(G.wv), y, P(G.eps), P(G.beta), P(G.qd));
+  {
+    const int64_t chunk = (n + kChunks - 1) / kChunks;
+    wteps_kernel<<<dim3((k + 255) / 256, kChunks), 256, 0, st>>>(n, k, WE, P(G.eps), chunk, P(G.spart));
+    sum_parts_kernel<<<(k + 255) / 256, 256, 0, st>>>(P(G.spart), kChunks, k, P(G.svec));
+  }
+  adj_kernel<<<(unsigned)gridw, 256, 0, st>>>(n, m, k, nn, nn_cnt, P(G.Y), U, D, P(G.eps), P(G.beta), P(G.qd),
+                                              P(G.abar), P(G.dbar));
+  // residual-block pass (covariance part of the gradient, block weights out)
+  {
+    LagD* lagd = reinterpret_cast<LagD*>(base + L.lagd);
+    LagF* lagf = reinterpret_cast<LagF*>(base + L.lagf);
+    launch_lag_table(th, lagd, lagf, st);
+    RowArgs g{};
+    g.xy = pts->xy;
+    g.t = pts->t;
+    g.nn = nn;
+    g.nn_cnt = nn_cnt;
+    g.n = n;
+    g.m = m;
+    g.th = th;
+    g.lagd = lagd;
+    g.lagf = lagf;
+    g.flag = reinterpret_cast<uint8_t*>(base + L.flag);
+    g.hdr = hdr;
+    g.tau = 1.0e4f;
+    g.partial = reinterpret_cast<double*>(base + L.partial);
+    g.gram_d = reinterpret_cast<const double*>(vb + V.gram);
+    g.abar = P(G.abar);
+    g.dbar = P(G.dbar);
+    g.wblk = P(G.wblk);
+    apply_launch_shape(g, 0, VST_FP64, nu, m + 1);
+    int64_t w = 0;
+    cudaError_t e = launch_rows(false, nu, m + 1, kModeVifAdj, g, st, &w);
+    if (e != cudaSuccess) return cuda_fail(e, "VIF adjoint row kernel");
+    if (w > kMaxPartialWarps) return fail(VST_EINTERNAL, "too many warps");
+    launch_reduce_partials(g.partial, w, g.partial, 0, 0.0, P(G.grows) + 5, P(G.grows), st);
+  }
+  // reverse index and G_U
+  {
+    int64_t* off = reinterpret_cast<int64_t*>(gb + G.roff);
+    int32_t* cur = reinterpret_cast<int32_t*>(gb + G.rcur);
+    int2* ent = reinterpret_cast<int2*>(gb + G.rent);
+    int64_t* bsum = reinterpret_cast<int64_t*>(gb + G.bsum);
+    cudaError_t e = cudaMemsetAsync(off, 0, 8 * (size_t)(n + 1), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(cur, 0, 4 * (size_t)n, st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    const unsigned g1 = (unsigned)std::min<int64_t>((n + 255) / 256, 8192);
+    rcount_kernel<<<g1, 256, 0, st>>>(n, m, nn, nn_cnt, off);
+    const int nb = (int)((n + 1 + 1023) / 1024);
+    rscan_blocks_kernel<<<nb, 1024, 0, st>>>(off, n + 1, bsum);
+    rscan_sums_kernel<<<1, 32, 0, st>>>(bsum, nb);
+    rscan_add_kernel<<<nb, 1024, 0, st>>>(off, n + 1, bsum);
+    rfill_kernel<<<g1, 256, 0, st>>>(n, m, pm - 1, nn, nn_cnt, off, cur, ent);
+    rsort_kernel<<<g1, 256, 0, st>>>(n, off, ent);
+    const unsigned g2 = (unsigned)std::min<int64_t>((n + 3) / 4, 65535);
+    switch (pm) {
+      case 8: gu_kernel<8><<<g2, 128, 0, st>>>(n, m, k, nn, nn_cnt, off, ent, A, D, P(G.Y), P(G.eps), P(G.svec), U, P(G.wblk), P(G.GU)); break;
+      case 16: gu_kernel<16><<<g2, 128, 0, st>>>(n, m, k, nn, nn_cnt, off, ent, A, D, P(G.Y), P(G.eps), P(G.svec), U, P(G.wblk), P(G.GU)); break;
+      case 24: gu_kernel<24><<<g2, 128, 0, st>>>(n, m, k, nn, nn_cnt, off, ent, A, D, P(G.Y), P(G.eps), P(G.svec), U, P(G.wblk), P(G.GU)); break;
+      default: gu_kernel<32><<<g2, 128, 0, st>>>(n, m, k, nn, nn_cnt, off, ent, A, D, P(G.Y), P(G.eps), P(G.svec), U, P(G.wblk), P(G.GU));
+    }
+  }
+  // H = G_U L^{-1}; term1 = <H, dSigma_nk>; J = H^T U
+  gemm_nn(P(G.GU), k, X, k, P(G.H), k, n, k, k, true, st);
+  const int nb1 = (int)std::min<int64_t>((n * k + 255) / 256, 4096);
+  if (nu == 0) term1_kernel<0><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, P(G.H), P(G.t1part));
+  else if (nu == 1) term1_kernel<1><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, P(G.H), P(G.t1part));
+  else term1_kernel<2><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, P(G.H), P(G.t1part));
+  gemm_tn(P(G.H), k, U, k, n, k, k, false, P(G.Jpart), P(G.J), st);
+  // K' = L^T J, Psi, Omega = X^T (Psi X), term2 = <Omega, dSigma_kk>
+  gemm_tn(Lkk, k, P(G.J), k, k, k, k, true, P(G.Jpart), P(G.Kp), st);
+  psi_kernel<<<(unsigned)(((int64_t)k * k + 255) / 256), 256, 0, st>>>(k, P(G.Kp), P(G.Psi));
+  gemm_nn(P(G.Psi), k, X, k, P(G.T1), k, k, k, k, true, st);
+  gemm_tn(X, k, P(G.T1), k, k, k, k, true, P(G.Jpart), P(G.Omega), st);
+  const int nb2 = (int)std::min<int64_t>(((int64_t)k * k + 255) / 256, 4096);
+  if (nu == 0) term2_kernel<0><<<nb2, 256, 0, st>>>(k, ind->xy, ind->t, th, P(G.Omega), P(G.t2part));
+  else if (nu == 1) term2_kernel<1><<<nb2, 256, 0, st>>>(k, ind->xy, ind->t, th, P(G.Omega), P(G.t2part));
+  else term2_kernel<2><<<nb2, 256, 0, st>>>(k, ind->xy, ind->t, th, P(G.Omega), P(G.t2part));
+  combine_kernel<<<1, 32, 0, st>>>(P(G.grows), P(G.t1part), nb1, P(G.t2part), nb2, grad);
+  const cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? VST_OK : cuda_fail(e, "VIF gradient kernels");
+}
+
+}  // namespace vst

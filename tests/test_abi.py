@@ -80,11 +80,17 @@ def test_host_validation_without_gpu(vst):
     rc = L.vecchia_factor(ctypes.byref(pts), ctypes.byref(th), 5, None, 1024, 2048, 0, 4096, 8192, 256, 16,
                           None)
     assert rc == 2
-    # the VIF gradient is not available in this version; too many inducing points
+    # the VIF gradient: FP64 only, and it needs its own (larger) workspace;
+    # too many inducing points
     ind = vst._Inducing(256, 512, 5)
-    rc = L.vecchia_nll_grad(ctypes.byref(pts), ctypes.byref(th), 5, ctypes.byref(ind), 1024, 2048, 4096, 0, 8192,
+    rc = L.vecchia_nll_grad(ctypes.byref(pts), ctypes.byref(th), 5, ctypes.byref(ind), 1024, 2048, 4096, 1, 8192,
                             8448, 256, 1 << 40, None)
     assert rc == 1 and b"VIF gradient" in L.vst_last_error()
+    need = L.vst_workspace_size_vif_grad(10, 5, 5)
+    assert need > L.vst_workspace_size(10, 5, 5)
+    rc = L.vecchia_nll_grad(ctypes.byref(pts), ctypes.byref(th), 5, ctypes.byref(ind), 1024, 2048, 4096, 0, 8192,
+                            8448, 256, need - 1, None)
+    assert rc == 2
     big = vst._Inducing(256, 512, 1 << 20)
     rc = L.vif_build_neighbors(ctypes.byref(pts), ctypes.byref(th), 5, ctypes.byref(big), 1024, 2048, None, 0,
                                256, 1 << 40, None)
