@@ -111,19 +111,70 @@ def describe(w):
 
 # ---------------------------------------------------------------------------
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """SM clock and throttle reasons sampled during the timed region: NVML
+    (read-only queries through ctypes) polled every 20 ms from a thread, so
+    that a timed region of a few tens of ms still gets samples; nvidia-smi
+    (-lms 200) if NVML cannot be loaded.  The GPU is found by its UUID."""
+    # NVML clock-event reason bits
+    REASONS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20, "hw_thermal_slowdown": 0x40}
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
+    def __init__(self, index, uuid=None):
         self.index = index
+        self.uuid = uuid
         self.proc = None
+        self.nvml = None
         self.lines = []
+        self.samples = []
+        self.mx = None
+        self.stop_ev = threading.Event()
+
+    def _nvml_handle(self):
+        import ctypes
+        L = ctypes.CDLL("libnvidia-ml.so.1")
+        if L.nvmlInit_v2() != 0:
+            return None
+        h = ctypes.c_void_p()
+        if self.uuid:
+            rc = L.nvmlDeviceGetHandleByUUID(self.uuid.encode(), ctypes.byref(h))
+        else:
+            rc = L.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.index), ctypes.byref(h))
+        if rc != 0:
+            return None
+        mx = ctypes.c_uint()
+        if L.nvmlDeviceGetMaxClockInfo(h, ctypes.c_int(1), ctypes.byref(mx)) == 0:  # NVML_CLOCK_SM
+            self.mx = float(mx.value)
+        try:
+            reasons = L.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            reasons = L.nvmlDeviceGetCurrentClocksThrottleReasons
+        return L.nvmlDeviceGetClockInfo, reasons, h
+
+    def _poll(self):
+        import ctypes
+        clock_info, reasons, h = self.nvml
+        clk = ctypes.c_uint()
+        rs = ctypes.c_ulonglong()
+        while not self.stop_ev.is_set():
+            if clock_info(h, ctypes.c_int(1), ctypes.byref(clk)) == 0:
+                r = rs.value if reasons(h, ctypes.byref(rs)) == 0 else 0
+                self.samples.append((float(clk.value), r))
+            self.stop_ev.wait(0.02)
 
     def start(self):
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+            self.nvml = self._nvml_handle()
+        except (OSError, AttributeError):
+            self.nvml = None
+        if self.nvml is not None:
+            self.th = threading.Thread(target=self._poll, daemon=True)
+            self.th.start()
+            return
+        try:
+            gid = self.uuid or str(self.index)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={gid}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "200"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.th = threading.Thread(target=self._read, daemon=True)
@@ -136,6 +187,14 @@ class Clocks:
             self.lines.append(line.strip())
 
     def stop(self):
+        if self.nvml is not None:
+            self.stop_ev.set()
+            self.th.join(timeout=2)
+            if not self.samples:
+                return None
+            reasons = sorted(nm for nm, bit in self.REASONS.items() if any(r & bit for _, r in self.samples))
+            return {"sm_mhz": statistics.median(c for c, _ in self.samples), "sm_max_mhz": self.mx,
+                    "reasons": reasons, "samples": len(self.samples), "source": "nvml, 20 ms"}
         if self.proc is None:
             return None
         self.proc.terminate()
@@ -159,7 +218,17 @@ class Clocks:
                     reasons.add(nm)
         if not sm:
             return None
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm),
+                "source": "nvidia-smi, 200 ms"}
+
+
+def device_uuid(torch, index):
+    """'GPU-…' UUID of a CUDA device (for NVML / nvidia-smi), or None."""
+    try:
+        u = str(torch.cuda.get_device_properties(index).uuid)
+    except (AttributeError, RuntimeError):
+        return None
+    return u if u.startswith("GPU-") else "GPU-" + u
 
 
 def batched_leg(vst, torch, dev, steps):
@@ -524,41 +593,54 @@ def run_ours(args):
 
     fp64_steps = max(1, min(args.fp64_steps, args.steps))
     ms64, l64, k64, _, _ = timed(vst.FP64, 1, fp64_steps)
-    clocks = Clocks(local)
+    clocks = Clocks(local, device_uuid(torch, local))
     clocks.start()
     ms, lrows, krows, lfb, kfb = timed(vst.MIXED, args.warmup, args.steps)
     clk = clocks.stop()
 
     # end to end through the public API with host buffers: pinned host inputs
-    # copied in, result copied out, every step
+    # copied in, result copied out, every step.  Two device input buffers and
+    # a copy stream: the host-to-device copy of step s + 1 overlaps the
+    # evaluation of step s (the inputs do not depend on the result); the
+    # copy into a buffer waits until the evaluation that last read it is done
     h_in = [torch.from_numpy(a).pin_memory() for a in (w.xy, w.t)]
     h_y = y.cpu().pin_memory()
     h_nn, h_cnt = nn.cpu().pin_memory(), cnt.cpu().pin_memory()
     h_out = torch.empty(6, dtype=torch.float64).pin_memory()
-    d_xy, d_t, d_y = torch.empty_like(xy), torch.empty_like(t), torch.empty_like(y)
-    d_nn, d_cnt = torch.empty_like(nn), torch.empty_like(cnt)
+    bufs = [tuple(torch.empty_like(x) for x in (xy, t, y, nn, cnt)) for _ in range(2)]
     h2d = sum(x.numel() * x.element_size() for x in (h_in[0], h_in[1], h_y, h_nn, h_cnt))
     d2h = 6 * 8
     out6 = torch.empty(6, dtype=torch.float64, device=dev)
+    cstream = torch.cuda.Stream(device=dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
 
-    def e2e_step():
-        d_xy.copy_(h_in[0], non_blocking=True)
-        d_t.copy_(h_in[1], non_blocking=True)
-        d_y.copy_(h_y, non_blocking=True)
-        d_nn.copy_(h_nn, non_blocking=True)
-        d_cnt.copy_(h_cnt, non_blocking=True)
+    def e2e_step(s):
+        bi = s % 2
+        d_xy, d_t, d_y, d_nn, d_cnt = bufs[bi]
+        with torch.cuda.stream(cstream):
+            cstream.wait_event(freed[bi])
+            d_xy.copy_(h_in[0], non_blocking=True)
+            d_t.copy_(h_in[1], non_blocking=True)
+            d_y.copy_(h_y, non_blocking=True)
+            d_nn.copy_(h_nn, non_blocking=True)
+            d_cnt.copy_(h_cnt, non_blocking=True)
+            copied[bi].record(cstream)
+        stream.wait_event(copied[bi])
         vst.vecchia_nll_grad(d_xy, d_t, th, w.m, d_nn, d_cnt, d_y, precision=vst.MIXED, nll=out6[:1],
-                             grad=out6[1:], ws=ws)
+                             grad=out6[1:], ws=ws, stream=stream)
+        freed[bi].record(stream)
         h_out.copy_(out6, non_blocking=True)
 
-    for _ in range(2):
-        e2e_step()
+    for s_ in range(2):
+        e2e_step(s_)
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2e_steps = max(3, args.steps // 2)
     a.record(stream)
-    for _ in range(e2e_steps):
-        e2e_step()
+    cstream.wait_event(a)
+    for s_ in range(e2e_steps):
+        e2e_step(s_)
     b.record(stream)
     torch.cuda.synchronize()
     e2e_ms = a.elapsed_time(b) / e2e_steps

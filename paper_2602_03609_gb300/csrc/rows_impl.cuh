@@ -113,12 +113,16 @@ struct WarpSm {
   double tt[PM];                                    // times (non-integer lag path)
 };
 
-// Block-wide tables shared by the warps: the (r, c) position pair of each
-// packed lower-triangle index, and the first kLagSmem lags of the lag table.
+// Block-wide tables shared by the warps: the off-diagonal position pairs
+// (r, c) a local block can use, as r | c << 8 | e << 16 with e the packed
+// lower-triangle index (positions 0..m-1 and the row's own position PM-1;
+// positions m..PM-2 are padding for every row and never enter the pair
+// loops), and the first kLagSmem lags of the lag table.
 constexpr int kLagSmem = 128;
 template <typename T, int PM>
 struct BlockSm {
-  uint16_t pairs[PM * (PM + 1) / 2];
+  uint32_t pairs[PM * (PM + 1) / 2];
+  int npairs;
   alignas(16) typename std::conditional<std::is_same<T, float>::value, LagF, LagD>::type lag[kLagSmem];
 };
 
@@ -183,6 +187,13 @@ template <int PM>
 __device__ __forceinline__ void pair_of(int e, int& r, int& c) {
   const int pr = e / (PM + 1), off = e - pr * (PM + 1);
   if (off <= pr) { r = pr; c = off; } else { r = PM - 1 - pr; c = off - pr - 1; }
+}
+// packed index of the pair (r, c), r >= c (the inverse of pair_of)
+template <int PM>
+__device__ __forceinline__ int pair_e(int r, int c) {
+  if (r < PM / 2) return r * (PM + 1) + c;
+  const int pr = PM - 1 - r;
+  return pr * (PM + 1) + pr + 1 + c;
 }
 
 // 16-byte vector load / store of 16 / sizeof(T) consecutive shared elements
@@ -293,17 +304,16 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   const bool vif = CAN_VIF && (g.gram_d != nullptr || g.gram_f != nullptr);
   (void)vif;
   const auto* lags = lag_smem ? bs->lag : nullptr;
+  const int npairs = bs->npairs;
 #pragma unroll 2
-  for (int e = lane; e < NPAIR; e += 32) {
-    const int rc = bs->pairs[e];
-    const int r = rc & 0xff, c = rc >> 8;
+  for (int q = lane; q < npairs; q += 32) {
+    const uint32_t rce = bs->pairs[q];
+    const int r = rce & 0xff, c = (rce >> 8) & 0xff, e = (int)(rce >> 16);
     T v;
     float q1 = 0.f;
     T xv = T(0), ev = T(1);
     const Pos<T> pr = s.pos[r], pc = s.pos[c];
-    if (r == c) {
-      v = pr.valid ? diag : T(1);
-    } else if (!pr.valid || !pc.valid) {
+    if (!pr.valid || !pc.valid) {
       v = T(0);
     } else {
       const T dx = pr.ox - pc.ox, dy = pr.oy - pc.oy;
@@ -351,8 +361,6 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     if (CAN_VIF && vif && pr.valid && pc.valid) {
       if (g.gram_d) {
         v -= (T)g.gram_d[gi * NPAIR + e];
-      } else if (g.gram_f && r == c) {
-        v = (T)((th.sigma1sq + th.nugget) - (double)g.gram_f[gi * NPAIR + e]);
       } else if (g.gram_f && !MIXED) {
         v -= (T)g.gram_f[gi * NPAIR + e];
       }
@@ -365,6 +373,24 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       } else {
         s.xe[e][0] = xv;
         s.xe[e][1] = ev;
+      }
+    }
+  }
+  // diagonal (unused positions: 1), and the padding positions m..PM-2, which
+  // the pair loop skips: identity rows and columns
+  if (lane < PM) {
+    const bool vj = s.pos[lane].valid;
+    T v = vj ? diag : T(1);
+    if (CAN_VIF && vif && vj) {
+      const int ed = pair_e<PM>(lane, lane);
+      if (g.gram_d) v -= (T)g.gram_d[gi * NPAIR + ed];
+      else if (g.gram_f) v = (T)((th.sigma1sq + th.nugget) - (double)g.gram_f[gi * NPAIR + ed]);
+    }
+    s.K[lane][lane] = v;
+    for (int j = m; j < LAST; ++j) {
+      if (lane != j) {
+        s.K[j][lane] = T(0);
+        s.K[lane][j] = T(0);
       }
     }
   }
@@ -601,9 +627,9 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     const T pexp = MIXED ? (T)th.pf : (T)th.p, hg = MIXED ? (T)th.hgf : (T)(0.5 * th.gamma);
     const T hc2 = T(0.5) * c2;
 #pragma unroll 2
-    for (int e = lane; e < NPAIR; e += 32) {
-      const int rc = bs->pairs[e];
-      const int r = rc & 0xff, c = rc >> 8;
+    for (int q = lane; q < npairs; q += 32) {
+      const uint32_t rce = bs->pairs[q];
+      const int r = rce & 0xff, c = (rce >> 8) & 0xff, e = (int)(rce >> 16);
       const Pos<T> pr = s.pos[r], pc = s.pos[c];
       if (!pr.valid || !pc.valid) {
         if (MODE == kModeVifAdj) g.wblk[ri * NPAIR + e] = 0.0;
@@ -612,9 +638,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       const T ar = s.ab[r][0], br = s.ab[r][1], ac = s.ab[c][0], bc = s.ab[c][1];
       const T w = ar * (c1 * ac - hc2 * bc) - hc2 * br * ac;
       if (MODE == kModeVifAdj) g.wblk[ri * NPAIR + e] = (double)w;
-      if (r == c) {
-        gd += w;  // dC(0,0)/dsigma1^2 = 1 and d/dnugget = 1
-      } else {
+      {
         T P, G, Qa, L;
         lag_lookup<T>(th, lagd, lagf, lags, allint, pr.td, pc.td, s.tt[r], s.tt[c], P, G, Qa, L);
         T Kv, Xv;  // P M(x) and P x M'(x)
@@ -632,6 +656,14 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
         g2 = fma(w2 * Qa, -pexp * Kv - hg * Xv, g2);
         g3 = fma(-w2 * L, Kv + T(0.5) * Xv, g3);
       }
+    }
+    // diagonal pairs: dC(0,0)/dsigma1^2 = 1 and d/dnugget = 1
+    if (lane < PM) {
+      const T at = s.ab[lane][0], bt = s.ab[lane][1];
+      const T w = at * (c1 * at - hc2 * bt) - hc2 * bt * at;
+      const bool vj = s.pos[lane].valid;
+      if (vj) gd += w;
+      if (MODE == kModeVifAdj) g.wblk[ri * NPAIR + pair_e<PM>(lane, lane)] = vj ? (double)w : 0.0;
     }
     const T inv_s1 = MIXED ? (T)th.inv_s1f : T(1.0 / th.sigma1sq);
     const T inv_c = MIXED ? (T)th.inv_cf : T(1.0 / th.c);
@@ -660,10 +692,24 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) rows_kernel(RowArgs g)
   WarpSm<T, PM>* sm = reinterpret_cast<WarpSm<T, PM>*>(smem_raw + block_sm_bytes<T, PM>());
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   WarpSm<T, PM>& s = sm[wib];
-  for (int e = threadIdx.x; e < WarpSm<T, PM>::NPAIR; e += WARPS * 32) {
-    int r, c;
-    pair_of<PM>(e, r, c);
-    bs->pairs[e] = (uint16_t)(r | (c << 8));
+  if (wib == 0) {
+    // the off-diagonal pairs among positions 0..m-1 and PM-1, in packed order
+    constexpr int NP = WarpSm<T, PM>::NPAIR;
+    const int m = g.m;
+    int count = 0;
+    for (int base = 0; base < NP; base += 32) {
+      const int e = base + lane;
+      int r = 0, c = 0;
+      bool keep = false;
+      if (e < NP) {
+        pair_of<PM>(e, r, c);
+        keep = r != c && (r < m || r == PM - 1) && (c < m || c == PM - 1);
+      }
+      const unsigned mask = __ballot_sync(kFull, keep);
+      if (keep) bs->pairs[count + __popc(mask & ((1u << lane) - 1u))] = (uint32_t)(r | (c << 8) | (e << 16));
+      count += __popc(mask);
+    }
+    if (lane == 0) bs->npairs = count;
   }
   if (g.offsets == nullptr) {
     for (int u = threadIdx.x; u < kLagSmem; u += WARPS * 32) {
