@@ -83,11 +83,11 @@ struct RowArgs {
   const float4* lagdf;
   // mixed form: per-point records (row0-relative like xy, t, y); required
   const PrepPt* prep;
-  // kModeVifAdj: adjoints dNLL/dA_i [n][m] and dNLL/dD_i [n]; out: the
-  // block's symmetric adjoint weights W_pq per packed pair [n][NPAIR]
+  // kModeVifAdj: adjoints dNLL/dA_i [n][m] and dNLL/dD_i [n]; out:
+  // b~_i = K_N^{-1} Abar_i [n][m] (0 beyond nn_cnt[i])
   const double* abar;
   const double* dbar;
-  double* wblk;
+  double* btil;
   // single-dataset form: rows out0..n-1 are processed and their per-row
   // arrays (nn, nn_cnt, flag, A, D) hold row i at index i - out0 (0: all rows)
   int64_t out0;
@@ -410,6 +410,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   T dinv = T(1);
 #pragma unroll
   for (int k = 0; k < PM; ++k) {
+    if (!MIXED && k >= m && k < LAST) continue;  // FP64: skip padding positions (identity rows and columns)
     const T piv = __shfl_sync(kFull, a[k], k);
     ok = ok && (piv > T(0));
     const T rs = drsqrt<T>(piv > T(0) ? piv : T(1));
@@ -477,6 +478,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     T accz = (lane < PM) ? yv : T(0);
 #pragma unroll
     for (int k = 0; k < PM; ++k) {
+      if (!MIXED && k >= m && k < LAST) continue;  // FP64: skip padding positions (identity rows and columns)
       const T zk = __shfl_sync(kFull, accz * dinv, k);
       if (lane == k) zj = zk;
       if (lane > k) accz = fma(-a[k], zk, accz);
@@ -491,6 +493,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     T acc_a = wj, acc_b = (lane < LAST) ? zj : T(0);
 #pragma unroll
     for (int k = LAST - 1; k >= 0; --k) {
+      if (!MIXED && k >= m && k < LAST) continue;  // FP64: skip padding positions (identity rows and columns)
       const T ak = __shfl_sync(kFull, acc_a * dinv, k);
       T bk = T(0);
       if (need_b) bk = __shfl_sync(kFull, acc_b * dinv, k);
@@ -538,6 +541,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       float accr = (lane < LAST) ? rf : 0.0f, dz = 0.0f;
 #pragma unroll
       for (int k = 0; k < LAST; ++k) {
+        if (!MIXED && k >= m && k < LAST) continue;  // FP64: skip padding positions (identity rows and columns)
         const float zk = __shfl_sync(kFull, accr * dinv, k);
         if (lane == k) dz = zk;
         if (lane > k) accr = fmaf(-a[k], zk, accr);
@@ -545,6 +549,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       float acc2 = (lane < LAST) ? dz : 0.0f, da = 0.0f;
 #pragma unroll
       for (int k = LAST - 1; k >= 0; --k) {
+        if (!MIXED && k >= m && k < LAST) continue;  // FP64: skip padding positions (identity rows and columns)
         const float dk = __shfl_sync(kFull, acc2 * dinv, k);
         if (lane == k) da = dk;
         if (lane < k) acc2 = fmaf(-Lsm[k][lane], dk, acc2);
@@ -621,6 +626,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       s.ab[lane][0] = at;
       s.ab[lane][1] = bt;
     }
+    if (MODE == kModeVifAdj && lane < m) g.btil[ri * m + lane] = (lane < cnt) ? (double)bj : 0.0;
     __syncwarp();
     // off-diagonal sums of w K and w X are scaled by 1/sigma1^2 and 1/c at the end
     T gd = 0, g0 = 0, g1 = 0, g2 = 0, g3 = 0;
@@ -632,12 +638,10 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       const int r = rce & 0xff, c = (rce >> 8) & 0xff, e = (int)(rce >> 16);
       const Pos<T> pr = s.pos[r], pc = s.pos[c];
       if (!pr.valid || !pc.valid) {
-        if (MODE == kModeVifAdj) g.wblk[ri * NPAIR + e] = 0.0;
         continue;
       }
       const T ar = s.ab[r][0], br = s.ab[r][1], ac = s.ab[c][0], bc = s.ab[c][1];
       const T w = ar * (c1 * ac - hc2 * bc) - hc2 * br * ac;
-      if (MODE == kModeVifAdj) g.wblk[ri * NPAIR + e] = (double)w;
       {
         T P, G, Qa, L;
         lag_lookup<T>(th, lagd, lagf, lags, allint, pr.td, pc.td, s.tt[r], s.tt[c], P, G, Qa, L);
@@ -663,7 +667,6 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       const T w = at * (c1 * at - hc2 * bt) - hc2 * bt * at;
       const bool vj = s.pos[lane].valid;
       if (vj) gd += w;
-      if (MODE == kModeVifAdj) g.wblk[ri * NPAIR + pair_e<PM>(lane, lane)] = vj ? (double)w : 0.0;
     }
     const T inv_s1 = MIXED ? (T)th.inv_s1f : T(1.0 / th.sigma1sq);
     const T inv_c = MIXED ? (T)th.inv_cf : T(1.0 / th.c);

@@ -18,10 +18,15 @@
 //   Wb = Dbar a~ a~^T + (a~ b~^T + b~ a~^T) / 2,  a~ = (-A_i, 1),
 //   b~ = (K_N^{-1} Abar_i, 0).
 // dK = dC + dnugget I - (dU_p . U_q + U_p . dU_q): the first part is the
-// fused row kernel's adjoint pass (kModeVifAdj); the second adds -2 Z U to
-// the gradient with respect to U, Z = sum_i (block i's Wb placed at its
-// rows), gathered per row through the reverse neighbour index.  With
-// G_U = B^T F - 2 Z U, H = G_U L^{-1} and J = H^T U,
+// fused row kernel's adjoint pass (kModeVifAdj); the second adds
+// -2 Wb U_block to the U sensitivity of the block's rows.  Wb has rank 2, so
+// with alpha_i = U_block^T a~ = (B U)_i = sqrt(D_i) W_i, beta_i =
+// U_block^T b~ and gamma_i = Dbar_i alpha_i + beta_i / 2 the block adds
+// -2 gamma_i to row i and 2 A_iq gamma_i - b~_q alpha_i to its neighbour
+// N(i)_q.  Altogether, with Phi_i = F_i - 2 gamma_i,
+//   G_U[r] = Phi_r - sum over (i, q) with N(i)_q = r of (A_iq Phi_i + b~_iq alpha_i),
+// gathered per row through the reverse neighbour index.  With
+// H = G_U L^{-1} and J = H^T U,
 //   <G_U, dU> = <H, dSigma_nk> - <J, dL>,  dL = L Phi(L^{-1} dSigma_kk L^{-T})
 // (Phi: lower triangle, halved diagonal), and <J, dL> = <Omega, dSigma_kk>,
 // Omega = L^{-T} Psi L^{-1}, Psi the symmetric part of L^T J with the strict
@@ -50,7 +55,7 @@ namespace {
 constexpr int kChunks = 32;  // row chunks of the deterministic column reductions
 
 struct GradLayout {
-  size_t LinvM, Minv, Y, GU, H, abar, dbar, eps, beta, qd, wv, svec, spart, wblk, roff, rcur, rent, bsum,
+  size_t LinvM, Minv, Y, GU, H, abar, dbar, eps, beta, qd, wv, svec, spart, btil, roff, rcur, rent, bsum,
       t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, total;
 };
 
@@ -64,8 +69,6 @@ GradLayout grad_layout(int64_t n, int m, int64_t k) {
   };
   const size_t nn = (size_t)std::max<int64_t>(n, 1), kk = (size_t)std::max<int64_t>(k, 1);
   const size_t mm = (size_t)std::max(m, 1);
-  const int pm = padded_pm(m + 1);
-  const size_t npair = (size_t)pm * (pm + 1) / 2;
   G.LinvM = take(8 * kk * kk);
   G.Minv = take(8 * kk * kk);
   G.Y = take(8 * nn * kk);
@@ -79,10 +82,10 @@ GradLayout grad_layout(int64_t n, int m, int64_t k) {
   G.wv = take(8 * kk);
   G.svec = take(8 * kk);
   G.spart = take(8 * kk * kChunks);
-  G.wblk = take(8 * nn * npair);
+  G.btil = take(8 * nn * mm);
   G.roff = take(8 * (nn + 1));
   G.rcur = take(4 * nn);
-  G.rent = take(8 * nn * (mm + 1));
+  G.rent = take(8 * nn * mm);
   G.bsum = take(8 * (nn / 1024 + 2));
   G.t1part = take(8 * 4 * 4096);
   G.Jpart = take(8 * kk * kk * kChunks);
@@ -278,12 +281,10 @@ __global__ void adj_kernel(int64_t n, int m, int k, const int32_t* nn, const int
   }
 }
 
-// ---- reverse index: for every row r the (block row i, position p) pairs of
-// the residual blocks that contain r (p < cnt_i: neighbour slot, p = PM - 1:
-// r = i itself), in increasing (i, p)
+// ---- reverse index: for every row r the (block row i, slot q) pairs with
+// N(i)_q = r, in increasing (i, q)
 __global__ void rcount_kernel(int64_t n, int m, const int32_t* nn, const int32_t* nn_cnt, int64_t* cnt) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    atomicAdd(reinterpret_cast<unsigned long long*>(&cnt[i + 1]), 1ull);
     const int c = min(max(nn_cnt[i], 0), m);
     for (int q = 0; q < c; ++q) {
       const int j = nn[i * m + q];
@@ -314,10 +315,9 @@ __global__ void rscan_add_kernel(int64_t* a, int64_t n, const int64_t* bsum) {
   const int64_t i = blockIdx.x * 1024 + threadIdx.x;
   if (i < n && blockIdx.x > 0) a[i] += bsum[blockIdx.x - 1];
 }
-__global__ void rfill_kernel(int64_t n, int m, int last, const int32_t* nn, const int32_t* nn_cnt, const int64_t* off,
+__global__ void rfill_kernel(int64_t n, int m, const int32_t* nn, const int32_t* nn_cnt, const int64_t* off,
                              int32_t* cur, int2* ent) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    ent[off[i] + atomicAdd(&cur[i], 1)] = make_int2((int)i, last);
     const int c = min(max(nn_cnt[i], 0), m);
     for (int q = 0; q < c; ++q) {
       const int j = nn[i * m + q];
@@ -340,55 +340,55 @@ __global__ void rsort_kernel(int64_t n, const int64_t* off, int2* ent) {
   }
 }
 
-template <int PM>
-__device__ __forceinline__ int pair_index(int r, int c) {  // r >= c, inverse of pair_of
-  if (r < PM / 2) return r * (PM + 1) + c;
-  const int pr = PM - 1 - r;
-  return pr * (PM + 1) + pr + 1 + c;
+// per row i: alpha_i = sqrt(D_i) W_i (into `alpha`), and Phi_i = F_i - 2 gamma_i
+// (in place over Y_i), F_i = (Y_i - eps_i s) / sqrt(D_i), gamma_i = Dbar_i
+// alpha_i + beta_i / 2, beta_i = sum_q b~_iq U_N(i)_q.  One warp per row.
+__global__ void __launch_bounds__(256) phi_kernel(int64_t n, int m, int k, const int32_t* nn,
+                                                  const int32_t* nn_cnt, const double* D, const double* dbar,
+                                                  const double* eps, const double* svec, const double* WE,
+                                                  const double* btil, const double* U, double* Y,
+                                                  double* alpha) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w; i < n; i += nw) {
+    const int cnt = min(max(nn_cnt[i], 0), m);
+    const double Di = D[i], sd = 1.0 / sqrt(Di), sq = sqrt(Di), db = dbar[i], ei = eps[i];
+    const double* Wi = WE + i * (int64_t)(k + 1);
+    for (int c = lane; c < k; c += 32) {
+      double be = 0.0;
+      for (int q = 0; q < cnt; ++q) {
+        const int j = nn[i * m + q];
+        if (j >= 0 && j < i) be = fma(btil[i * m + q], U[(int64_t)j * k + c], be);
+      }
+      const double al = sq * Wi[c];
+      const double F = (Y[i * k + c] - ei * svec[c]) * sd;
+      Y[i * k + c] = F - 2.0 * fma(db, al, 0.5 * be);
+      alpha[i * k + c] = al;
+    }
+  }
 }
 
-// G_U[r] = F_r - sum_{(i,p): p < last} A_ip F_i - 2 sum_{(i,p)} sum_q Wb^(i)_pq U_(block i, q),
-// F_i = (Y_i - eps_i s) / sqrt(D_i).  One warp per row, 32 columns at a time.
-template <int PM>
-__global__ void __launch_bounds__(128) gu_kernel(int64_t n, int m, int k, const int32_t* nn, const int32_t* nn_cnt,
-                                                 const int64_t* off, const int2* ent, const double* A,
-                                                 const double* D, const double* Y, const double* eps,
-                                                 const double* svec, const double* U, const double* wblk,
-                                                 double* GU) {
-  constexpr int NPAIR = PM * (PM + 1) / 2, L = PM - 1;
+// G_U[r] = Phi_r - sum over the reverse entries (i, q) of r of
+// (A_iq Phi_i + b~_iq alpha_i).  One warp per row, 32 columns at a time.
+__global__ void __launch_bounds__(256) gu_kernel(int64_t n, int m, int k, const int64_t* off, const int2* ent,
+                                                 const double* A, const double* btil, const double* Phi,
+                                                 const double* alpha, double* GU) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = w; r < n; r += nw) {
     const int64_t a = off[r], b = off[r + 1];
-    const double sr = 1.0 / sqrt(D[r]), er = eps[r];
-    for (int c0 = 0; c0 < k; c0 += 32) {
-      const int c = c0 + lane;
-      const bool on = c < k;
-      const double sc = on ? svec[c] : 0.0;
-      double acc = on ? (Y[r * k + c] - er * sc) * sr : 0.0;
+    for (int c = lane; c < k; c += 32) {
+      double acc = Phi[r * k + c];
       for (int64_t x = a; x < b; ++x) {
         const int2 en = ent[x];
         const int64_t i = en.x;
-        const int p = en.y;
-        const int cnt = min(max(nn_cnt[i], 0), min(m, L));
-        if (p < L) {  // B^T F: r is neighbour p of row i
-          const double Aip = A[i * m + p];
-          if (on) acc = fma(-Aip, (Y[i * k + c] - eps[i] * sc) / sqrt(D[i]), acc);
-        }
-        // -2 Z U: block i's weights of position p against every position q
-        const double* Wi = wblk + i * NPAIR;
-        for (int q = 0; q < PM; ++q) {
-          int row;
-          if (q == L) row = (int)i;
-          else if (q < cnt) row = nn[i * m + q];
-          else continue;
-          if (row < 0 || row > i) continue;  // invalid lists are reported by the row kernel
-          const double wpq = Wi[p >= q ? pair_index<PM>(p, q) : pair_index<PM>(q, p)];
-          if (on) acc = fma(-2.0 * wpq, U[(int64_t)row * k + c], acc);
-        }
+        const int64_t iq = i * m + en.y;
+        acc = fma(-A[iq], Phi[i * k + c], acc);
+        acc = fma(-btil[iq], alpha[i * k + c], acc);
       }
-      if (on) GU[r * k + c] = acc;
+      GU[r * k + c] = acc;
     }
   }
 }
@@ -538,7 +538,6 @@ vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, 
   const double* LM = reinterpret_cast<const double*>(vb + V.M);   // Cholesky factor of M
   const double* v = reinterpret_cast<const double*>(vb + V.v);    // W^T e
   const DevTheta th = dev_theta_vif(theta);
-  const int pm = padded_pm(m + 1);
   const int64_t gridw = std::min<int64_t>((n + 7) / 8, 65535);  // 8 warps per block of 256
 
   // M^{-1} = L_M^{-T} L_M^{-1}
@@ -560,7 +559,7 @@ vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, 
   }
   adj_kernel<<<(unsigned)gridw, 256, 0, st>>>(n, m, k, nn, nn_cnt, P(G.Y), U, D, P(G.eps), P(G.beta), P(G.qd),
                                               P(G.abar), P(G.dbar));
-  // residual-block pass (covariance part of the gradient, block weights out)
+  // residual-block pass: covariance part of the gradient, b~ out
   {
     LagD* lagd = reinterpret_cast<LagD*>(base + L.lagd);
     LagF* lagf = reinterpret_cast<LagF*>(base + L.lagf);
@@ -582,7 +581,7 @@ vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, 
     g.gram_d = reinterpret_cast<const double*>(vb + V.gram);
     g.abar = P(G.abar);
     g.dbar = P(G.dbar);
-    g.wblk = P(G.wblk);
+    g.btil = P(G.btil);
     apply_launch_shape(g, 0, VST_FP64, nu, m + 1);
     int64_t w = 0;
     cudaError_t e = launch_rows(false, nu, m + 1, kModeVifAdj, g, st, &w);
@@ -590,7 +589,9 @@ vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, 
     if (w > kMaxPartialWarps) return fail(VST_EINTERNAL, "too many warps");
     launch_reduce_partials(g.partial, w, g.partial, 0, 0.0, P(G.grows) + 5, P(G.grows), st);
   }
-  // reverse index and G_U
+  // Phi and alpha per row, then G_U through the reverse index
+  phi_kernel<<<(unsigned)gridw, 256, 0, st>>>(n, m, k, nn, nn_cnt, D, P(G.dbar), P(G.eps), P(G.svec), WE,
+                                              P(G.btil), U, P(G.Y), P(G.H));
   {
     int64_t* off = reinterpret_cast<int64_t*>(gb + G.roff);
     int32_t* cur = reinterpret_cast<int32_t*>(gb + G.rcur);
@@ -605,15 +606,9 @@ vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, 
     rscan_blocks_kernel<<<nb, 1024, 0, st>>>(off, n + 1, bsum);
     rscan_sums_kernel<<<1, 32, 0, st>>>(bsum, nb);
     rscan_add_kernel<<<nb, 1024, 0, st>>>(off, n + 1, bsum);
-    rfill_kernel<<<g1, 256, 0, st>>>(n, m, pm - 1, nn, nn_cnt, off, cur, ent);
+    rfill_kernel<<<g1, 256, 0, st>>>(n, m, nn, nn_cnt, off, cur, ent);
     rsort_kernel<<<g1, 256, 0, st>>>(n, off, ent);
-    const unsigned g2 = (unsigned)std::min<int64_t>((n + 3) / 4, 65535);
-    switch (pm) {
-      case 8: gu_kernel<8><<<g2, 128, 0, st>>>(n, m, k, nn, nn_cnt, off, ent, A, D, P(G.Y), P(G.eps), P(G.svec), U, P(G.wblk), P(G.GU)); break;
-      case 16: gu_kernel<16><<<g2, 128, 0, st>>>(n, m, k, nn, nn_cnt, off, ent, A, D, P(G.Y), P(G.eps), P(G.svec), U, P(G.wblk), P(G.GU)); break;
-      case 24: gu_kernel<24><<<g2, 128, 0, st>>>(n, m, k, nn, nn_cnt, off, ent, A, D, P(G.Y), P(G.eps), P(G.svec), U, P(G.wblk), P(G.GU)); break;
-      default: gu_kernel<32><<<g2, 128, 0, st>>>(n, m, k, nn, nn_cnt, off, ent, A, D, P(G.Y), P(G.eps), P(G.svec), U, P(G.wblk), P(G.GU));
-    }
+    gu_kernel<<<(unsigned)gridw, 256, 0, st>>>(n, m, k, off, ent, A, P(G.btil), P(G.Y), P(G.H), P(G.GU));
   }
   // H = G_U L^{-1}; term1 = <H, dSigma_nk>; J = H^T U
   gemm_nn(P(G.GU), k, X, k, P(G.H), k, n, k, k, true, st);
