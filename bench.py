@@ -324,6 +324,7 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
     ws = vst.Workspace(nv, w.m, k, device=dev)
     knn_ms = timed(lambda: vst.vif_build_neighbors(xy, t, th, w.m, ws=ws, inducing=ind), 1)
     nn, cnt = vst.vif_build_neighbors(xy, t, th, w.m, ws=ws, inducing=ind)
+    knn_info = vst.vst_workspace_status(ws)
     t64 = timed(lambda: vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.FP64, ws=ws, inducing=ind), 2)
     v64 = vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.FP64, ws=ws, inducing=ind).item()
     tmx = timed(lambda: vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED, ws=ws, inducing=ind), 3)
@@ -340,6 +341,7 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
     vg, gg = vst.vecchia_nll_grad(xy, t, th, w.m, nn, cnt, y, precision=vst.FP64, ws=wsg, inducing=ind)
     vst.vst_workspace_status(wsg)
     out["sub"] = {"n": nv, "k": k, "m": w.m, "knn_ms": knn_ms, "knn_queries_per_s": nv / (knn_ms * 1e-3),
+                  "knn_brute_force_rows": knn_info["n_fallback"], "knn_tie_rows": knn_info["n_tie"],
                   "nll_fp64_ms": t64, "nll_mixed_ms": tmx, "dnll_per_n": abs(vmx - v64) / nv,
                   "nll_mixed_bf16x3_ms": t3, "dnll_per_n_bf16x3": abs(v3 - v64) / nv,
                   "nll_grad_fp64_ms": tg, "nll_grad_fp64_evals_per_s": 1e3 / tg,

@@ -107,7 +107,8 @@ typedef struct {
   int32_t status;        /* vst_status of the last call that used the workspace */
   int32_t reserved;
   int64_t bad_row;       /* first offending row, or -1 */
-  int64_t n_fallback;    /* VST_MIXED: rows redone in FP64 */
+  int64_t n_fallback;    /* VST_MIXED: rows redone in FP64; vif_build_neighbors with
+                            inducing points: rows searched by FP64 brute force */
   int64_t n_tie;         /* vif_build_neighbors: rows with a cut-off tie */
 } vst_ws_info;
 

@@ -683,9 +683,7 @@ extern "C" vst_status vif_build_neighbors(const vst_points* pts, const vst_theta
     return e == cudaSuccess ? VST_OK : cuda_fail(e, "memset");
   }
   if (kind > 0) {
-    const WsLayout LV = ws_layout(n, m, kind);
-    return vif_knn(pts, theta, m, ind, nu_code(theta->nu), nn, nn_cnt, tie_rows, tie_cap, base + LV.vif,
-                   vif_layout(n, m, kind), hdr, st);
+    return vif_knn(pts, theta, m, ind, nu_code(theta->nu), nn, nn_cnt, tie_rows, tie_cap, base, hdr, st);
   }
   return plain_knn(pts->xy, pts->t, n, theta, m, nn, nn_cnt, tie_rows, tie_cap, base, L, hdr, n, 0, st);
 }

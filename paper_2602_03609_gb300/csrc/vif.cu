@@ -18,7 +18,6 @@
 //   trinv_kernel         L^{-1}, FP64, one warp per column
 //   ugemm_kernel<T>      U = Sigma_nk L^{-T} (tiled; Sigma_nk evaluated on the fly)
 //   rdiag_kernel<T>      r_i = sigma1^2 - ||U_i||^2
-//   vif_knn_kernel       residual-correlation kNN, FP64 brute force
 //   gram64_kernel        FP64: per-row U_p . U_q over the local block (fed to the row kernel)
 //   gram_delta_kernel    mixed: per-row U_p . U_q, accumulated without cancellation
 //   wvec_kernel<T>       rows of [W e] and sum log D_i
@@ -41,15 +40,6 @@ vst_status cuda_fail(cudaError_t e, const char* where);
 void launch_init_header(WsHeader* h, cudaStream_t st);
 void launch_lag_table(const DevTheta& th, LagD* d, LagF* f, cudaStream_t st);
 void apply_launch_shape(RowArgs& g, int batched, int precision, int nu, int pm);
-
-// ---------------------------------------------------------------------------
-// covariance of Eq. (2) for one pair, FP64 (any lag)
-template <int NU>
-__device__ __forceinline__ double cov64(const DevTheta& th, double dx, double dy, double u) {
-  const LagD f = lag_factors(th, u);
-  const double x = f.G * sqrt(dx * dx + dy * dy);
-  return f.P * matern_M<NU, double>(x, exp(-x));
-}
 
 // 16-byte read-only vector load of VEC consecutive values
 template <typename T, int VEC>
@@ -364,85 +354,6 @@ __global__ void rdiag_kernel(const T* U, int64_t n, int k, double s1, double* r)
     }
     s = warp_sum(s);
     if (lane == 0) r[i] = s1 - s;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// residual-correlation kNN, FP64 brute force over all predecessors
-struct VifKnnArgs {
-  const double* xy;
-  const double* t;
-  int64_t n;
-  int m;
-  int k;
-  DevTheta th;
-  const double* U;  // FP64 [n][k]
-  const double* r;  // [n]
-  int32_t* nn;
-  int32_t* nn_cnt;
-  int64_t* tie_rows;
-  int64_t tie_cap;
-  WsHeader* hdr;
-};
-
-template <int NU, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) vif_knn_kernel(VifKnnArgs A) {
-  extern __shared__ double ui_raw[];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  double* ui = ui_raw + (int64_t)wib * A.k;
-  const int64_t warp = (int64_t)blockIdx.x * WARPS + wib;
-  const int64_t total = (int64_t)gridDim.x * WARPS;
-  const int K = A.m + 1;
-  const double NEG = -1.0e300;
-  const double tiny = 1e-12 * A.th.sigma1sq;
-  for (int64_t i = warp; i < A.n; i += total) {
-    for (int c = lane; c < A.k; c += 32) ui[c] = A.U[i * A.k + c];
-    __syncwarp();
-    const double xi = A.xy[2 * i], yi = A.xy[2 * i + 1], ti = A.t[i], ri = A.r[i];
-    double lr = NEG;
-    int lid = INT_MAX, count = 0;
-    double thr = NEG;
-    for (int64_t j0 = 0; j0 < i; j0 += 32) {
-      const int64_t j = j0 + lane;
-      double rho = NEG;
-      if (j < i) {
-        const double* uj = A.U + j * A.k;
-        double dot = 0.0;
-        for (int c = 0; c < A.k; ++c) dot = fma(ui[c], uj[c], dot);
-        const double R = cov64<NU>(A.th, xi - A.xy[2 * j], yi - A.xy[2 * j + 1], ti - A.t[j]) - dot;
-        const double rj = A.r[j];
-        rho = (ri > tiny && rj > tiny) ? fabs(R) / sqrt(ri * rj) : 0.0;
-      }
-      unsigned mm = __ballot_sync(kFull, j < i && (count < K || rho >= thr));
-      while (mm) {
-        const int src = __ffs(mm) - 1;
-        mm &= mm - 1;
-        const double cr = __shfl_sync(kFull, rho, src);
-        const int cj = (int)(j0 + src);
-        if (count >= K && cr < thr) continue;
-        const bool better = lane < count && (lr > cr || (lr == cr && lid < cj));
-        const int p = __popc(__ballot_sync(kFull, better));
-        if (p >= K) continue;
-        const double ur = __shfl_up_sync(kFull, lr, 1);
-        const int uid = __shfl_up_sync(kFull, lid, 1);
-        if (lane > p) { lr = ur; lid = uid; }
-        if (lane == p) { lr = cr; lid = cj; }
-        count = min(count + 1, K);
-        if (count >= K) thr = __shfl_sync(kFull, lr, K - 1);
-      }
-    }
-    const int cnt = min(count, A.m);
-    if (lane < A.m) A.nn[i * A.m + lane] = lane < cnt ? lid : -1;
-    if (lane == 0) A.nn_cnt[i] = cnt;
-    if (count == K && A.m > 0) {
-      const double rm = __shfl_sync(kFull, lr, A.m - 1);
-      const double rm1 = __shfl_sync(kFull, lr, A.m);
-      if (lane == 0 && (rm - rm1) <= 1e-12 * fabs(rm)) {
-        const unsigned long long slot = atomicAdd(&A.hdr->n_tie, 1ull);
-        if (A.tie_rows && (int64_t)slot < A.tie_cap) A.tie_rows[slot] = i;
-      }
-    }
-    __syncwarp();
   }
 }
 
@@ -954,44 +865,6 @@ vst_status vif_lowrank(const vst_points* pts, const vst_theta* theta, const vst_
                        int precision, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
   if (precision == VST_FP64) return lowrank_T<double>(pts, theta, ind, nu, 0, vbase, V, hdr, st);
   return lowrank_T<float>(pts, theta, ind, nu, precision == VST_MIXED_BF16X3 ? 3 : 6, vbase, V, hdr, st);
-}
-
-vst_status vif_knn(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
-                   int32_t* nn, int32_t* nn_cnt, int64_t* tie_rows, int64_t tie_cap, char* vbase,
-                   const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
-  vst_status s = vif_lowrank(pts, theta, ind, nu, VST_FP64, vbase, V, hdr, st);
-  if (s != VST_OK) return s;
-  VifKnnArgs A{};
-  A.xy = pts->xy;
-  A.t = pts->t;
-  A.n = pts->n;
-  A.m = m;
-  A.k = (int)ind->k;
-  A.th = dev_theta_vif(theta);
-  A.U = reinterpret_cast<const double*>(vbase + V.U);
-  A.r = reinterpret_cast<const double*>(vbase + V.r);
-  A.nn = nn;
-  A.nn_cnt = nn_cnt;
-  A.tie_rows = tie_rows;
-  A.tie_cap = tie_rows ? tie_cap : 0;
-  A.hdr = hdr;
-  constexpr int W = 4;
-  const size_t smem = sizeof(double) * A.k * W;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  auto launch = [&](auto kern) {
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    int per = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, W * 32, smem);
-    ProfileScope ps(kProfKnn, st);
-    kern<<<std::max(1, per) * sms, W * 32, smem, st>>>(A);
-  };
-  if (nu == 0) launch(vif_knn_kernel<0, W>);
-  else if (nu == 1) launch(vif_knn_kernel<1, W>);
-  else launch(vif_knn_kernel<2, W>);
-  const cudaError_t e = cudaGetLastError();
-  return e == cudaSuccess ? VST_OK : cuda_fail(e, "VIF knn kernel");
 }
 
 // FP64: gram = U_p . U_q;  mixed: gram = U_p . U_q - sigma1^2 (see gram_delta_kernel)

@@ -11,6 +11,14 @@ namespace vst {
 DevTheta dev_theta(const vst_theta* th);
 inline DevTheta dev_theta_vif(const vst_theta* th) { return dev_theta(th); }
 
+// covariance of Eq. (2) for one pair, FP64 (any lag)
+template <int NU>
+__device__ __forceinline__ double cov64(const DevTheta& th, double dx, double dy, double u) {
+  const LagD f = lag_factors(th, u);
+  const double x = f.G * sqrt(dx * dx + dy * dy);
+  return f.P * matern_M<NU, double>(x, exp(-x));
+}
+
 // the same in FP32 for the mixed form (psi powers through log2/exp2)
 template <int NU>
 __device__ __forceinline__ float cov32(const DevTheta& th, float dx, float dy, float u) {
@@ -32,9 +40,12 @@ __device__ __forceinline__ float cov32(const DevTheta& th, float dx, float dy, f
 vst_status lowrank_tc(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu,
                       int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st);
 
+// residual-correlation neighbours (vif_knn.cu); base: the whole workspace
 vst_status vif_knn(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
-                   int32_t* nn, int32_t* nn_cnt, int64_t* tie_rows, int64_t tie_cap, char* vbase,
-                   const VifLayout& V, WsHeader* hdr, cudaStream_t st);
+                   int32_t* nn, int32_t* nn_cnt, int64_t* tie_rows, int64_t tie_cap, char* base,
+                   WsHeader* hdr, cudaStream_t st);
+vst_status vif_lowrank(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu,
+                       int precision, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st);
 vst_status vif_factor(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
                       const int32_t* nn, const int32_t* nn_cnt, int precision, double* A, double* D, void* ws,
                       cudaStream_t st);

@@ -28,12 +28,16 @@ struct VifLayout {
   size_t rpart;       // per (row, column tile) sums of U_ic^2 from the GEMM epilogue
   size_t dpart;       // day-range partials
   size_t lagdf;       // per-lag (P, G) as double-floats (mixed residual covariance)
+  // residual-correlation neighbour search: per-row threshold, candidate
+  // lists and counts, rows left to the brute-force search and their count
+  size_t tau, cand, ccount, fbrows, fbcount;
   size_t total;
 };
 
 // inducing-point dimension padded for the tensor-core GEMM (N tiles of 256)
 inline int64_t vif_kp(int64_t k) { return (k + 255) / 256 * 256; }
 constexpr int kVifMaxParts = 3;  // BF16 parts per operand value
+constexpr int kVifCand = 2048;   // candidate slots per row of the filtered neighbour search
 
 inline size_t align256(size_t v);
 
@@ -69,6 +73,11 @@ inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
   L.rpart = take(sizeof(double) * nn * (kp / 128));
   L.dpart = take(sizeof(double) * 3 * kVifDayBlocks);
   L.lagdf = take(16 * (size_t)kLagTab);
+  L.tau = take(16 * nn);
+  L.cand = take(sizeof(int32_t) * nn * kVifCand);
+  L.ccount = take(sizeof(int32_t) * nn);
+  L.fbrows = take(sizeof(int32_t) * nn);
+  L.fbcount = take(256);
   L.total = off;
   return L;
 }

@@ -59,6 +59,25 @@ def test_vif_neighbours_factor_nll(env, k, m, order):
     assert abs(vm.item() - v_o) / n <= 1e-6
 
 
+def test_vif_neighbours_short_range_uses_brute_force_rows(env):
+    """Residual correlations all tiny (effective ranges far below the point
+    spacing): the FP32 filter cannot separate them, every predecessor stays
+    a candidate, rows past the candidate capacity (256) are searched by the
+    FP64 brute force and the rest ranked from their full candidate lists."""
+    torch, vst = env
+    xy, t, th, xyk, tk, y = problem(40, 8, 16, seed=3, rs=0.01, rt=0.05)
+    n = t.shape[0]
+    assert n > 300
+    m = 6
+    U, r = ovif.lowrank(xy, t, xyk, tk, th)
+    nn_o, cnt_o, rm, rm1 = ovif.knn(xy, t, th, U, r, m)
+    xy_d, t_d, xyk_d, tk_d = dev(torch, xy, t, xyk, tk)
+    ws = vst.Workspace(n, m, 16)
+    nn_g, cnt_g = vst.vif_build_neighbors(xy_d, t_d, th, m, ws=ws, inducing=(xyk_d, tk_d))
+    vst.vst_workspace_status(ws)
+    check_neighbours(nn_g.cpu().numpy(), cnt_g.cpu().numpy(), nn_o, cnt_o, rm, rm1)
+
+
 def test_vif_m0_is_fitc(env):
     torch, vst = env
     xy, t, th, xyk, tk, y = problem(30, 6, 16, seed=4)
