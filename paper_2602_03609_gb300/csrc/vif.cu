@@ -16,7 +16,7 @@
 //                        block in one warp, panel rows by forward substitution,
 //                        tiled trailing update
 //   trinv_kernel         L^{-1}, FP64, one warp per column
-//   ugemm_kernel<T>      U = Sigma_nk L^{-T} (tiled; Sigma_nk evaluated on the fly)
+//   snk64_kernel, gemm_nt U = Sigma_nk L^{-T} (FP64: Sigma_nk once, then the dense tile GEMM)
 //   rdiag_kernel<T>      r_i = sigma1^2 - ||U_i||^2
 //   gram64_kernel        FP64: per-row U_p . U_q over the local block (fed to the row kernel)
 //   gram_delta_kernel    mixed: per-row U_p . U_q, accumulated without cancellation
@@ -28,6 +28,7 @@
 #include <climits>
 #include <cmath>
 
+#include "dgemm.cuh"
 #include "kernels.h"
 #include "profile.h"
 #include "vif.h"
@@ -262,82 +263,15 @@ __global__ void trinv_kernel(const double* L, int k, double* X) {
 }
 
 // ---------------------------------------------------------------------------
-// FP64 form: U[i][c] = sum_{p <= c} S[i][p] X[c][p], S[i][p] = C(x_i, z_p),
-// X = L^{-1}.  64 x 64 output tile per block of 256 threads, 4 x 4 per
-// thread, K step 16, Sigma_nk evaluated on the fly.  (The mixed form uses the
-// tensor-core GEMM of vif_tc.cu.)
+// FP64 form: Sigma_nk[i][p] = C(x_i, z_p), one thread per entry
 template <int NU>
-__global__ void __launch_bounds__(256) ugemm_kernel(const double* xy, const double* t, int64_t n,
-                                                    const double* xyk, const double* tk, int k, DevTheta th,
-                                                    const double* X, double* U) {
-  constexpr int BM = 64, BN = 64, BK = 16;
-  __shared__ double As[BK][BM + 2];
-  __shared__ double Bs[BK][BN + 2];
-  __shared__ double rx[BM], ry[BM], rt[BM];
-  __shared__ double zx[BK], zy[BK], zt[BK];
-  const int64_t i0 = (int64_t)blockIdx.y * BM;
-  const int c0 = blockIdx.x * BN;
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  if (tid < BM) {
-    const int64_t i = i0 + tid;
-    rx[tid] = i < n ? xy[2 * i] : 0.0;
-    ry[tid] = i < n ? xy[2 * i + 1] : 0.0;
-    rt[tid] = i < n ? t[i] : 0.0;
-  }
-  double acc[4][4];
-#pragma unroll
-  for (int a = 0; a < 4; ++a)
-#pragma unroll
-    for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
-  const int pend = k < c0 + BN ? k : c0 + BN;  // X[c][p] = 0 for p > c
-  for (int p0 = 0; p0 < pend; p0 += BK) {
-    __syncthreads();
-    if (tid < BK) {
-      const int p = p0 + tid;
-      zx[tid] = p < k ? xyk[2 * p] : 0.0;
-      zy[tid] = p < k ? xyk[2 * p + 1] : 0.0;
-      zt[tid] = p < k ? tk[p] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = tid + q * 256;
-      const int ii = e & (BM - 1), kk = e >> 6;
-      double v = 0.0;
-      if (i0 + ii < n && p0 + kk < k) v = cov64<NU>(th, rx[ii] - zx[kk], ry[ii] - zy[kk], rt[ii] - zt[kk]);
-      As[kk][ii] = v;
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int e = tid + q * 256;
-      const int kk = e & (BK - 1), cc = e >> 4;
-      const int c = c0 + cc, p = p0 + kk;
-      Bs[kk][cc] = (c < k && p < k && p <= c) ? X[(int64_t)c * k + p] : 0.0;
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < BK; ++kk) {
-      double a[4], b[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        a[u] = As[kk][ty * 4 + u];
-        b[u] = Bs[kk][tx * 4 + u];
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(a[u], b[v], acc[u][v]);
-    }
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int64_t i = i0 + ty * 4 + u;
-    if (i >= n) continue;
-#pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int c = c0 + tx * 4 + v;
-      if (c < k) U[i * k + c] = acc[u][v];
-    }
+__global__ void snk64_kernel(const double* xy, const double* t, int64_t n, const double* xyk, const double* tk,
+                             int k, DevTheta th, double* S) {
+  const int64_t total = n * k;
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = q / k;
+    const int p = (int)(q - i * k);
+    S[q] = cov64<NU>(th, xy[2 * i] - xyk[2 * p], xy[2 * i + 1] - xyk[2 * p + 1], t[i] - tk[p]);
   }
 }
 
@@ -841,11 +775,15 @@ static vst_status lowrank_T(const vst_points* pts, const vst_theta* theta, const
     day_range_kernel<<<1, 256, 0, st>>>(dpart, dblocks, n, dinfo);
     day_lag_kernel<<<(int)((kVifMaxDays * (int64_t)k + 255) / 256), 256, 0, st>>>(ind->t, k, th, dinfo, dtab);
     if constexpr (std::is_same<T, double>::value) {
-      const dim3 grid((k + 63) / 64, (unsigned)((n + 63) / 64));
+      // Sigma_nk once (into the [W e] buffer, unused until the Woodbury
+      // step), then U = Sigma_nk X^T with X = L^{-1} lower triangular
+      double* Snk = reinterpret_cast<double*>(vbase + V.WE);
+      const unsigned gs = (unsigned)std::min<int64_t>((n * k + 255) / 256, 65535 * 16);
+      if (nu == 0) snk64_kernel<0><<<gs, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, Snk);
+      else if (nu == 1) snk64_kernel<1><<<gs, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, Snk);
+      else snk64_kernel<2><<<gs, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, Snk);
       ProfileScope ps(kProfVifGemm, st);
-      if (nu == 0) ugemm_kernel<0><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U);
-      else if (nu == 1) ugemm_kernel<1><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U);
-      else ugemm_kernel<2><<<grid, 256, 0, st>>>(pts->xy, pts->t, n, ind->xy, ind->t, k, th, X, U);
+      gemm_nt(Snk, k, X, k, U, k, n, k, k, true, st);
     } else {
       (void)dtab;
       s = lowrank_tc(pts, theta, ind, nu, split_terms, vbase, V, hdr, st);
