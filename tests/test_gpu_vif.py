@@ -78,6 +78,25 @@ def test_vif_neighbours_short_range_uses_brute_force_rows(env):
     check_neighbours(nn_g.cpu().numpy(), cnt_g.cpu().numpy(), nn_o, cnt_o, rm, rm1)
 
 
+def test_vif_neighbours_non_integer_times(env):
+    """Times that are not whole days: the FP32 tile filter cannot bound the
+    lag rounding and keeps every pair of such tiles (rows beyond the
+    candidate capacity go through the second pass, which evaluates those
+    lags exactly in FP64)."""
+    torch, vst = env
+    xy, t, th, xyk, tk, y = problem(40, 8, 20, seed=8, order="random")
+    t = np.ascontiguousarray(t + 0.37 * si.stations_uniform(t.shape[0], 21)[:, 0])
+    n = t.shape[0]
+    m = 7
+    U, r = ovif.lowrank(xy, t, xyk, tk, th)
+    nn_o, cnt_o, rm, rm1 = ovif.knn(xy, t, th, U, r, m)
+    xy_d, t_d, xyk_d, tk_d = dev(torch, xy, t, xyk, tk)
+    ws = vst.Workspace(n, m, 20)
+    nn_g, cnt_g = vst.vif_build_neighbors(xy_d, t_d, th, m, ws=ws, inducing=(xyk_d, tk_d))
+    vst.vst_workspace_status(ws)
+    check_neighbours(nn_g.cpu().numpy(), cnt_g.cpu().numpy(), nn_o, cnt_o, rm, rm1)
+
+
 def test_vif_m0_is_fitc(env):
     torch, vst = env
     xy, t, th, xyk, tk, y = problem(30, 6, 16, seed=4)
