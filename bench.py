@@ -340,12 +340,19 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
                                             inducing=ind), 2)
     vg, gg = vst.vecchia_nll_grad(xy, t, th, w.m, nn, cnt, y, precision=vst.FP64, ws=wsg, inducing=ind)
     vst.vst_workspace_status(wsg)
+    v64g, g64 = vg.item(), gg.cpu().numpy()
+    tgm = timed(lambda: vst.vecchia_nll_grad(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED, ws=wsg,
+                                             inducing=ind), 3)
+    _, ggm = vst.vecchia_nll_grad(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED, ws=wsg, inducing=ind)
+    vst.vst_workspace_status(wsg)
+    gm = ggm.cpu().numpy()
     out["sub"] = {"n": nv, "k": k, "m": w.m, "knn_ms": knn_ms, "knn_queries_per_s": nv / (knn_ms * 1e-3),
                   "knn_brute_force_rows": knn_info["n_fallback"], "knn_tie_rows": knn_info["n_tie"],
                   "nll_fp64_ms": t64, "nll_mixed_ms": tmx, "dnll_per_n": abs(vmx - v64) / nv,
                   "nll_mixed_bf16x3_ms": t3, "dnll_per_n_bf16x3": abs(v3 - v64) / nv,
                   "nll_grad_fp64_ms": tg, "nll_grad_fp64_evals_per_s": 1e3 / tg,
-                  "grad_nll_equals_nll": vg.item() == v64, "grad": [float(v) for v in gg.cpu()]}
+                  "grad_nll_equals_nll": v64g == v64, "grad": [float(v) for v in g64],
+                  "nll_grad_mixed_ms": tgm, "grad_mixed_abs_err_per_n": (np.abs(gm - g64) / nv).tolist()}
     del wsg, nn, cnt
     if not full:
         return out
@@ -359,7 +366,7 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
     sub = type(w)(name="sub", xy=w.xy[r], t=w.t[r], z=w.z[r], theta=w.theta, m=w.m, order=None)
     xyk, tk = si.inducing_points(sub, k, seed=11, lloyd_iters=10)
     ind = (torch.from_numpy(xyk).to(dev), torch.from_numpy(tk).to(dev))
-    ws = vst.Workspace(w.n, w.m, k, device=dev)
+    ws = vst.Workspace(w.n, w.m, k, device=dev, vif_grad=True)
     full = {"n": w.n, "k": k, "m": w.m}
     for name, prec, terms in (("mixed", vst.MIXED, 6), ("mixed_bf16x3", vst.MIXED_BF16X3, 3)):
         f = (lambda p=prec: vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=p, ws=ws, inducing=ind))
@@ -379,6 +386,10 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
                                           "peak": BF16_PEAK, "unit": "TFLOP/s",
                                           "frac": flops / (gemm_ms * 1e-3) / 1e12 / BF16_PEAK,
                                           "flops_per_launch": flops, "peak_note": "measured cuBLAS bf16 (burst)"}}
+    # NLL + gradient, mixed (FP32 low rank and n x k products, FP64 reductions)
+    fg = (lambda: vst.vecchia_nll_grad(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED, ws=ws, inducing=ind))
+    full["nll_grad_mixed_ms"] = timed(fg, 2)
+    vst.vst_workspace_status(ws)
     full["nll_mixed_ms"] = full["mixed"]["nll_ms"]
     full["value"] = full["mixed"]["value"]
     full["unit"] = "VIF NLL evals/s"

@@ -184,11 +184,14 @@ vst_status vecchia_nll(const vst_points* pts, const vst_theta* theta, int m,
  * neighbour sets are held fixed.  grad: 5 FP64 device values.  The factor is
  * recomputed, not stored.
  * VIF (ind != NULL, k > 0; the likelihood of Sect. 4.3 as in vecchia_nll,
- * inducing points held fixed): FP64 only (precision VST_FP64, else
- * VST_EINVAL); workspace vst_workspace_size_vif_grad(n, m, k) bytes.  The
- * gradient is the exact derivative of the VIF NLL that vecchia_nll returns,
- * by an adjoint pass through the Woodbury terms, the residual blocks and the
- * low-rank part U = Sigma_nk L^{-T} (L L^T = Sigma_kk). */
+ * inducing points held fixed): workspace vst_workspace_size_vif_grad(n, m, k)
+ * bytes.  The gradient is the derivative of the VIF NLL, by an adjoint pass
+ * through the Woodbury terms, the residual blocks and the low-rank part
+ * U = Sigma_nk L^{-T} (L L^T = Sigma_kk); nll is the value vecchia_nll returns
+ * for the same precision.  VST_FP64: FP64 throughout.  VST_MIXED /
+ * VST_MIXED_BF16X3: the mixed NLL's FP32 low rank, W and residual Gram, FP32
+ * n x k products (double-float chunk sums), FP64 reductions over the points
+ * and FP64 k x k algebra. */
 vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m,
                             const vst_inducing* ind, const int32_t* nn, const int32_t* nn_cnt,
                             const double* y, int precision, double* nll, double* grad,

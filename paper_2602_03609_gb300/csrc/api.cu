@@ -372,13 +372,12 @@ vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m
   if (!valid_precision(precision)) return fail(VST_EINVAL, "bad precision %d", precision);
   if (!nll || !grad || (pts->n > 0 && !y)) return fail(VST_EINVAL, "y/nll/grad is NULL");
   if (k > 0) {
-    if (precision != VST_FP64) return fail(VST_EINVAL, "the VIF gradient is computed in FP64 only (precision 0)");
     const size_t need = vst_workspace_size_vif_grad(pts->n, m, k);
     if (ws_bytes < need) return fail(VST_ENOMEM, "workspace has %zu bytes, %zu needed", ws_bytes, need);
     const WsLayout L = ws_layout(pts->n, m, k);
     launch_init_header(reinterpret_cast<WsHeader*>(static_cast<char*>(ws) + L.hdr), (cudaStream_t)stream);
-    return vif_nll_grad64(pts, theta, m, ind, nu_code(theta->nu), nn, nn_cnt, y, nll, grad, ws,
-                          (cudaStream_t)stream);
+    return vif_nll_grad(pts, theta, m, ind, nu_code(theta->nu), nn, nn_cnt, y, precision, nll, grad, ws,
+                        (cudaStream_t)stream);
   }
   return run_rows(pts, theta, m, nn, nn_cnt, y, plain_precision(precision), kModeNllGrad, nll, grad, nullptr,
                   nullptr, ws, (cudaStream_t)stream);

@@ -53,11 +53,11 @@ vst_status vif_nll(const vst_points* pts, const vst_theta* theta, int m, const v
                    const int32_t* nn, const int32_t* nn_cnt, const double* y, int precision, double* nll, void* ws,
                    cudaStream_t st);
 
-// VIF NLL and its gradient in FP64 (vif_grad.cu); the workspace is
+// VIF NLL and its gradient (vif_grad.cu), FP64 or mixed; the workspace is
 // ws_layout(n, m, k) followed by vif_grad_extra_bytes(n, m, k) bytes.
 size_t vif_grad_extra_bytes(int64_t n, int m, int64_t k);
-vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
-                          const int32_t* nn, const int32_t* nn_cnt, const double* y, double* nll, double* grad,
-                          void* ws, cudaStream_t st);
+vst_status vif_nll_grad(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
+                        const int32_t* nn, const int32_t* nn_cnt, const double* y, int precision, double* nll,
+                        double* grad, void* ws, cudaStream_t st);
 
 }  // namespace vst

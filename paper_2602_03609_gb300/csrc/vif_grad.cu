@@ -33,6 +33,7 @@
 // lower triangle halved on each side and the diagonal halved.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "dgemm.cuh"
 #include "kernels.h"
@@ -56,7 +57,7 @@ namespace {
 constexpr int kChunks = kDgemmChunks;
 
 struct GradLayout {
-  size_t LinvM, Minv, Y, GU, H, abar, dbar, eps, beta, qd, wv, svec, spart, btil, roff, rcur, rent, bsum,
+  size_t LinvM, Minv, MinvF, XF, Y, GU, H, abar, dbar, eps, beta, qd, wv, svec, spart, btil, roff, rcur, rent, bsum,
       t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, total;
 };
 
@@ -72,6 +73,8 @@ GradLayout grad_layout(int64_t n, int m, int64_t k) {
   const size_t mm = (size_t)std::max(m, 1);
   G.LinvM = take(8 * kk * kk);
   G.Minv = take(8 * kk * kk);
+  G.MinvF = take(4 * kk * kk);
+  G.XF = take(4 * kk * kk);
   G.Y = take(8 * nn * kk);
   G.GU = take(8 * nn * kk);
   G.H = take(8 * nn * kk);
@@ -101,6 +104,11 @@ GradLayout grad_layout(int64_t n, int m, int64_t k) {
   return G;
 }
 
+__global__ void narrow_kernel(const double* src, int64_t count, float* dst) {
+  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x)
+    dst[q] = (float)src[q];
+}
+
 // y = A x for a k x k row-major A
 __global__ void gemv_kernel(const double* A, const double* x, int k, double* y) {
   const int lane = threadIdx.x & 31;
@@ -112,27 +120,30 @@ __global__ void gemv_kernel(const double* A, const double* x, int k, double* y) 
   if (lane == 0) y[r] = s;
 }
 
-// per row: eps = e - Y v, beta = y - U wv, qd = Y . W
-__global__ void rowvec_kernel(int64_t n, int k, const double* Y, const double* WE, const double* U, const double* v,
+// per row: eps = e - Y v, beta = y - U wv, qd = Y . W (T: the storage type of
+// Y, W and U; FP64 products and sums)
+template <typename T>
+__global__ void rowvec_kernel(int64_t n, int k, const T* Y, const T* WE, const T* U, const double* v,
                               const double* wv, const double* y, double* eps, double* beta, double* qd) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w; i < n; i += nw) {
     double a = 0.0, b = 0.0, c = 0.0;
-    const double* Yi = Y + i * k;
-    const double* Wi = WE + i * (int64_t)(k + 1);
-    const double* Ui = U + i * k;
+    const T* Yi = Y + i * k;
+    const T* Wi = WE + i * (int64_t)(k + 1);
+    const T* Ui = U + i * k;
     for (int p = lane; p < k; p += 32) {
-      a = fma(Yi[p], v[p], a);
-      b = fma(Ui[p], wv[p], b);
-      c = fma(Yi[p], Wi[p], c);
+      const double yp = (double)Yi[p];
+      a = fma(yp, v[p], a);
+      b = fma((double)Ui[p], wv[p], b);
+      c = fma(yp, (double)Wi[p], c);
     }
     a = warp_sum(a);
     b = warp_sum(b);
     c = warp_sum(c);
     if (lane == 0) {
-      eps[i] = Wi[k] - a;
+      eps[i] = (double)Wi[k] - a;
       beta[i] = y[i] - b;
       qd[i] = c;
     }
@@ -140,18 +151,21 @@ __global__ void rowvec_kernel(int64_t n, int k, const double* Y, const double* W
 }
 
 // s = W^T eps: per row chunk, partial column sums
-__global__ void wteps_kernel(int64_t n, int k, const double* WE, const double* eps, int64_t chunk, double* part) {
+template <typename T>
+__global__ void wteps_kernel(int64_t n, int k, const T* WE, const double* eps, int64_t chunk, double* part) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= k) return;
   const int64_t r0 = (int64_t)blockIdx.y * chunk, r1 = n < r0 + chunk ? n : r0 + chunk;
   double s = 0.0;
-  for (int64_t i = r0; i < r1; ++i) s = fma(WE[i * (int64_t)(k + 1) + c], eps[i], s);
+  for (int64_t i = r0; i < r1; ++i) s = fma((double)WE[i * (int64_t)(k + 1) + c], eps[i], s);
   part[(int64_t)blockIdx.y * k + c] = s;
 }
 
-// Abar and Dbar per row
-__global__ void adj_kernel(int64_t n, int m, int k, const int32_t* nn, const int32_t* nn_cnt, const double* Y,
-                           const double* U, const double* D, const double* eps, const double* beta,
+// Abar and Dbar per row (dot products: T products, summed in T per lane and
+// in FP64 across the lanes)
+template <typename T>
+__global__ void adj_kernel(int64_t n, int m, int k, const int32_t* nn, const int32_t* nn_cnt, const T* Y,
+                           const T* U, const double* D, const double* eps, const double* beta,
                            const double* qd, double* abar, double* dbar) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -159,16 +173,16 @@ __global__ void adj_kernel(int64_t n, int m, int k, const int32_t* nn, const int
   for (int64_t i = w; i < n; i += nw) {
     const int cnt = min(max(nn_cnt[i], 0), m);
     const double Di = D[i], sd = 1.0 / sqrt(Di);
-    const double* Yi = Y + i * k;
+    const T* Yi = Y + i * k;
     for (int q = 0; q < m; ++q) {
       double val = 0.0;
       if (q < cnt) {
         const int j = nn[i * m + q];
         if (j >= 0 && j < i) {
-          double s = 0.0;
-          const double* Uj = U + (int64_t)j * k;
-          for (int p = lane; p < k; p += 32) s = fma(Yi[p], Uj[p], s);
-          s = warp_sum(s);
+          T sl = T(0);
+          const T* Uj = U + (int64_t)j * k;
+          for (int p = lane; p < k; p += 32) sl = fma(Yi[p], Uj[p], sl);
+          const double s = warp_sum((double)sl);
           val = -(s + eps[i] * beta[j]) * sd;
         }
       }
@@ -240,50 +254,52 @@ __global__ void rsort_kernel(int64_t n, const int64_t* off, int2* ent) {
 // per row i: alpha_i = sqrt(D_i) W_i (into `alpha`), and Phi_i = F_i - 2 gamma_i
 // (in place over Y_i), F_i = (Y_i - eps_i s) / sqrt(D_i), gamma_i = Dbar_i
 // alpha_i + beta_i / 2, beta_i = sum_q b~_iq U_N(i)_q.  One warp per row.
+template <typename T>
 __global__ void __launch_bounds__(256) phi_kernel(int64_t n, int m, int k, const int32_t* nn,
                                                   const int32_t* nn_cnt, const double* D, const double* dbar,
-                                                  const double* eps, const double* svec, const double* WE,
-                                                  const double* btil, const double* U, double* Y,
-                                                  double* alpha) {
+                                                  const double* eps, const double* svec, const T* WE,
+                                                  const double* btil, const T* U, T* Y, T* alpha) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w; i < n; i += nw) {
     const int cnt = min(max(nn_cnt[i], 0), m);
     const double Di = D[i], sd = 1.0 / sqrt(Di), sq = sqrt(Di), db = dbar[i], ei = eps[i];
-    const double* Wi = WE + i * (int64_t)(k + 1);
+    const T* Wi = WE + i * (int64_t)(k + 1);
     for (int c = lane; c < k; c += 32) {
-      double be = 0.0;
+      T bt = T(0);
       for (int q = 0; q < cnt; ++q) {
         const int j = nn[i * m + q];
-        if (j >= 0 && j < i) be = fma(btil[i * m + q], U[(int64_t)j * k + c], be);
+        if (j >= 0 && j < i) bt = fma((T)btil[i * m + q], U[(int64_t)j * k + c], bt);
       }
-      const double al = sq * Wi[c];
-      const double F = (Y[i * k + c] - ei * svec[c]) * sd;
-      Y[i * k + c] = F - 2.0 * fma(db, al, 0.5 * be);
-      alpha[i * k + c] = al;
+      const double be = (double)bt;
+      const double al = sq * (double)Wi[c];
+      const double F = ((double)Y[i * k + c] - ei * svec[c]) * sd;
+      Y[i * k + c] = (T)(F - 2.0 * fma(db, al, 0.5 * be));
+      alpha[i * k + c] = (T)al;
     }
   }
 }
 
 // G_U[r] = Phi_r - sum over the reverse entries (i, q) of r of
 // (A_iq Phi_i + b~_iq alpha_i).  One warp per row, 32 columns at a time.
+template <typename T>
 __global__ void __launch_bounds__(256) gu_kernel(int64_t n, int m, int k, const int64_t* off, const int2* ent,
-                                                 const double* A, const double* btil, const double* Phi,
-                                                 const double* alpha, double* GU) {
+                                                 const double* A, const double* btil, const T* Phi,
+                                                 const T* alpha, T* GU) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = w; r < n; r += nw) {
     const int64_t a = off[r], b = off[r + 1];
     for (int c = lane; c < k; c += 32) {
-      double acc = Phi[r * k + c];
+      T acc = Phi[r * k + c];
       for (int64_t x = a; x < b; ++x) {
         const int2 en = ent[x];
         const int64_t i = en.x;
         const int64_t iq = i * m + en.y;
-        acc = fma(-A[iq], Phi[i * k + c], acc);
-        acc = fma(-btil[iq], alpha[i * k + c], acc);
+        acc = fma(-(T)A[iq], Phi[i * k + c], acc);
+        acc = fma(-(T)btil[iq], alpha[i * k + c], acc);
       }
       GU[r * k + c] = acc;
     }
@@ -305,9 +321,9 @@ __device__ __forceinline__ void cov_derivs(const DevTheta& th, double dx, double
 }
 
 // sum over (i, p) of H[i][p] dSigma_nk[i][p]/dtheta, per block partials
-template <int NU>
+template <int NU, typename T>
 __global__ void term1_kernel(int64_t n, int k, const double* xy, const double* t, const double* xyk,
-                             const double* tk, DevTheta th, const double* H, double* part) {
+                             const double* tk, DevTheta th, const T* H, double* part) {
   __shared__ double sh[4][256];
   double acc[4] = {0, 0, 0, 0};
   const int64_t total = n * k;
@@ -316,7 +332,7 @@ __global__ void term1_kernel(int64_t n, int k, const double* xy, const double* t
     const int p = (int)(q % k);
     double d[4];
     cov_derivs<NU>(th, xy[2 * i] - xyk[2 * p], xy[2 * i + 1] - xyk[2 * p + 1], t[i] - tk[p], d);
-    const double h = H[q];
+    const double h = (double)H[q];
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[j] = fma(h, d[j], acc[j]);
   }
@@ -388,14 +404,20 @@ __global__ void combine_kernel(const double* grows, const double* t1, int n1, co
 
 size_t vif_grad_extra_bytes(int64_t n, int m, int64_t k) { return grad_layout(n, m, k).total; }
 
-// VIF NLL and gradient, FP64.  The workspace is ws_layout(n, m, k) followed by
-// the gradient scratch (vif_grad_extra_bytes).
-vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
-                          const int32_t* nn, const int32_t* nn_cnt, const double* y, double* nll, double* grad,
-                          void* ws, cudaStream_t st) {
+// VIF NLL and gradient.  T = double: the FP64 NLL and FP64 throughout.
+// T = float: the mixed NLL (U, W and the residual Gram in FP32 from the
+// tensor-core path; A_i, D_i refined, M in FP64), the n x k products Y, G_U
+// and H in FP32 (FP32 products, double-float chunk sums), every n-long
+// reduction and the k x k algebra in FP64.  The workspace is ws_layout(n, m,
+// k) followed by the gradient scratch (vif_grad_extra_bytes).
+template <typename T>
+vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
+                          const int32_t* nn, const int32_t* nn_cnt, const double* y, int precision, double* nll,
+                          double* grad, void* ws, cudaStream_t st) {
+  constexpr bool F32 = std::is_same<T, float>::value;
   const int64_t n = pts->n;
   const int k = (int)ind->k;
-  vst_status s = vif_nll(pts, theta, m, ind, nu, nn, nn_cnt, y, VST_FP64, nll, ws, st);
+  vst_status s = vif_nll(pts, theta, m, ind, nu, nn, nn_cnt, y, precision, nll, ws, st);
   if (s != VST_OK) return s;
   if (n == 0) return cudaMemsetAsync(grad, 0, 5 * sizeof(double), st) == cudaSuccess ? VST_OK : VST_ECUDA;
   char* base = static_cast<char*>(ws);
@@ -406,16 +428,19 @@ vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, 
   const GradLayout G = grad_layout(n, m, k);
   WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
   auto P = [&](size_t o) { return reinterpret_cast<double*>(gb + o); };
+  auto PT = [&](size_t o) { return reinterpret_cast<T*>(gb + o); };
   const double* A = reinterpret_cast<const double*>(base + L.sA);
   const double* D = reinterpret_cast<const double*>(base + L.sD);
-  const double* U = reinterpret_cast<const double*>(vb + V.U);
+  const T* U = reinterpret_cast<const T*>(vb + V.U);
   const double* X = reinterpret_cast<const double*>(vb + V.X);   // L^{-1}
   const double* Lkk = reinterpret_cast<const double*>(vb + V.S);  // L (lower, in place)
-  const double* WE = reinterpret_cast<const double*>(vb + V.WE);
+  const T* WE = reinterpret_cast<const T*>(vb + V.WE);
   const double* LM = reinterpret_cast<const double*>(vb + V.M);   // Cholesky factor of M
   const double* v = reinterpret_cast<const double*>(vb + V.v);    // W^T e
   const DevTheta th = dev_theta_vif(theta);
   const int64_t gridw = std::min<int64_t>((n + 7) / 8, 65535);  // 8 warps per block of 256
+  const int64_t kk2 = (int64_t)k * k;
+  const unsigned gkk = (unsigned)std::min<int64_t>((kk2 + 255) / 256, 4096);
 
   // M^{-1} = L_M^{-T} L_M^{-1}
   {
@@ -425,18 +450,31 @@ vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, 
     trinv_kernel<<<(k + wpb - 1) / wpb, 32 * wpb, smem, st>>>(LM, k, P(G.LinvM));
     gemm_tn(P(G.LinvM), k, P(G.LinvM), k, k, k, k, false, P(G.Jpart), P(G.Minv), st);
   }
+  const T* MinvT;
+  const T* XT;
+  if constexpr (F32) {
+    narrow_kernel<<<gkk, 256, 0, st>>>(P(G.Minv), kk2, reinterpret_cast<float*>(gb + G.MinvF));
+    narrow_kernel<<<gkk, 256, 0, st>>>(X, kk2, reinterpret_cast<float*>(gb + G.XF));
+    MinvT = reinterpret_cast<const T*>(gb + G.MinvF);
+    XT = reinterpret_cast<const T*>(gb + G.XF);
+  } else {
+    MinvT = reinterpret_cast<const T*>(P(G.Minv));
+    XT = reinterpret_cast<const T*>(X);
+  }
   // Y = W M^{-1}; wv = M^{-1} v
-  gemm_nn(WE, k + 1, P(G.Minv), k, P(G.Y), k, n, k, k, false, st);
+  gemm_nn<T>(WE, k + 1, MinvT, k, PT(G.Y), k, n, k, k, false, st);
   gemv_kernel<<<(k * 32 + 255) / 256, 256, 0, st>>>(P(G.Minv), v, k, P(G.wv));
-  rowvec_kernel<<<(unsigned)gridw, 256, 0, st>>>(n, k, P(G.Y), WE, U, v, P(G.wv), y, P(G.eps), P(G.beta), P(G.qd));
+  rowvec_kernel<T><<<(unsigned)gridw, 256, 0, st>>>(n, k, PT(G.Y), WE, U, v, P(G.wv), y, P(G.eps), P(G.beta),
+                                                    P(G.qd));
   {
     const int64_t chunk = (n + kChunks - 1) / kChunks;
-    wteps_kernel<<<dim3((k + 255) / 256, kChunks), 256, 0, st>>>(n, k, WE, P(G.eps), chunk, P(G.spart));
+    wteps_kernel<T><<<dim3((k + 255) / 256, kChunks), 256, 0, st>>>(n, k, WE, P(G.eps), chunk, P(G.spart));
     sum_parts_kernel<<<(k + 255) / 256, 256, 0, st>>>(P(G.spart), kChunks, k, P(G.svec));
   }
-  adj_kernel<<<(unsigned)gridw, 256, 0, st>>>(n, m, k, nn, nn_cnt, P(G.Y), U, D, P(G.eps), P(G.beta), P(G.qd),
-                                              P(G.abar), P(G.dbar));
-  // residual-block pass: covariance part of the gradient, b~ out
+  adj_kernel<T><<<(unsigned)gridw, 256, 0, st>>>(n, m, k, nn, nn_cnt, PT(G.Y), U, D, P(G.eps), P(G.beta),
+                                                 P(G.qd), P(G.abar), P(G.dbar));
+  // residual-block pass (FP64 row kernel on the NLL's residual Gram):
+  // covariance part of the gradient, b~ out
   {
     LagD* lagd = reinterpret_cast<LagD*>(base + L.lagd);
     LagF* lagf = reinterpret_cast<LagF*>(base + L.lagf);
@@ -455,7 +493,8 @@ vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, 
     g.hdr = hdr;
     g.tau = 1.0e4f;
     g.partial = reinterpret_cast<double*>(base + L.partial);
-    g.gram_d = reinterpret_cast<const double*>(vb + V.gram);
+    if constexpr (F32) g.gram_f = reinterpret_cast<const float*>(vb + V.gram);
+    else g.gram_d = reinterpret_cast<const double*>(vb + V.gram);
     g.abar = P(G.abar);
     g.dbar = P(G.dbar);
     g.btil = P(G.btil);
@@ -467,8 +506,8 @@ vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, 
     launch_reduce_partials(g.partial, w, g.partial, 0, 0.0, P(G.grows) + 5, P(G.grows), st);
   }
   // Phi and alpha per row, then G_U through the reverse index
-  phi_kernel<<<(unsigned)gridw, 256, 0, st>>>(n, m, k, nn, nn_cnt, D, P(G.dbar), P(G.eps), P(G.svec), WE,
-                                              P(G.btil), U, P(G.Y), P(G.H));
+  phi_kernel<T><<<(unsigned)gridw, 256, 0, st>>>(n, m, k, nn, nn_cnt, D, P(G.dbar), P(G.eps), P(G.svec), WE,
+                                                 P(G.btil), U, PT(G.Y), PT(G.H));
   {
     int64_t* off = reinterpret_cast<int64_t*>(gb + G.roff);
     int32_t* cur = reinterpret_cast<int32_t*>(gb + G.rcur);
@@ -485,27 +524,35 @@ vst_status vif_nll_grad64(const vst_points* pts, const vst_theta* theta, int m, 
     rscan_add_kernel<<<nb, 1024, 0, st>>>(off, n + 1, bsum);
     rfill_kernel<<<g1, 256, 0, st>>>(n, m, nn, nn_cnt, off, cur, ent);
     rsort_kernel<<<g1, 256, 0, st>>>(n, off, ent);
-    gu_kernel<<<(unsigned)gridw, 256, 0, st>>>(n, m, k, off, ent, A, P(G.btil), P(G.Y), P(G.H), P(G.GU));
+    gu_kernel<T><<<(unsigned)gridw, 256, 0, st>>>(n, m, k, off, ent, A, P(G.btil), PT(G.Y), PT(G.H), PT(G.GU));
   }
   // H = G_U L^{-1}; term1 = <H, dSigma_nk>; J = H^T U
-  gemm_nn(P(G.GU), k, X, k, P(G.H), k, n, k, k, true, st);
+  gemm_nn<T>(PT(G.GU), k, XT, k, PT(G.H), k, n, k, k, true, st);
   const int nb1 = (int)std::min<int64_t>((n * k + 255) / 256, 4096);
-  if (nu == 0) term1_kernel<0><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, P(G.H), P(G.t1part));
-  else if (nu == 1) term1_kernel<1><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, P(G.H), P(G.t1part));
-  else term1_kernel<2><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, P(G.H), P(G.t1part));
-  gemm_tn(P(G.H), k, U, k, n, k, k, false, P(G.Jpart), P(G.J), st);
+  if (nu == 0) term1_kernel<0, T><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, PT(G.H), P(G.t1part));
+  else if (nu == 1) term1_kernel<1, T><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, PT(G.H), P(G.t1part));
+  else term1_kernel<2, T><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, PT(G.H), P(G.t1part));
+  gemm_tn<T>(PT(G.H), k, U, k, n, k, k, false, P(G.Jpart), P(G.J), st);
   // K' = L^T J, Psi, Omega = X^T (Psi X), term2 = <Omega, dSigma_kk>
   gemm_tn(Lkk, k, P(G.J), k, k, k, k, true, P(G.Jpart), P(G.Kp), st);
-  psi_kernel<<<(unsigned)(((int64_t)k * k + 255) / 256), 256, 0, st>>>(k, P(G.Kp), P(G.Psi));
+  psi_kernel<<<(unsigned)((kk2 + 255) / 256), 256, 0, st>>>(k, P(G.Kp), P(G.Psi));
   gemm_nn(P(G.Psi), k, X, k, P(G.T1), k, k, k, k, true, st);
   gemm_tn(X, k, P(G.T1), k, k, k, k, true, P(G.Jpart), P(G.Omega), st);
-  const int nb2 = (int)std::min<int64_t>(((int64_t)k * k + 255) / 256, 4096);
+  const int nb2 = (int)std::min<int64_t>((kk2 + 255) / 256, 4096);
   if (nu == 0) term2_kernel<0><<<nb2, 256, 0, st>>>(k, ind->xy, ind->t, th, P(G.Omega), P(G.t2part));
   else if (nu == 1) term2_kernel<1><<<nb2, 256, 0, st>>>(k, ind->xy, ind->t, th, P(G.Omega), P(G.t2part));
   else term2_kernel<2><<<nb2, 256, 0, st>>>(k, ind->xy, ind->t, th, P(G.Omega), P(G.t2part));
   combine_kernel<<<1, 32, 0, st>>>(P(G.grows), P(G.t1part), nb1, P(G.t2part), nb2, grad);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "VIF gradient kernels");
+}
+
+vst_status vif_nll_grad(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
+                        const int32_t* nn, const int32_t* nn_cnt, const double* y, int precision, double* nll,
+                        double* grad, void* ws, cudaStream_t st) {
+  if (precision == VST_FP64)
+    return vif_nll_grad_T<double>(pts, theta, m, ind, nu, nn, nn_cnt, y, precision, nll, grad, ws, st);
+  return vif_nll_grad_T<float>(pts, theta, m, ind, nu, nn, nn_cnt, y, precision, nll, grad, ws, st);
 }
 
 }  // namespace vst

@@ -80,12 +80,12 @@ def test_host_validation_without_gpu(vst):
     rc = L.vecchia_factor(ctypes.byref(pts), ctypes.byref(th), 5, None, 1024, 2048, 0, 4096, 8192, 256, 16,
                           None)
     assert rc == 2
-    # the VIF gradient: FP64 only, and it needs its own (larger) workspace;
+    # the VIF gradient: a bad precision, and its own (larger) workspace;
     # too many inducing points
     ind = vst._Inducing(256, 512, 5)
-    rc = L.vecchia_nll_grad(ctypes.byref(pts), ctypes.byref(th), 5, ctypes.byref(ind), 1024, 2048, 4096, 1, 8192,
+    rc = L.vecchia_nll_grad(ctypes.byref(pts), ctypes.byref(th), 5, ctypes.byref(ind), 1024, 2048, 4096, 9, 8192,
                             8448, 256, 1 << 40, None)
-    assert rc == 1 and b"VIF gradient" in L.vst_last_error()
+    assert rc == 1 and b"precision" in L.vst_last_error()
     need = L.vst_workspace_size_vif_grad(10, 5, 5)
     assert need > L.vst_workspace_size(10, 5, 5)
     rc = L.vecchia_nll_grad(ctypes.byref(pts), ctypes.byref(th), 5, ctypes.byref(ind), 1024, 2048, 4096, 0, 8192,
