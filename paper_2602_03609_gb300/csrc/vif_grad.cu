@@ -58,7 +58,7 @@ constexpr int kChunks = kDgemmChunks;
 
 struct GradLayout {
   size_t LinvM, Minv, MinvF, XF, Y, GU, H, abar, dbar, eps, beta, qd, wv, svec, spart, btil, roff, rcur, rent, bsum,
-      t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, total;
+      t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, ltab, total;
 };
 
 GradLayout grad_layout(int64_t n, int m, int64_t k) {
@@ -100,6 +100,7 @@ GradLayout grad_layout(int64_t n, int m, int64_t k) {
   G.Omega = take(8 * kk * kk);
   G.t2part = take(8 * 4 * 4096);
   G.grows = take(8 * 8);
+  G.ltab = take(sizeof(LagD) * (size_t)kVifMaxDays * kk);
   G.total = off;
   return G;
 }
@@ -320,18 +321,62 @@ __device__ __forceinline__ void cov_derivs(const DevTheta& th, double dx, double
   d[3] = -f.L * (C + 0.5 * X);
 }
 
-// sum over (i, p) of H[i][p] dSigma_nk[i][p]/dtheta, per block partials
+// lag factors (P, G, Qa, L) of Eq. (2) per (data day dmin + d, inducing point
+// p), FP64, when every data time is a whole day within kVifMaxDays days (the
+// day range of the low-rank step, info)
+__global__ void day_factors_kernel(const double* tk, int k, DevTheta th, const int64_t* info, LagD* tab) {
+  const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (info[2] == 0) return;
+  if (id >= info[1] * k) return;
+  const int64_t d = id / k;
+  const int p = (int)(id % k);
+  tab[id] = lag_factors(th, (double)(info[0] + d) - tk[p]);
+}
+
+// the derivatives of Eq. (2) from given lag factors; T = float evaluates the
+// spatial part (h, e^-x, the Matern polynomial) in FP32
+template <int NU, typename T>
+__device__ __forceinline__ void cov_derivs_f(const DevTheta& th, const LagD& f, double dx, double dy, double (&d)[4]) {
+  if constexpr (std::is_same<T, float>::value) {
+    const float fx = (float)dx, fy = (float)dy;
+    const float x = (float)f.G * sqrtf(fx * fx + fy * fy);
+    const float E = expf(-x);
+    const float P = (float)f.P;
+    const float C = P * matern_M<NU, float>(x, E);
+    const float X = P * matern_xdM<NU, float>(x, E);
+    d[0] = (double)C / th.sigma1sq;
+    d[1] = (double)X / th.c;
+    d[2] = f.Qa * (-th.p * (double)C - 0.5 * th.gamma * (double)X);
+    d[3] = -f.L * ((double)C + 0.5 * (double)X);
+  } else {
+    const double x = f.G * sqrt(dx * dx + dy * dy);
+    const double E = exp(-x);
+    const double C = f.P * matern_M<NU, double>(x, E);
+    const double X = f.P * matern_xdM<NU, double>(x, E);
+    d[0] = C / th.sigma1sq;
+    d[1] = X / th.c;
+    d[2] = f.Qa * (-th.p * C - 0.5 * th.gamma * X);
+    d[3] = -f.L * (C + 0.5 * X);
+  }
+}
+
+// sum over (i, p) of H[i][p] dSigma_nk[i][p]/dtheta, per block partials;
+// the lag factors from the day table when info says it holds
 template <int NU, typename T>
 __global__ void term1_kernel(int64_t n, int k, const double* xy, const double* t, const double* xyk,
-                             const double* tk, DevTheta th, const T* H, double* part) {
+                             const double* tk, DevTheta th, const LagD* tab, const int64_t* info, const T* H,
+                             double* part) {
   __shared__ double sh[4][256];
   double acc[4] = {0, 0, 0, 0};
   const int64_t total = n * k;
+  const bool use_tab = info[2] != 0;
+  const int64_t d0 = info[0];
   for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = q / k;
-    const int p = (int)(q % k);
+    const int p = (int)(q - i * k);
+    const LagD f = use_tab ? tab[((int64_t)t[i] - d0) * k + p] : lag_factors(th, t[i] - tk[p]);
     double d[4];
-    cov_derivs<NU>(th, xy[2 * i] - xyk[2 * p], xy[2 * i + 1] - xyk[2 * p + 1], t[i] - tk[p], d);
+    cov_derivs_f<NU, T>(th, f, xy[2 * i] - xyk[2 * p], xy[2 * i + 1] - xyk[2 * p + 1], d);
     const double h = (double)H[q];
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[j] = fma(h, d[j], acc[j]);
@@ -529,9 +574,17 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
   // H = G_U L^{-1}; term1 = <H, dSigma_nk>; J = H^T U
   gemm_nn<T>(PT(G.GU), k, XT, k, PT(G.H), k, n, k, k, true, st);
   const int nb1 = (int)std::min<int64_t>((n * k + 255) / 256, 4096);
-  if (nu == 0) term1_kernel<0, T><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, PT(G.H), P(G.t1part));
-  else if (nu == 1) term1_kernel<1, T><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, PT(G.H), P(G.t1part));
-  else term1_kernel<2, T><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, PT(G.H), P(G.t1part));
+  {
+    const int64_t* info = reinterpret_cast<const int64_t*>(vb + V.dinfo);  // day range of the low-rank step
+    LagD* tab = reinterpret_cast<LagD*>(gb + G.ltab);
+    day_factors_kernel<<<(unsigned)((kVifMaxDays * (int64_t)k + 255) / 256), 256, 0, st>>>(ind->t, k, th, info, tab);
+    if (nu == 0)
+      term1_kernel<0, T><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, tab, info, PT(G.H), P(G.t1part));
+    else if (nu == 1)
+      term1_kernel<1, T><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, tab, info, PT(G.H), P(G.t1part));
+    else
+      term1_kernel<2, T><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, tab, info, PT(G.H), P(G.t1part));
+  }
   gemm_tn<T>(PT(G.H), k, U, k, n, k, k, false, P(G.Jpart), P(G.J), st);
   // K' = L^T J, Psi, Omega = X^T (Psi X), term2 = <Omega, dSigma_kk>
   gemm_tn(Lkk, k, P(G.J), k, k, k, k, true, P(G.Jpart), P(G.Kp), st);
