@@ -135,3 +135,30 @@ def test_vif_grad_small_workspace(env):
     ws = vst.Workspace(n, 4, 8)  # the NLL's workspace: too small for the gradient
     with pytest.raises(ValueError):
         vst.vecchia_nll_grad(xy_d, t_d, th, 4, nn_d, cnt_d, y_d, precision=vst.FP64, inducing=(xyk_d, tk_d), ws=ws)
+
+
+@pytest.mark.parametrize("n", [0, 1, 5])
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+def test_vif_grad_empty_and_tiny(env, n, precision):
+    """n = 0 (NLL and gradient 0), a single point, and n <= m (every row's
+    neighbours are all its predecessors), with k = 3 inducing points."""
+    torch, vst = env
+    prec = getattr(vst, precision)
+    xy0, t0, th, xyk, tk, y0 = problem(10, 4, 3, seed=6)
+    xy, t, y = (np.ascontiguousarray(a[:n]) for a in (xy0, t0, y0))
+    m = 4
+    xy_d, t_d, y_d, xyk_d, tk_d = dev(torch, xy, t, y, xyk, tk)
+    ind = (xyk_d, tk_d)
+    nn_d, cnt_d = vst.vif_build_neighbors(xy_d, t_d, th, m, inducing=ind)
+    cnt = cnt_d.cpu().numpy()
+    assert cnt.tolist() == [min(i, m) for i in range(n)]
+    nll, grad = vst.vecchia_nll_grad(xy_d, t_d, th, m, nn_d, cnt_d, y_d, precision=prec, inducing=ind)
+    if n == 0:
+        assert nll.item() == 0.0 and np.all(grad.cpu().numpy() == 0.0)
+        return
+    nn = nn_d.cpu().numpy()
+    v_o, g_o = ovif.nll_grad(xy, t, th, xyk, tk, m, nn, cnt, y)
+    tol_v, tol_g = (1e-10, 1e-7) if precision == "FP64" else (1e-6, 1e-4)
+    assert abs(nll.item() - v_o) / n <= tol_v
+    err = np.abs(grad.cpu().numpy() - g_o)
+    assert np.all(err <= tol_g * np.abs(g_o) + 1e-6 * n), (grad.cpu().numpy(), g_o)
