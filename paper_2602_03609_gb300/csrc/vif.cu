@@ -150,31 +150,41 @@ __global__ void kk_kernel(const double* xyk, const double* tk, int k, DevTheta t
 // blocked Cholesky, FP64, lower, in place (A row-major k x k)
 constexpr int kPanel = 32;
 
-// diagonal block of the panel, jb x jb (jb <= 32), factored in shared memory
-// by one warp: lane r holds row r; a non-positive pivot is reported and
+// diagonal block of the panel, jb x jb (jb <= 32), factored by one warp with
+// lane r holding row r in registers (the block staged through shared memory
+// for coalesced loads and stores); a non-positive pivot is reported and
 // replaced by 1 so that the factorisation finishes
 __global__ void chol_diag_kernel(double* A, int k, int j0, int jb, WsHeader* hdr, int err_code) {
-  __shared__ double a[32][33];
+  __shared__ double st[32][33];
+  __shared__ double col[32];
   const int lane = threadIdx.x;
-  for (int q = 0; q < jb; ++q) a[lane][q] = (lane < jb) ? A[(int64_t)(j0 + lane) * k + j0 + q] : 0.0;
+  for (int r = 0; r < 32; ++r) st[r][lane] = (r < jb && lane < jb) ? A[(int64_t)(j0 + r) * k + j0 + lane] : 0.0;
   __syncwarp();
-  for (int c = 0; c < jb; ++c) {
-    double d = a[c][c];
+  double a[32];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) a[q] = st[lane][q];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    if (c >= jb) break;
+    double d = __shfl_sync(0xffffffffu, a[c], c);
     if (!(d > 0.0)) {
       if (lane == 0) report_error(hdr, err_code, j0 + c);
       d = 1.0;
     }
     d = sqrt(d);
+    if (lane == c) a[c] = d;
+    if (lane > c) a[c] /= d;
+    col[lane] = a[c];
     __syncwarp();
-    if (lane == c) a[c][c] = d;
-    if (lane > c && lane < jb) a[lane][c] /= d;
-    __syncwarp();
-    if (lane > c && lane < jb)
-      for (int c2 = c + 1; c2 <= lane; ++c2) a[lane][c2] -= a[lane][c] * a[c2][c];
+#pragma unroll
+    for (int q = c + 1; q < 32; ++q) a[q] = fma(-a[c], col[q], a[q]);
     __syncwarp();
   }
-  if (lane < jb)
-    for (int q = 0; q <= lane; ++q) A[(int64_t)(j0 + lane) * k + j0 + q] = a[lane][q];
+#pragma unroll
+  for (int q = 0; q < 32; ++q) st[lane][q] = a[q];
+  __syncwarp();
+  for (int r = 0; r < jb; ++r)
+    if (lane <= r) A[(int64_t)(j0 + r) * k + j0 + lane] = st[r][lane];
 }
 
 // panel rows below the diagonal block: L21 = A21 L11^{-T}, one thread per row
