@@ -261,8 +261,21 @@ __global__ void trinv_kernel(const double* L, int k, double* X) {
     if (lane == 0) x[j] = 1.0 / L[(int64_t)j * k + j];
     __syncwarp();
     for (int r = j + 1; r < k; ++r) {
+      // row segment L[r][j..r) read 8 loads per lane at a time (independent
+      // loads in flight instead of one dependent load per step)
       double s = 0.0;
-      for (int p = j + lane; p < r; p += 32) s += L[(int64_t)r * k + p] * x[p];
+      const double* Lr = L + (int64_t)r * k;
+      for (int p0 = j; p0 < r; p0 += 256) {
+        double lv[8], xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int p = p0 + u * 32 + lane;
+          lv[u] = p < r ? Lr[p] : 0.0;
+          xv[u] = p < r ? x[p] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s = fma(lv[u], xv[u], s);
+      }
       s = warp_sum(s);
       if (lane == 0) x[r] = -s / L[(int64_t)r * k + r];
       __syncwarp();
@@ -711,45 +724,78 @@ __global__ void make_m_kernel(const double* G, int k, double* M, double* v, doub
   if (id == 0) *ete = G[(int64_t)k * kk + k];
 }
 
-// z = L_M^{-1} v (one block), then the NLL
-__global__ void final_kernel(const double* Lm, int k, const double* v, const double* ete, const double* logd_part,
-                             int64_t nparts, int64_t n, double* z, double* nll) {
-  __shared__ double sh[256];
-  // sum log D_i (fixed order) and log det M
+// z = L_M^{-1} v (one block of 1024 threads), then the NLL.  The forward
+// substitution runs in blocks of 32 rows: the 32 warps each take one row's
+// product with the solved part (lanes over the row, 8 loads in flight per
+// lane), then warp 0 solves the 32 x 32 diagonal block by shuffles with the
+// reciprocal diagonal computed up front.
+__global__ void __launch_bounds__(1024) final_kernel(const double* Lm, int k, const double* v, const double* ete,
+                                                     const double* logd_part, int64_t nparts, int64_t n, double* z,
+                                                     double* nll) {
+  __shared__ double sh[1024];
+  __shared__ double rhs[32];
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // sum log D_i (fixed order) and log det M; reciprocal diagonal into z
   double s = 0.0;
-  for (int64_t q = threadIdx.x; q < nparts; q += 256) s += logd_part[q];
+  for (int64_t q = tid; q < nparts; q += 1024) s += logd_part[q];
   double ld = 0.0;
-  for (int r = threadIdx.x; r < k; r += 256) ld += 2.0 * log(Lm[(int64_t)r * k + r]);
-  sh[threadIdx.x] = s + ld;
+  for (int r = tid; r < k; r += 1024) {
+    const double d = Lm[(int64_t)r * k + r];
+    ld += 2.0 * log(d);
+    z[r] = 1.0 / d;
+  }
+  sh[tid] = s + ld;
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+  for (int w = 512; w > 0; w >>= 1) {
+    if (tid < w) sh[tid] += sh[tid + w];
     __syncthreads();
   }
   const double logdet = sh[0];
   __syncthreads();
-  // forward substitution, row by row, block-parallel dot products
-  for (int r = 0; r < k; ++r) {
-    double d = 0.0;
-    for (int p = threadIdx.x; p < r; p += 256) d += Lm[(int64_t)r * k + p] * z[p];
-    sh[threadIdx.x] = d;
-    __syncthreads();
-    for (int w = 128; w > 0; w >>= 1) {
-      if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
-      __syncthreads();
+  for (int b0 = 0; b0 < k; b0 += 32) {
+    const int R = min(32, k - b0);
+    if (wid < R) {
+      const int r = b0 + wid;
+      const double* Lr = Lm + (int64_t)r * k;
+      double d = 0.0;
+      for (int p0 = 0; p0 < b0; p0 += 256) {
+        double lv[8], zv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int p = p0 + u * 32 + lane;
+          lv[u] = p < b0 ? Lr[p] : 0.0;
+          zv[u] = p < b0 ? z[p] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) d = fma(lv[u], zv[u], d);
+      }
+      d = warp_sum(d);
+      if (lane == 0) rhs[wid] = v[r] - d;
     }
-    if (threadIdx.x == 0) z[r] = (v[r] - sh[0]) / Lm[(int64_t)r * k + r];
+    __syncthreads();
+    if (wid == 0) {
+      // lane i: row b0 + i of the diagonal block
+      double acc = lane < R ? rhs[lane] : 0.0;
+      const double rd = lane < R ? z[b0 + lane] : 0.0;  // 1 / L_ii
+      double zi = 0.0;
+      for (int c = 0; c < R; ++c) {
+        const double zc = __shfl_sync(0xffffffffu, acc * rd, c);
+        if (lane == c) zi = zc;
+        if (lane > c && lane < R) acc = fma(-Lm[(int64_t)(b0 + lane) * k + b0 + c], zc, acc);
+      }
+      if (lane < R) z[b0 + lane] = zi;
+    }
     __syncthreads();
   }
   double zz = 0.0;
-  for (int r = threadIdx.x; r < k; r += 256) zz += z[r] * z[r];
-  sh[threadIdx.x] = zz;
+  for (int r = tid; r < k; r += 1024) zz += z[r] * z[r];
+  sh[tid] = zz;
   __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+  for (int w = 512; w > 0; w >>= 1) {
+    if (tid < w) sh[tid] += sh[tid + w];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *nll = 0.5 * (double)n * log(2.0 * M_PI) + 0.5 * logdet + 0.5 * (*ete - sh[0]);
+  if (tid == 0) *nll = 0.5 * (double)n * log(2.0 * M_PI) + 0.5 * logdet + 0.5 * (*ete - sh[0]);
 }
 
 // ---------------------------------------------------------------------------
@@ -973,7 +1019,7 @@ static vst_status vif_nll_T(const vst_points* pts, const vst_theta* theta, int m
   make_m_kernel<<<(int)(((int64_t)k * k + 255) / 256 + 1), 256, 0, st>>>(G, k, M, v, z + k);
   s = chol64(M, k, hdr, VST_ENOTSPD, st);
   if (s != VST_OK) return s;
-  final_kernel<<<1, 256, 0, st>>>(M, k, v, z + k, logd, nparts, n, z, nll);
+  final_kernel<<<1, 1024, 0, st>>>(M, k, v, z + k, logd, nparts, n, z, nll);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "VIF Woodbury kernels");
 }
