@@ -390,15 +390,22 @@ __global__ void __launch_bounds__(WARPS * 32) rerank_kernel(KnnArgsV A) {
 
 // ---- second pass over all predecessors of the listed rows: lane-local FP32
 // screening with the same error bound as the tile pass (threshold from the
-// row's record; -1 keeps every j), exact FP64 |rho| for the survivors
-template <int NU, int WARPS>
-__global__ void __launch_bounds__(WARPS * 32) pass2_kernel(KnnArgsV A) {
+// row's record; -1 keeps every j), exact FP64 |rho| for the survivors.  One
+// block of 8 warps per row: warp w takes the 32-wide j groups w, w + 8, ...
+// into its own top-(m+1) list; warp 0 then merges the 8 lists (the merge
+// keeps the same (|rho| desc, j asc) order, so the result does not depend
+// on how j was split).
+constexpr int kPass2Warps = 8;
+
+template <int NU>
+__global__ void __launch_bounds__(kPass2Warps * 32) pass2_kernel(KnnArgsV A) {
   extern __shared__ double ui_raw[];
+  double* ui = ui_raw;
+  float* uif = reinterpret_cast<float*>(ui_raw + A.k);
+  __shared__ double mr[kPass2Warps][32];
+  __shared__ int mid[kPass2Warps][32];
+  __shared__ int mcnt[kPass2Warps];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  double* ui = ui_raw + (int64_t)wib * A.k;
-  float* uif = reinterpret_cast<float*>(ui_raw + (int64_t)WARPS * A.k) + (int64_t)wib * A.k;
-  const int64_t warp = (int64_t)blockIdx.x * WARPS + wib;
-  const int64_t total = (int64_t)gridDim.x * WARPS;
   const int K = A.m + 1;
   const double NEG = -1.0e300;
   const double tiny = 1e-12 * A.th.sigma1sq;
@@ -406,18 +413,19 @@ __global__ void __launch_bounds__(WARPS * 32) pass2_kernel(KnnArgsV A) {
   const float dotc = 24.0f * 1.05f * kU;
   const int64_t nrows = (int64_t)*A.fbcount;
   if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&A.hdr->n_fallback, (unsigned long long)nrows);
-  for (int64_t w = warp; w < nrows; w += total) {
+  for (int64_t w = blockIdx.x; w < nrows; w += gridDim.x) {
     const int64_t i = A.fbrows[w];
-    for (int c = lane; c < A.k; c += 32) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < A.k; c += kPass2Warps * 32) {
       ui[c] = A.U[i * A.k + c];
       uif[c] = A.Uf[i * A.k + c];
     }
-    __syncwarp();
+    __syncthreads();
     const float4 info = A.rowinfo[i];
     const double xi = A.xy[2 * i], yi = A.xy[2 * i + 1], ti = A.t[i], ri = A.r[i];
     double lr = NEG, thr = NEG;
     int lid = INT_MAX, count = 0;
-    for (int64_t j0 = 0; j0 < i; j0 += 32) {
+    for (int64_t j0 = (int64_t)wib * 32; j0 < i; j0 += kPass2Warps * 32) {
       const int64_t j = j0 + lane;
       double rho = NEG;
       if (j < i) {
@@ -461,8 +469,19 @@ __global__ void __launch_bounds__(WARPS * 32) pass2_kernel(KnnArgsV A) {
         topk_insert(lane, K, cr, (int)(j0 + src), lr, lid, count, thr);
       }
     }
-    write_row(A, lane, i, count, lr, lid);
-    __syncwarp();
+    mr[wib][lane] = lr;
+    mid[wib][lane] = lid;
+    if (lane == 0) mcnt[wib] = count;
+    __syncthreads();
+    if (wib == 0) {
+      double fr = NEG, fthr = NEG;
+      int fid = INT_MAX, fcount = 0;
+      for (int q = 0; q < kPass2Warps; ++q) {
+        const int cq = mcnt[q];
+        for (int e = 0; e < cq; ++e) topk_insert(lane, K, mr[q][e], mid[q][e], fr, fid, fcount, fthr);
+      }
+      write_row(A, lane, i, fcount, fr, fid);
+    }
   }
 }
 
@@ -491,7 +510,16 @@ vst_status knn_stages(const KnnArgsV& A, cudaStream_t st) {
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(1, per) * sms * 8);
   filter_kernel<NU><<<(unsigned)grid, 256, 0, st>>>(A, ntiles);
   launch_rows_per_warp(rerank_kernel<NU, W>, A, st);
-  launch_rows_per_warp(pass2_kernel<NU, W>, A, st, sizeof(double) + sizeof(float));
+  {
+    const size_t smem = (sizeof(double) + sizeof(float)) * A.k;
+    int dev = 0, sms2 = 0, per2 = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms2, cudaDevAttrMultiProcessorCount, dev);
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(pass2_kernel<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, pass2_kernel<NU>, kPass2Warps * 32, smem);
+    pass2_kernel<NU><<<std::max(1, per2) * sms2, kPass2Warps * 32, smem, st>>>(A);
+  }
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "VIF neighbour kernels");
 }
