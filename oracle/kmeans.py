@@ -10,7 +10,8 @@ on the unique locations S and the unique times T; the inducing points are the
 Cartesian product S_bar x T_bar, point a m_t + b = (location a, time b).
 
 kMeans++ (Arthur and Vassilvitskii, 2007) with the discrete choices made from
-exact integers (reading recorded in the design doc):
+exact integers (a reading of the paper's kMeans++ step, chosen so that both sides
+can agree bit for bit):
   * draws u_j = (mix(x0 + (j + 1) gamma) >> 11) 2^-53, SplitMix64 (Steele,
     Lea and Flood, 2014), x0 = seed (times) or seed ^ 0xD1B54A32D192ED03
     (locations);

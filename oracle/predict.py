@@ -6,7 +6,7 @@ TEST INFRASTRUCTURE (see oracle/__init__.py).  Plain numpy/scipy, FP64, for
 small inputs: a dense correlation matrix between prediction and training
 points, and one dense local solve per prediction point.
 
-Reading (recorded in the design doc): every prediction point conditions on the
+Reading of Sect. 3.1 under the Vecchia approximation: every prediction point conditions on the
 min(m, n) training points with the largest correlation C(p, j) / sigma1^2
 (latent covariance, no nugget; ties to the smaller training index; sorted by
 decreasing correlation); prediction points do not condition on one another.

@@ -4,7 +4,7 @@ TEST INFRASTRUCTURE (see oracle/__init__.py).  Plain numpy/scipy, FP64, for
 small n (dense k x k algebra, per-row loops).  Library primitives (Cholesky,
 triangular solve) are used as steps; everything else is written out.
 
-Model (reading recorded in the design doc): the latent process is b = b_l + b_s
+Model (the reading of Sect. 4.3 taken here): the latent process is b = b_l + b_s
 with the predictive-process part Cov(b_l) = Sigma_nk Sigma_kk^{-1} Sigma_kn
 (k inducing points) and the residual Cov(b_s) = Sigma - Sigma_nk Sigma_kk^{-1}
 Sigma_kn.  The residual plus the nugget, R~ = Cov(b_s) + sigma^2 I, is
@@ -66,7 +66,7 @@ def knn(xy, t, theta, U, r, m):
     predecessors with the largest |R_ij| / sqrt(R_ii R_jj); ties -> smaller
     index; sorted by decreasing |rho|.  A point whose residual variance is at
     most 1e-12 sigma1^2 (an inducing point on top of it) has no defined
-    residual correlation; it is taken as 0 (the design doc reading).
+    residual correlation; it is taken as 0 (a reading: the paper is silent).
     Returns nn, cnt, rho_m, rho_m1."""
     n = t.shape[0]
     nn = np.full((n, m), -1, dtype=np.int32)
