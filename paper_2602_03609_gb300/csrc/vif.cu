@@ -428,9 +428,10 @@ __global__ void __launch_bounds__(128) gram_delta_kernel(const int32_t* nn, cons
   for (int q = 0; q < GT::ROUNDS; ++q) {
     int rs = 0, t = 0;
     bool on = true;
+    constexpr int FD = GT::FULL > 0 ? GT::FULL : 1;  // (no full rounds when PM = 8)
     if (q < GT::FULL * GT::RW) {
-      rs = q / GT::FULL;
-      t = (q % GT::FULL) * 32 + lane;
+      rs = q / FD;
+      t = (q % FD) * 32 + lane;
     } else {
       const int j = (q - GT::FULL * GT::RW) * 32 + lane;
       on = j < GT::LEFT * GT::RW;
