@@ -41,6 +41,12 @@ vst_status lowrank_tc(const vst_points* pts, const vst_theta* theta, const vst_i
                       int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st);
 
 // residual-correlation neighbours (vif_knn.cu); base: the whole workspace
+// C[i][c] = sum_p A[i][p] B[c][p] on the tensor cores (vif_tc.cu), A FP32
+// [n][k] with row stride lda, B from the FP64 k x k matrix M (bmode 1: M; 2:
+// B[c][p] = M[p][c] of a lower-triangular M), C FP32 [n][k]
+vst_status tc_product(const float* A, int64_t lda, int64_t n, const double* M, int bmode, int k, float* C,
+                      int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st);
+
 vst_status vif_knn(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
                    int32_t* nn, int32_t* nn_cnt, int64_t* tie_rows, int64_t tie_cap, char* base,
                    WsHeader* hdr, cudaStream_t st);

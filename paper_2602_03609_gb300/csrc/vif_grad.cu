@@ -57,7 +57,7 @@ namespace {
 constexpr int kChunks = kDgemmChunks;
 
 struct GradLayout {
-  size_t LinvM, Minv, MinvF, XF, Y, GU, H, abar, dbar, eps, beta, qd, wv, svec, spart, btil, roff, rcur, rent, bsum,
+  size_t LinvM, Minv, Y, GU, H, abar, dbar, eps, beta, qd, wv, svec, spart, btil, roff, rcur, rent, bsum,
       t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, ltab, total;
 };
 
@@ -73,8 +73,6 @@ GradLayout grad_layout(int64_t n, int m, int64_t k) {
   const size_t mm = (size_t)std::max(m, 1);
   G.LinvM = take(8 * kk * kk);
   G.Minv = take(8 * kk * kk);
-  G.MinvF = take(4 * kk * kk);
-  G.XF = take(4 * kk * kk);
   G.Y = take(8 * nn * kk);
   G.GU = take(8 * nn * kk);
   G.H = take(8 * nn * kk);
@@ -103,11 +101,6 @@ GradLayout grad_layout(int64_t n, int m, int64_t k) {
   G.ltab = take(sizeof(LagD) * (size_t)kVifMaxDays * kk);
   G.total = off;
   return G;
-}
-
-__global__ void narrow_kernel(const double* src, int64_t count, float* dst) {
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x)
-    dst[q] = (float)src[q];
 }
 
 // y = A x for a k x k row-major A
@@ -485,7 +478,6 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
   const DevTheta th = dev_theta_vif(theta);
   const int64_t gridw = std::min<int64_t>((n + 7) / 8, 65535);  // 8 warps per block of 256
   const int64_t kk2 = (int64_t)k * k;
-  const unsigned gkk = (unsigned)std::min<int64_t>((kk2 + 255) / 256, 4096);
 
   // M^{-1} = L_M^{-T} L_M^{-1}
   {
@@ -495,19 +487,18 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
     trinv_kernel<<<(k + wpb - 1) / wpb, 32 * wpb, smem, st>>>(LM, k, P(G.LinvM));
     gemm_tn(P(G.LinvM), k, P(G.LinvM), k, k, k, k, false, P(G.Jpart), P(G.Minv), st);
   }
-  const T* MinvT;
-  const T* XT;
+  // FP64 form: the dense products on the FP64 tile GEMM
+  const T* MinvT = reinterpret_cast<const T*>(P(G.Minv));
+  const T* XT = reinterpret_cast<const T*>(X);
+  // Y = W M^{-1} (mixed: on the tensor cores, M^{-1} symmetric); wv = M^{-1} v
+  const int terms = precision == VST_MIXED_BF16X3 ? 3 : 6;
   if constexpr (F32) {
-    narrow_kernel<<<gkk, 256, 0, st>>>(P(G.Minv), kk2, reinterpret_cast<float*>(gb + G.MinvF));
-    narrow_kernel<<<gkk, 256, 0, st>>>(X, kk2, reinterpret_cast<float*>(gb + G.XF));
-    MinvT = reinterpret_cast<const T*>(gb + G.MinvF);
-    XT = reinterpret_cast<const T*>(gb + G.XF);
+    s = tc_product(reinterpret_cast<const float*>(WE), k + 1, n, P(G.Minv), 1, k, reinterpret_cast<float*>(PT(G.Y)),
+                   terms, vb, V, hdr, st);
+    if (s != VST_OK) return s;
   } else {
-    MinvT = reinterpret_cast<const T*>(P(G.Minv));
-    XT = reinterpret_cast<const T*>(X);
+    gemm_nn<T>(WE, k + 1, MinvT, k, PT(G.Y), k, n, k, k, false, st);
   }
-  // Y = W M^{-1}; wv = M^{-1} v
-  gemm_nn<T>(WE, k + 1, MinvT, k, PT(G.Y), k, n, k, k, false, st);
   gemv_kernel<<<(k * 32 + 255) / 256, 256, 0, st>>>(P(G.Minv), v, k, P(G.wv));
   rowvec_kernel<T><<<(unsigned)gridw, 256, 0, st>>>(n, k, PT(G.Y), WE, U, v, P(G.wv), y, P(G.eps), P(G.beta),
                                                     P(G.qd));
@@ -571,8 +562,15 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
     rsort_kernel<<<g1, 256, 0, st>>>(n, off, ent);
     gu_kernel<T><<<(unsigned)gridw, 256, 0, st>>>(n, m, k, off, ent, A, P(G.btil), PT(G.Y), PT(G.H), PT(G.GU));
   }
-  // H = G_U L^{-1}; term1 = <H, dSigma_nk>; J = H^T U
-  gemm_nn<T>(PT(G.GU), k, XT, k, PT(G.H), k, n, k, k, true, st);
+  // H = G_U L^{-1} (mixed: on the tensor cores, B[c][p] = (L^{-1})[p][c]);
+  // term1 = <H, dSigma_nk>; J = H^T U
+  if constexpr (F32) {
+    s = tc_product(reinterpret_cast<const float*>(PT(G.GU)), k, n, X, 2, k, reinterpret_cast<float*>(PT(G.H)), terms,
+                   vb, V, hdr, st);
+    if (s != VST_OK) return s;
+  } else {
+    gemm_nn<T>(PT(G.GU), k, XT, k, PT(G.H), k, n, k, k, true, st);
+  }
   const int nb1 = (int)std::min<int64_t>((n * k + 255) / 256, 4096);
   {
     const int64_t* info = reinterpret_cast<const int64_t*>(vb + V.dinfo);  // day range of the low-rank step

@@ -97,6 +97,50 @@ __global__ void split_x_kernel(const double* X, int k, int kp, __nv_bfloat16* B)
   }
 }
 
+// A parts from an FP32 matrix (row stride lda): [P][n][kp], zero beyond k
+template <int P>
+__global__ void split_a_kernel(const float* A, int64_t lda, int64_t n, int k, int kp, __nv_bfloat16* Ap) {
+  const int groups = kp / 8;
+  const int64_t total = n * groups;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = id / groups;
+    const int p0 = (int)(id % groups) * 8;
+    __align__(16) __nv_bfloat16 o[P][8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int p = p0 + q;
+      __nv_bfloat16 s[P];
+      split_parts<P>(p < k ? A[i * lda + p] : 0.0f, s);
+#pragma unroll
+      for (int j = 0; j < P; ++j) o[j][q] = s[j];
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      *reinterpret_cast<uint4*>(Ap + ((int64_t)j * n + i) * kp + p0) = *reinterpret_cast<const uint4*>(o[j]);
+  }
+}
+
+// B parts [P][kp][kp] from an FP64 k x k matrix M: mode 1, B[c][p] = M[c][p];
+// mode 2, B[c][p] = M[p][c] for p >= c (M lower triangular); zero elsewhere
+template <int P>
+__global__ void split_b_kernel(const double* M, int k, int kp, int mode, __nv_bfloat16* B) {
+  const int64_t total = (int64_t)kp * kp;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < total;
+       id += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(id / kp), p = (int)(id % kp);
+    double v = 0.0;
+    if (c < k && p < k) {
+      if (mode == 1) v = M[(int64_t)c * k + p];
+      else if (p >= c) v = M[(int64_t)p * k + c];
+    }
+    __nv_bfloat16 o[P];
+    split_parts<P>(v, o);
+#pragma unroll
+    for (int j = 0; j < P; ++j) B[(int64_t)j * total + id] = o[j];
+  }
+}
+
 // double-float coordinates of the inducing points
 __global__ void ind_coords_kernel(const double* xyk, int k, float4* zf) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -168,7 +212,10 @@ struct SplitTerms<3> {
   static __device__ __forceinline__ int b(int t) { return t == 1 ? 1 : t == 3 ? 2 : t == 4 ? 1 : 0; }
 };
 
-template <int P, int BN, int STAGES>
+// K range of a column tile: KMODE 0, B[c][p] = 0 for p > c (K up to the
+// tile's last column); 1, the whole K; 2, B[c][p] = 0 for p < c (K from the
+// tile's first column).  RPART: also the row sums of the squared outputs.
+template <int P, int BN, int STAGES, int KMODE = 0, bool RPART = true>
 __global__ void __launch_bounds__(128, 1)
     ugemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
                     int k, int kp, float* U, double* rpart, WsHeader* hdr) {
@@ -188,8 +235,9 @@ __global__ void __launch_bounds__(128, 1)
   const int ntile = kp / BN;
   const int64_t m0 = (int64_t)(blockIdx.x / ntile) * S::BM;
   const int c0 = (int)(blockIdx.x % ntile) * BN;
-  const int kend = kp < c0 + BN ? kp : c0 + BN;  // B[c][p] = 0 for p > c
-  const int nkb = (kend + S::BK - 1) / S::BK;
+  const int kend = KMODE == 0 ? (kp < c0 + BN ? kp : c0 + BN) : kp;
+  const int kb0 = KMODE == 2 ? c0 / S::BK : 0;
+  const int nkb = (kend + S::BK - 1) / S::BK - kb0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -229,8 +277,8 @@ __global__ void __launch_bounds__(128, 1)
         const uint32_t sa = base + s * S::STAGE_BYTES, sb = sa + P * S::A_BYTES;
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-          umma::tma_load_2d(sa + j * S::A_BYTES, &tmA, kb * S::BK, (int)(j * n + m0), &full[s]);
-          umma::tma_load_2d(sb + j * S::B_BYTES, &tmB, kb * S::BK, j * kp + c0, &full[s]);
+          umma::tma_load_2d(sa + j * S::A_BYTES, &tmA, (kb0 + kb) * S::BK, (int)(j * n + m0), &full[s]);
+          umma::tma_load_2d(sb + j * S::B_BYTES, &tmB, (kb0 + kb) * S::BK, j * kp + c0, &full[s]);
         }
       }
       __syncwarp();
@@ -288,10 +336,12 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
     for (int q = 0; q < 32; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
     const int cc = c0 + cb;
+    if constexpr (RPART) {
 #pragma unroll
-    for (int q = 0; q < 32; ++q) {
-      const float u = __uint_as_float(v[q]);
-      if (cc + q < k) df_fma_acc(sq, u, df{u, 0.f});
+      for (int q = 0; q < 32; ++q) {
+        const float u = __uint_as_float(v[q]);
+        if (cc + q < k) df_fma_acc(sq, u, df{u, 0.f});
+      }
     }
     if (i < n && cc < k) {
       float* dst = U + i * k + cc;
@@ -307,7 +357,7 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
   }
-  if (i < n) rpart[i * ntile + c0 / BN] = df_to_double(sq);
+  if (RPART && i < n) rpart[i * ntile + c0 / BN] = df_to_double(sq);
   if (!ok) report_error(hdr, VST_ETIMEOUT, m0);
   umma::fence_before_sync();
   __syncthreads();
@@ -372,6 +422,36 @@ cudaError_t launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t 
   return cudaGetLastError();
 }
 
+// C[i][c] = sum_p A[i][p] B[c][p] on the tensor cores (FP32 out [n][k]);
+// bmode 1: B = M (full), bmode 2: B[c][p] = M[p][c], M lower triangular
+template <int P, int BN, int KMODE>
+vst_status tc_product_P(const float* A, int64_t lda, int64_t n, const double* M, int k, float* C, char* vbase,
+                        const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
+  using S = TcShape<P, BN, 2>;
+  const int kp = vif_kp(k);
+  __nv_bfloat16* Ap = reinterpret_cast<__nv_bfloat16*>(vbase + V.Ap);
+  __nv_bfloat16* Bp = reinterpret_cast<__nv_bfloat16*>(vbase + V.Bp);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, sms) * 8;
+  split_a_kernel<P><<<grid, 256, 0, st>>>(A, lda, n, k, kp, Ap);
+  split_b_kernel<P><<<grid, 256, 0, st>>>(M, k, kp, KMODE, Bp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "split kernels");
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, Ap, (uint64_t)P * n, (uint64_t)kp, S::BM) || !make_map(&tb, Bp, (uint64_t)P * kp, (uint64_t)kp, BN))
+    return fail(VST_ECUDA, "cuTensorMapEncodeTiled unavailable or rejected the operand layout");
+  auto kern = ugemm_tc_kernel<P, BN, 2, KMODE, false>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core product attributes");
+  const int64_t tiles = (n + S::BM - 1) / S::BM * (kp / BN);
+  if (tiles > 0x7fffffff) return fail(VST_EINVAL, "too many tiles");
+  kern<<<(unsigned)tiles, 128, S::SMEM, st>>>(ta, tb, n, k, kp, C, nullptr, hdr);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? VST_OK : cuda_fail(e, "tensor-core product");
+}
+
 template <int P>
 vst_status lowrank_tc_P(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu,
                         char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
@@ -411,6 +491,22 @@ vst_status lowrank_tc_P(const vst_points* pts, const vst_theta* theta, const vst
 }
 
 }  // namespace
+
+// C = A B^T-shaped products of the mixed VIF gradient on the tensor cores:
+// C[i][c] = sum_p A[i][p] B[c][p], A FP32 [n][k] (row stride lda), B from the
+// FP64 k x k matrix M (bmode 1: M itself; 2: M^T of a lower-triangular M),
+// split_terms = 3 or 6 as in the mixed NLL.  Uses the NLL's operand-part
+// buffers, free once U is formed.
+vst_status tc_product(const float* A, int64_t lda, int64_t n, const double* M, int bmode, int k, float* C,
+                      int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
+  if (n <= 0) return VST_OK;
+  if (bmode != 1 && bmode != 2) return fail(VST_EINVAL, "bad operand mode %d", bmode);
+  if (split_terms == 3)
+    return bmode == 1 ? tc_product_P<2, 256, 1>(A, lda, n, M, k, C, vbase, V, hdr, st)
+                      : tc_product_P<2, 256, 2>(A, lda, n, M, k, C, vbase, V, hdr, st);
+  return bmode == 1 ? tc_product_P<3, 128, 1>(A, lda, n, M, k, C, vbase, V, hdr, st)
+                    : tc_product_P<3, 128, 2>(A, lda, n, M, k, C, vbase, V, hdr, st);
+}
 
 // U (FP32, [n][k]) of the mixed form on the tensor cores; split_terms = 3 or 6.
 // Needs X = L^{-1}, the day range and the day lag table already in place.
