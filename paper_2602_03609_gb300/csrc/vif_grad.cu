@@ -58,7 +58,7 @@ constexpr int kChunks = kDgemmChunks;
 
 struct GradLayout {
   size_t LinvM, Minv, Y, GU, H, abar, dbar, eps, beta, qd, wv, svec, spart, btil, roff, rcur, rent, bsum,
-      t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, ltab, total;
+      t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, ltab, ltabf, xyf, xykf, total;
 };
 
 GradLayout grad_layout(int64_t n, int m, int64_t k) {
@@ -99,6 +99,9 @@ GradLayout grad_layout(int64_t n, int m, int64_t k) {
   G.t2part = take(8 * 4 * 4096);
   G.grows = take(8 * 8);
   G.ltab = take(sizeof(LagD) * (size_t)kVifMaxDays * kk);
+  G.ltabf = take(16 * (size_t)kVifMaxDays * kk);
+  G.xyf = take(8 * nn);
+  G.xykf = take(8 * kk);
   G.total = off;
   return G;
 }
@@ -317,13 +320,22 @@ __device__ __forceinline__ void cov_derivs(const DevTheta& th, double dx, double
 // lag factors (P, G, Qa, L) of Eq. (2) per (data day dmin + d, inducing point
 // p), FP64, when every data time is a whole day within kVifMaxDays days (the
 // day range of the low-rank step, info)
-__global__ void day_factors_kernel(const double* tk, int k, DevTheta th, const int64_t* info, LagD* tab) {
+__global__ void day_factors_kernel(const double* tk, int k, DevTheta th, const int64_t* info, LagD* tab,
+                                   float4* tabf) {
   const int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (info[2] == 0) return;
   if (id >= info[1] * k) return;
   const int64_t d = id / k;
   const int p = (int)(id % k);
-  tab[id] = lag_factors(th, (double)(info[0] + d) - tk[p]);
+  const LagD f = lag_factors(th, (double)(info[0] + d) - tk[p]);
+  tab[id] = f;
+  tabf[id] = make_float4((float)f.P, (float)f.G, (float)f.Qa, (float)f.L);
+}
+
+// coordinates in FP32 (the mixed form's derivative term)
+__global__ void coords_f32_kernel(const double* xy, int64_t n, float2* xyf) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    xyf[i] = make_float2((float)xy[2 * i], (float)xy[2 * i + 1]);
 }
 
 // the derivatives of Eq. (2) from given lag factors; T = float evaluates the
@@ -354,25 +366,68 @@ __device__ __forceinline__ void cov_derivs_f(const DevTheta& th, const LagD& f, 
 }
 
 // sum over (i, p) of H[i][p] dSigma_nk[i][p]/dtheta, per block partials;
-// the lag factors from the day table when info says it holds
+// one row per block at a time, threads over p; the lag factors from the day
+// table when info says it holds.  T = float: the derivatives and 32-term sums
+// in FP32 (FP32 coordinates and table), folded into FP64.
 template <int NU, typename T>
 __global__ void term1_kernel(int64_t n, int k, const double* xy, const double* t, const double* xyk,
-                             const double* tk, DevTheta th, const LagD* tab, const int64_t* info, const T* H,
-                             double* part) {
+                             const double* tk, DevTheta th, const LagD* tab, const float4* tabf, const float2* xyf,
+                             const float2* xykf, const int64_t* info, const T* H, double* part) {
   __shared__ double sh[4][256];
   double acc[4] = {0, 0, 0, 0};
-  const int64_t total = n * k;
   const bool use_tab = info[2] != 0;
   const int64_t d0 = info[0];
-  for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = q / k;
-    const int p = (int)(q - i * k);
-    const LagD f = use_tab ? tab[((int64_t)t[i] - d0) * k + p] : lag_factors(th, t[i] - tk[p]);
-    double d[4];
-    cov_derivs_f<NU, T>(th, f, xy[2 * i] - xyk[2 * p], xy[2 * i + 1] - xyk[2 * p + 1], d);
-    const double h = (double)H[q];
+  if constexpr (std::is_same<T, float>::value) {
+    const float inv_s1 = (float)(1.0 / th.sigma1sq), inv_c = (float)(1.0 / th.c);
+    const float pf = (float)th.p, hg = (float)(0.5 * th.gamma);
+    float fa[4] = {0.f, 0.f, 0.f, 0.f};
+    int cnt = 0;
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+      const float2 xi = xyf[i];
+      const int64_t day = use_tab ? (int64_t)t[i] - d0 : 0;
+      for (int p = threadIdx.x; p < k; p += blockDim.x) {
+        float P, G, Qa, L;
+        if (use_tab) {
+          const float4 f = tabf[day * k + p];
+          P = f.x; G = f.y; Qa = f.z; L = f.w;
+        } else {
+          const LagD f = lag_factors(th, t[i] - tk[p]);
+          P = (float)f.P; G = (float)f.G; Qa = (float)f.Qa; L = (float)f.L;
+        }
+        const float2 zp = xykf[p];
+        const float dx = xi.x - zp.x, dy = xi.y - zp.y;
+        const float x = G * sqrtf(dx * dx + dy * dy);
+        const float E = expf(-x);
+        const float C = P * matern_M<NU, float>(x, E);
+        const float X = P * matern_xdM<NU, float>(x, E);
+        const float h = H[i * k + p];
+        fa[0] = fmaf(h, C * inv_s1, fa[0]);
+        fa[1] = fmaf(h, X * inv_c, fa[1]);
+        fa[2] = fmaf(h, Qa * (-pf * C - hg * X), fa[2]);
+        fa[3] = fmaf(h, -L * (C + 0.5f * X), fa[3]);
+        if (++cnt == 32) {
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[j] = fma(h, d[j], acc[j]);
+          for (int j = 0; j < 4; ++j) {
+            acc[j] += (double)fa[j];
+            fa[j] = 0.f;
+          }
+          cnt = 0;
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] += (double)fa[j];
+  } else {
+    for (int64_t i = blockIdx.x; i < n; i += gridDim.x) {
+      for (int p = threadIdx.x; p < k; p += blockDim.x) {
+        const LagD f = use_tab ? tab[((int64_t)t[i] - d0) * k + p] : lag_factors(th, t[i] - tk[p]);
+        double d[4];
+        cov_derivs_f<NU, double>(th, f, xy[2 * i] - xyk[2 * p], xy[2 * i + 1] - xyk[2 * p + 1], d);
+        const double h = (double)H[i * k + p];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[j] = fma(h, d[j], acc[j]);
+      }
+    }
   }
 #pragma unroll
   for (int j = 0; j < 4; ++j) sh[j][threadIdx.x] = acc[j];
@@ -571,17 +626,26 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
   } else {
     gemm_nn<T>(PT(G.GU), k, XT, k, PT(G.H), k, n, k, k, true, st);
   }
-  const int nb1 = (int)std::min<int64_t>((n * k + 255) / 256, 4096);
+  const int nb1 = (int)std::min<int64_t>(n, 4096);
   {
     const int64_t* info = reinterpret_cast<const int64_t*>(vb + V.dinfo);  // day range of the low-rank step
     LagD* tab = reinterpret_cast<LagD*>(gb + G.ltab);
-    day_factors_kernel<<<(unsigned)((kVifMaxDays * (int64_t)k + 255) / 256), 256, 0, st>>>(ind->t, k, th, info, tab);
-    if (nu == 0)
-      term1_kernel<0, T><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, tab, info, PT(G.H), P(G.t1part));
-    else if (nu == 1)
-      term1_kernel<1, T><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, tab, info, PT(G.H), P(G.t1part));
-    else
-      term1_kernel<2, T><<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, tab, info, PT(G.H), P(G.t1part));
+    float4* tabf = reinterpret_cast<float4*>(gb + G.ltabf);
+    float2* xyf = reinterpret_cast<float2*>(gb + G.xyf);
+    float2* xykf = reinterpret_cast<float2*>(gb + G.xykf);
+    day_factors_kernel<<<(unsigned)((kVifMaxDays * (int64_t)k + 255) / 256), 256, 0, st>>>(ind->t, k, th, info, tab,
+                                                                                            tabf);
+    if constexpr (F32) {
+      coords_f32_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 4096), 256, 0, st>>>(pts->xy, n, xyf);
+      coords_f32_kernel<<<(k + 255) / 256, 256, 0, st>>>(ind->xy, k, xykf);
+    }
+    auto t1 = [&](auto kern) {
+      kern<<<nb1, 256, 0, st>>>(n, k, pts->xy, pts->t, ind->xy, ind->t, th, tab, tabf, xyf, xykf, info, PT(G.H),
+                                P(G.t1part));
+    };
+    if (nu == 0) t1(term1_kernel<0, T>);
+    else if (nu == 1) t1(term1_kernel<1, T>);
+    else t1(term1_kernel<2, T>);
   }
   gemm_tn<T>(PT(G.H), k, U, k, n, k, k, false, P(G.Jpart), P(G.J), st);
   // K' = L^T J, Psi, Omega = X^T (Psi X), term2 = <Omega, dSigma_kk>
