@@ -250,7 +250,9 @@ __global__ void rsort_kernel(int64_t n, const int64_t* off, int2* ent) {
 
 // per row i: alpha_i = sqrt(D_i) W_i (into `alpha`), and Phi_i = F_i - 2 gamma_i
 // (in place over Y_i), F_i = (Y_i - eps_i s) / sqrt(D_i), gamma_i = Dbar_i
-// alpha_i + beta_i / 2, beta_i = sum_q b~_iq U_N(i)_q.  One warp per row.
+// alpha_i + beta_i / 2, beta_i = sum_q b~_iq U_N(i)_q.  One warp per row; the
+// neighbours' U rows are streamed one at a time (contiguous, 32 columns per
+// lane in registers, blocks of 1024 columns).
 template <typename T>
 __global__ void __launch_bounds__(256) phi_kernel(int64_t n, int m, int k, const int32_t* nn,
                                                   const int32_t* nn_cnt, const double* D, const double* dbar,
@@ -263,23 +265,39 @@ __global__ void __launch_bounds__(256) phi_kernel(int64_t n, int m, int k, const
     const int cnt = min(max(nn_cnt[i], 0), m);
     const double Di = D[i], sd = 1.0 / sqrt(Di), sq = sqrt(Di), db = dbar[i], ei = eps[i];
     const T* Wi = WE + i * (int64_t)(k + 1);
-    for (int c = lane; c < k; c += 32) {
-      T bt = T(0);
+    for (int cb = 0; cb < k; cb += 1024) {
+      T bt[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) bt[u] = T(0);
       for (int q = 0; q < cnt; ++q) {
         const int j = nn[i * m + q];
-        if (j >= 0 && j < i) bt = fma((T)btil[i * m + q], U[(int64_t)j * k + c], bt);
+        if (j < 0 || j >= i) continue;
+        const T wq = (T)btil[i * m + q];
+        const T* Uj = U + (int64_t)j * k + cb;
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const int c = u * 32 + lane;
+          if (cb + c < k) bt[u] = fma(wq, Uj[c], bt[u]);
+        }
       }
-      const double be = (double)bt;
-      const double al = sq * (double)Wi[c];
-      const double F = ((double)Y[i * k + c] - ei * svec[c]) * sd;
-      Y[i * k + c] = (T)(F - 2.0 * fma(db, al, 0.5 * be));
-      alpha[i * k + c] = (T)al;
+#pragma unroll
+      for (int u = 0; u < 32; ++u) {
+        const int c = cb + u * 32 + lane;
+        if (c < k) {
+          const double al = sq * (double)Wi[c];
+          const double F = ((double)Y[i * k + c] - ei * svec[c]) * sd;
+          Y[i * k + c] = (T)(F - 2.0 * fma(db, al, 0.5 * (double)bt[u]));
+          alpha[i * k + c] = (T)al;
+        }
+      }
     }
   }
 }
 
 // G_U[r] = Phi_r - sum over the reverse entries (i, q) of r of
-// (A_iq Phi_i + b~_iq alpha_i).  One warp per row, 32 columns at a time.
+// (A_iq Phi_i + b~_iq alpha_i).  One warp per row; each entry's Phi_i and
+// alpha_i rows are streamed contiguously into 32 columns per lane held in
+// registers (blocks of 1024 columns).
 template <typename T>
 __global__ void __launch_bounds__(256) gu_kernel(int64_t n, int m, int k, const int64_t* off, const int2* ent,
                                                  const double* A, const double* btil, const T* Phi,
@@ -289,16 +307,31 @@ __global__ void __launch_bounds__(256) gu_kernel(int64_t n, int m, int k, const 
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t r = w; r < n; r += nw) {
     const int64_t a = off[r], b = off[r + 1];
-    for (int c = lane; c < k; c += 32) {
-      T acc = Phi[r * k + c];
+    for (int cb = 0; cb < k; cb += 1024) {
+      T acc[32];
+#pragma unroll
+      for (int u = 0; u < 32; ++u) {
+        const int c = cb + u * 32 + lane;
+        acc[u] = c < k ? Phi[r * k + c] : T(0);
+      }
       for (int64_t x = a; x < b; ++x) {
         const int2 en = ent[x];
         const int64_t i = en.x;
         const int64_t iq = i * m + en.y;
-        acc = fma(-(T)A[iq], Phi[i * k + c], acc);
-        acc = fma(-(T)btil[iq], alpha[i * k + c], acc);
+        const T na = -(T)A[iq], nb = -(T)btil[iq];
+        const T* Pi = Phi + i * k + cb;
+        const T* Ai = alpha + i * k + cb;
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const int c = u * 32 + lane;
+          if (cb + c < k) acc[u] = fma(nb, Ai[c], fma(na, Pi[c], acc[u]));
+        }
       }
-      GU[r * k + c] = acc;
+#pragma unroll
+      for (int u = 0; u < 32; ++u) {
+        const int c = cb + u * 32 + lane;
+        if (c < k) GU[r * k + c] = acc[u];
+      }
     }
   }
 }
