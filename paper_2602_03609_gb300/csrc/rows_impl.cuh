@@ -43,7 +43,7 @@
 
 namespace vst {
 
-// kModeVifAdj (FP64 only): the VIF gradient's pass over the residual blocks,
+// kModeVifAdj: the VIF gradient's pass over the residual blocks (FP64, or mixed),
 // with the per-row adjoints of A_i and D_i given (abar, dbar)
 enum RowMode { kModeNll = 0, kModeNllGrad = 1, kModeFactor = 2, kModeVifAdj = 3 };
 
@@ -259,7 +259,8 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     const float4 qj = __ldg(reinterpret_cast<const float4*>(pp + src) + 1);
     const int tdj = __float_as_int(qj.z);
     allint = __all_sync(kFull, __float_as_int(qj.w) != 0);
-    if (MODE != kModeFactor && valid) yl = df{qj.x, qj.y};
+    if (MODE == kModeVifAdj) yl = (lane < cnt) ? df_split(g.abar[ri * m + lane]) : df{0.0f, 0.0f};
+    else if (MODE != kModeFactor && valid) yl = df{qj.x, qj.y};
     if (lane < PM) {
       Pos<T> p;
       p.ox = df_diff(cj.x, cj.y, ci.x, ci.y);
@@ -342,7 +343,9 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
           }
           const df dx = df_two_sum(pr.ox, -pc.ox), dy = df_two_sum(pr.oy, -pc.oy);
           const df xx = dfm_mul(G2, dfm_sqrt(dfm_add(dfm_mul(dx, dx), dfm_mul(dy, dy))));
-          const df cc = dfm_mul(P2, dfm_matern<NU>(xx, dfm_exp_neg(xx)));
+          const df ee = dfm_exp_neg(xx);
+          const df cc = dfm_mul(P2, dfm_matern<NU>(xx, ee));
+          if (MODE == kModeVifAdj) q1 = P2.hi * matern_xdM<NU, float>(xx.hi, ee.hi);  // P x M'(x)
           const float gv = g.gram_f ? g.gram_f[gi * NPAIR + e] : 0.f;
           const df t = df_two_sum(cc.hi, -gv);
           v = t.hi + (t.lo + cc.lo);
@@ -474,7 +477,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
 
   // forward solve z = L^{-1} y_local (NLL of the FP64 form; b for the gradient)
   T zj = T(0);
-  if ((!MIXED && MODE != kModeFactor) || MODE == kModeNllGrad) {
+  if ((!MIXED && MODE != kModeFactor) || MODE == kModeNllGrad || MODE == kModeVifAdj) {
     T accz = (lane < PM) ? yv : T(0);
 #pragma unroll
     for (int k = 0; k < PM; ++k) {
@@ -510,7 +513,11 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   double Dd = 0.0;    // FP64 value of D_i (factor output)
   T Dt, rt;           // D_i and r_i in T for the adjoint weights
   df a_ref = {0.f, 0.f};  // mixed: refined A_i entry of this lane
-  if constexpr (MIXED) {
+  if constexpr (MIXED && MODE == kModeVifAdj) {
+    // the adjoint pass needs neither D_i nor r_i (Dbar is given): no refinement
+    Dt = T(1);
+    rt = T(0);
+  } else if constexpr (MIXED) {
     // One refinement step: res = k - K_N a (double-float), a += K_N^{-1} res.
     // The FP32 diagonal is sigma1^2 + nugget rounded once, the same way for
     // every row; the residual and D use its double-float value (dg_hi, dg_lo)
@@ -648,6 +655,8 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
         T Kv, Xv;  // P M(x) and P x M'(x)
         if constexpr (MIXED) {
           Kv = s.K[r][c];
+          // VIF: K holds the residual C - G; the derivative is that of C
+          if (MODE == kModeVifAdj && vif) Kv += g.gram_f[gi * NPAIR + e];
           Xv = s.q1[e];
         } else {
           const T x = s.xe[e][0], E = s.xe[e][1];

@@ -41,9 +41,7 @@ static cudaError_t launch_pm(int mode, const RowArgs& g, cudaStream_t st, int64_
   switch (mode) {
     case kModeNll: return launch_one<T, NU, PM, kModeNll>(g, st, w);
     case kModeNllGrad: return launch_one<T, NU, PM, kModeNllGrad>(g, st, w);
-    case kModeVifAdj:
-      if constexpr (std::is_same<T, double>::value) return launch_one<T, NU, PM, kModeVifAdj>(g, st, w);
-      return cudaErrorInvalidValue;
+    case kModeVifAdj: return launch_one<T, NU, PM, kModeVifAdj>(g, st, w);
     default: return launch_one<T, NU, PM, kModeFactor>(g, st, w);
   }
 }

@@ -622,12 +622,29 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
     g.abar = P(G.abar);
     g.dbar = P(G.dbar);
     g.btil = P(G.btil);
-    apply_launch_shape(g, 0, VST_FP64, nu, m + 1);
-    int64_t w = 0;
-    cudaError_t e = launch_rows(false, nu, m + 1, kModeVifAdj, g, st, &w);
-    if (e != cudaSuccess) return cuda_fail(e, "VIF adjoint row kernel");
-    if (w > kMaxPartialWarps) return fail(VST_EINTERNAL, "too many warps");
-    launch_reduce_partials(g.partial, w, g.partial, 0, 0.0, P(G.grows) + 5, P(G.grows), st);
+    int64_t w = 0, w1 = 0;
+    cudaError_t e = cudaSuccess;
+    if constexpr (F32) {
+      // mixed row kernel (the NLL's per-point records and double-float lag
+      // table), then the FP64 kernel for the rows it flags
+      g.prep = reinterpret_cast<const PrepPt*>(base + L.prep);
+      g.lagdf = reinterpret_cast<const float4*>(vb + V.lagdf);
+      apply_launch_shape(g, 0, VST_MIXED, nu, m + 1);
+      e = cudaMemsetAsync(g.flag, 0, (size_t)n, st);
+      if (e == cudaSuccess) e = launch_rows(true, nu, m + 1, kModeVifAdj, g, st, &w);
+      if (e != cudaSuccess) return cuda_fail(e, "VIF adjoint row kernel");
+      g.partial = reinterpret_cast<double*>(base + L.partial) + kMaxPartialWarps * 8;
+      g.fallback_only = 1;
+      e = launch_rows(false, nu, m + 1, kModeVifAdj, g, st, &w1);
+      if (e != cudaSuccess) return cuda_fail(e, "VIF adjoint fallback kernel");
+    } else {
+      apply_launch_shape(g, 0, VST_FP64, nu, m + 1);
+      e = launch_rows(false, nu, m + 1, kModeVifAdj, g, st, &w);
+      if (e != cudaSuccess) return cuda_fail(e, "VIF adjoint row kernel");
+    }
+    if (w > kMaxPartialWarps || w1 > kMaxPartialWarps) return fail(VST_EINTERNAL, "too many warps");
+    double* part0 = reinterpret_cast<double*>(base + L.partial);
+    launch_reduce_partials(part0, w, part0 + kMaxPartialWarps * 8, w1, 0.0, P(G.grows) + 5, P(G.grows), st);
   }
   // Phi and alpha per row, then G_U through the reverse index
   phi_kernel<T><<<(unsigned)gridw, 256, 0, st>>>(n, m, k, nn, nn_cnt, D, P(G.dbar), P(G.eps), P(G.svec), WE,
