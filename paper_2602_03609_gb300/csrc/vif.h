@@ -40,13 +40,20 @@ __device__ __forceinline__ float cov32(const DevTheta& th, float dx, float dy, f
 vst_status lowrank_tc(const vst_points* pts, const vst_theta* theta, const vst_inducing* ind, int nu,
                       int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st);
 
-// residual-correlation neighbours (vif_knn.cu); base: the whole workspace
 // C[i][c] = sum_p A[i][p] B[c][p] on the tensor cores (vif_tc.cu), A FP32
 // [n][k] with row stride lda, B from the FP64 k x k matrix M (bmode 1: M; 2:
 // B[c][p] = M[p][c] of a lower-triangular M), C FP32 [n][k]
 vst_status tc_product(const float* A, int64_t lda, int64_t n, const double* M, int bmode, int k, float* C,
                       int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st);
 
+// C = A^T B (FP64 k x k) for FP32 A, B [n][k] (row stride k) on the tensor
+// cores (vif_tc.cu): split-K over the n rows, FP32 partials per K segment
+// summed in FP64; tmp: tc_gram_bytes(n, k) bytes of device scratch
+size_t tc_gram_bytes(int64_t n, int64_t k);
+vst_status tc_gram(const float* A, const float* B, int64_t n, int k, double* C, int split_terms, void* tmp,
+                   WsHeader* hdr, cudaStream_t st);
+
+// residual-correlation neighbours (vif_knn.cu); base: the whole workspace
 vst_status vif_knn(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,
                    int32_t* nn, int32_t* nn_cnt, int64_t* tie_rows, int64_t tie_cap, char* base,
                    WsHeader* hdr, cudaStream_t st);

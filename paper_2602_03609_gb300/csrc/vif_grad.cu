@@ -58,7 +58,7 @@ constexpr int kChunks = kDgemmChunks;
 
 struct GradLayout {
   size_t LinvM, Minv, Y, GU, H, abar, dbar, eps, beta, qd, wv, svec, spart, btil, roff, rcur, rent, bsum,
-      t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, ltab, ltabf, xyf, xykf, total;
+      t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, ltab, ltabf, xyf, xykf, tcg, total;
 };
 
 GradLayout grad_layout(int64_t n, int m, int64_t k) {
@@ -102,6 +102,7 @@ GradLayout grad_layout(int64_t n, int m, int64_t k) {
   G.ltabf = take(16 * (size_t)kVifMaxDays * kk);
   G.xyf = take(8 * nn);
   G.xykf = take(8 * kk);
+  G.tcg = take(tc_gram_bytes(n, k));
   G.total = off;
   return G;
 }
@@ -697,7 +698,13 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
     else if (nu == 1) t1(term1_kernel<1, T>);
     else t1(term1_kernel<2, T>);
   }
-  gemm_tn<T>(PT(G.H), k, U, k, n, k, k, false, P(G.Jpart), P(G.J), st);
+  if constexpr (F32) {
+    s = tc_gram(reinterpret_cast<const float*>(PT(G.H)), reinterpret_cast<const float*>(U), n, k, P(G.J), terms,
+                gb + G.tcg, hdr, st);
+    if (s != VST_OK) return s;
+  } else {
+    gemm_tn<T>(PT(G.H), k, U, k, n, k, k, false, P(G.Jpart), P(G.J), st);
+  }
   // K' = L^T J, Psi, Omega = X^T (Psi X), term2 = <Omega, dSigma_kk>
   gemm_tn(Lkk, k, P(G.J), k, k, k, k, true, P(G.Jpart), P(G.Kp), st);
   psi_kernel<<<(unsigned)((kk2 + 255) / 256), 256, 0, st>>>(k, P(G.Kp), P(G.Psi));

@@ -141,6 +141,52 @@ __global__ void split_b_kernel(const double* M, int k, int kp, int mode, __nv_bf
   }
 }
 
+// Transposed parts of an FP32 matrix S [n][k] (row stride lds):
+// T[j][c][i] = part j of S[i][c], [P][kp][np], zero for i >= n or c >= k.
+// One block of 256 threads per 64 x 64 tile, staged through shared memory so
+// that both the reads (along c) and the writes (along i) are contiguous.
+template <int P>
+__global__ void split_t_kernel(const float* S, int64_t lds, int64_t n, int k, int kp, int64_t np, __nv_bfloat16* T) {
+  __shared__ float tile[64][65];
+  const int64_t i0 = (int64_t)blockIdx.x * 64;
+  const int c0 = blockIdx.y * 64;
+  const int tc = threadIdx.x & 63, tr = threadIdx.x >> 6;
+#pragma unroll 4
+  for (int q = 0; q < 16; ++q) {
+    const int r = tr + 4 * q;
+    const int64_t i = i0 + r;
+    const int c = c0 + tc;
+    tile[r][tc] = (i < n && c < k) ? S[i * lds + c] : 0.0f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int item = threadIdx.x + 256 * q;
+    const int cr = item >> 3, g = item & 7;
+    __align__(16) __nv_bfloat16 o[P][8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      __nv_bfloat16 sp[P];
+      split_parts<P>(tile[g * 8 + e][cr], sp);
+#pragma unroll
+      for (int j = 0; j < P; ++j) o[j][e] = sp[j];
+    }
+#pragma unroll
+    for (int j = 0; j < P; ++j)
+      *reinterpret_cast<uint4*>(T + ((int64_t)j * kp + c0 + cr) * np + i0 + g * 8) =
+          *reinterpret_cast<const uint4*>(o[j]);
+  }
+}
+
+// C[a][b] = sum over segments of the FP32 partials, in FP64 and a fixed order
+__global__ void seg_sum_kernel(const float* part, int nseg, int64_t kk, double* C) {
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < kk; id += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nseg; ++q) s += (double)part[q * kk + id];
+    C[id] = s;
+  }
+}
+
 // double-float coordinates of the inducing points
 __global__ void ind_coords_kernel(const double* xyk, int k, float4* zf) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -215,10 +261,15 @@ struct SplitTerms<3> {
 // K range of a column tile: KMODE 0, B[c][p] = 0 for p > c (K up to the
 // tile's last column); 1, the whole K; 2, B[c][p] = 0 for p < c (K from the
 // tile's first column).  RPART: also the row sums of the squared outputs.
+// KMODE 3 is the split-K form of C = A^T B for A, B [n][k]: both operands
+// come as transposed parts [P][kp][n] (kp rows of K = n, padded to a
+// multiple of 64, passed as n); CTA b computes output tile b % tiles over the
+// K segment b / tiles of seg_kb blocks and writes its FP32 partial to
+// U + segment * k * k (rows and columns < k).
 template <int P, int BN, int STAGES, int KMODE = 0, bool RPART = true>
 __global__ void __launch_bounds__(128, 1)
     ugemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
-                    int k, int kp, float* U, double* rpart, WsHeader* hdr) {
+                    int k, int kp, float* U, double* rpart, WsHeader* hdr, int seg_kb) {
   using S = TcShape<P, BN, STAGES>;
   extern __shared__ unsigned char tc_smem[];
   const uint32_t raw = umma::smem_u32(tc_smem);
@@ -233,11 +284,30 @@ __global__ void __launch_bounds__(128, 1)
   // consecutive CTAs share the A tile (N tile fastest), so that its reads
   // across the kp / BN column tiles come from L2
   const int ntile = kp / BN;
-  const int64_t m0 = (int64_t)(blockIdx.x / ntile) * S::BM;
-  const int c0 = (int)(blockIdx.x % ntile) * BN;
-  const int kend = KMODE == 0 ? (kp < c0 + BN ? kp : c0 + BN) : kp;
-  const int kb0 = KMODE == 2 ? c0 / S::BK : 0;
-  const int nkb = (kend + S::BK - 1) / S::BK - kb0;
+  int64_t m0;
+  int c0, kb0, nkb;
+  int64_t a_rows = n;    // rows of one operand part in A's tensor map
+  int64_t out_rows = n;  // output rows, row stride k
+  float* out = U;
+  if constexpr (KMODE == 3) {
+    const int tiles = (kp / S::BM) * ntile;
+    const int tile = (int)(blockIdx.x % tiles);
+    const int seg = (int)(blockIdx.x / tiles);
+    m0 = (int64_t)(tile / ntile) * S::BM;
+    c0 = (tile % ntile) * BN;
+    const int total = (int)(n / S::BK);
+    kb0 = seg * seg_kb;
+    nkb = total - kb0 < seg_kb ? total - kb0 : seg_kb;
+    a_rows = kp;
+    out_rows = k;
+    out = U + (int64_t)seg * k * k;
+  } else {
+    m0 = (int64_t)(blockIdx.x / ntile) * S::BM;
+    c0 = (int)(blockIdx.x % ntile) * BN;
+    const int kend = KMODE == 0 ? (kp < c0 + BN ? kp : c0 + BN) : kp;
+    kb0 = KMODE == 2 ? c0 / S::BK : 0;
+    nkb = (kend + S::BK - 1) / S::BK - kb0;
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -277,7 +347,7 @@ __global__ void __launch_bounds__(128, 1)
         const uint32_t sa = base + s * S::STAGE_BYTES, sb = sa + P * S::A_BYTES;
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-          umma::tma_load_2d(sa + j * S::A_BYTES, &tmA, (kb0 + kb) * S::BK, (int)(j * n + m0), &full[s]);
+          umma::tma_load_2d(sa + j * S::A_BYTES, &tmA, (kb0 + kb) * S::BK, (int)(j * a_rows + m0), &full[s]);
           umma::tma_load_2d(sb + j * S::B_BYTES, &tmB, (kb0 + kb) * S::BK, j * kp + c0, &full[s]);
         }
       }
@@ -343,8 +413,8 @@ __global__ void __launch_bounds__(128, 1)
         if (cc + q < k) df_fma_acc(sq, u, df{u, 0.f});
       }
     }
-    if (i < n && cc < k) {
-      float* dst = U + i * k + cc;
+    if (i < out_rows && cc < k) {
+      float* dst = out + i * k + cc;
       if (vec && cc + 32 <= k) {
 #pragma unroll
         for (int q = 0; q < 32; q += 4)
@@ -357,7 +427,7 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
   }
-  if (RPART && i < n) rpart[i * ntile + c0 / BN] = df_to_double(sq);
+  if (RPART && i < out_rows) rpart[i * ntile + c0 / BN] = df_to_double(sq);
   if (!ok) report_error(hdr, VST_ETIMEOUT, m0);
   umma::fence_before_sync();
   __syncthreads();
@@ -416,7 +486,7 @@ cudaError_t launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t 
   const dim3 grid((unsigned)tiles);
   {
     ProfileScope ps(kProfVifGemm, st);
-    kern<<<grid, 128, S::SMEM, st>>>(ta, tb, n, k, kp, U, rpart, hdr);
+    kern<<<grid, 128, S::SMEM, st>>>(ta, tb, n, k, kp, U, rpart, hdr, 0);
   }
   rsum_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 65535), 256, 0, st>>>(rpart, n, kp / BN, s1, r);
   return cudaGetLastError();
@@ -447,9 +517,59 @@ vst_status tc_product_P(const float* A, int64_t lda, int64_t n, const double* M,
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core product attributes");
   const int64_t tiles = (n + S::BM - 1) / S::BM * (kp / BN);
   if (tiles > 0x7fffffff) return fail(VST_EINVAL, "too many tiles");
-  kern<<<(unsigned)tiles, 128, S::SMEM, st>>>(ta, tb, n, k, kp, C, nullptr, hdr);
+  kern<<<(unsigned)tiles, 128, S::SMEM, st>>>(ta, tb, n, k, kp, C, nullptr, hdr, 0);
   e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "tensor-core product");
+}
+
+// split-K shape of C = A^T B: output tiles, K blocks of 64 rows per segment
+// (enough segments for ~1024 CTAs, at most 32 blocks each) and segments
+struct GramShape {
+  int64_t np;
+  int tiles, seg_kb, nseg;
+};
+GramShape gram_shape(int64_t n, int64_t k, int P) {
+  GramShape g{};
+  const int64_t kp = vif_kp(k);
+  g.np = (n + 63) / 64 * 64;
+  const int BN = P == 2 ? 256 : 128;
+  g.tiles = (int)((kp / 128) * (kp / BN));
+  const int64_t kb = g.np / 64;
+  g.seg_kb = (int)std::min<int64_t>(32, std::max<int64_t>(1, (kb * g.tiles + 1023) / 1024));
+  g.nseg = (int)((kb + g.seg_kb - 1) / g.seg_kb);
+  return g;
+}
+
+template <int P, int BN>
+vst_status tc_gram_P(const float* A, const float* B, int64_t n, int k, double* C, char* tmp, WsHeader* hdr,
+                     cudaStream_t st) {
+  using S = TcShape<P, BN, 2>;
+  const int kp = vif_kp(k);
+  const GramShape g = gram_shape(n, k, P);
+  const size_t part_elems = (size_t)P * kp * g.np;
+  __nv_bfloat16* At = reinterpret_cast<__nv_bfloat16*>(tmp);
+  __nv_bfloat16* Bt = At + part_elems;
+  // partials after the three-part operand region (tc_gram_bytes)
+  float* part = reinterpret_cast<float*>(tmp + ((size_t)4 * 3 * kp * g.np + 255) / 256 * 256);
+  const dim3 tgrid((unsigned)(g.np / 64), (unsigned)(kp / 64));
+  split_t_kernel<P><<<tgrid, 256, 0, st>>>(A, k, n, k, kp, g.np, At);
+  split_t_kernel<P><<<tgrid, 256, 0, st>>>(B, k, n, k, kp, g.np, Bt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "transposed split kernels");
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, At, (uint64_t)P * kp, (uint64_t)g.np, S::BM) ||
+      !make_map(&tb, Bt, (uint64_t)P * kp, (uint64_t)g.np, BN))
+    return fail(VST_ECUDA, "cuTensorMapEncodeTiled unavailable or rejected the operand layout");
+  auto kern = ugemm_tc_kernel<P, BN, 2, 3, false>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core product attributes");
+  const int64_t ctas = (int64_t)g.tiles * g.nseg;
+  if (ctas > 0x7fffffff) return fail(VST_EINVAL, "too many tiles");
+  kern<<<(unsigned)ctas, 128, S::SMEM, st>>>(ta, tb, g.np, k, kp, part, nullptr, hdr, g.seg_kb);
+  const int64_t kk = (int64_t)k * k;
+  seg_sum_kernel<<<(unsigned)std::min<int64_t>((kk + 255) / 256, 8192), 256, 0, st>>>(part, g.nseg, kk, C);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? VST_OK : cuda_fail(e, "tensor-core A^T B");
 }
 
 template <int P>
@@ -506,6 +626,29 @@ vst_status tc_product(const float* A, int64_t lda, int64_t n, const double* M, i
                       : tc_product_P<2, 256, 2>(A, lda, n, M, k, C, vbase, V, hdr, st);
   return bmode == 1 ? tc_product_P<3, 128, 1>(A, lda, n, M, k, C, vbase, V, hdr, st)
                     : tc_product_P<3, 128, 2>(A, lda, n, M, k, C, vbase, V, hdr, st);
+}
+
+// scratch of tc_gram: both transposed operands (three parts) and the FP32
+// partials of the largest segment count
+size_t tc_gram_bytes(int64_t n, int64_t k) {
+  if (n <= 0 || k <= 0) return 256;
+  const int64_t kp = vif_kp(k);
+  const int64_t np = (n + 63) / 64 * 64;
+  const size_t parts = (size_t)4 * 3 * kp * np;  // 2 operands x 3 parts x 2 bytes
+  const int nseg = std::max(gram_shape(n, k, 2).nseg, gram_shape(n, k, 3).nseg);
+  return (parts + 255) / 256 * 256 + (size_t)4 * nseg * k * k;
+}
+
+// C = A^T B (FP64 k x k) for FP32 A, B [n][k] (row stride k) on the tensor
+// cores: transposed split parts, split-K tiles over the point index with FP32
+// partials per segment, partials summed in FP64; split_terms = 3 or 6;
+// tmp holds tc_gram_bytes(n, k) bytes.
+vst_status tc_gram(const float* A, const float* B, int64_t n, int k, double* C, int split_terms, void* tmp,
+                   WsHeader* hdr, cudaStream_t st) {
+  if (k <= 0) return VST_OK;
+  if (n <= 0) return cudaMemsetAsync(C, 0, sizeof(double) * k * k, st) == cudaSuccess ? VST_OK : VST_ECUDA;
+  char* t = static_cast<char*>(tmp);
+  return split_terms == 3 ? tc_gram_P<2, 256>(A, B, n, k, C, t, hdr, st) : tc_gram_P<3, 128>(A, B, n, k, C, t, hdr, st);
 }
 
 // U (FP32, [n][k]) of the mixed form on the tensor cores; split_terms = 3 or 6.
