@@ -1010,6 +1010,11 @@ static vst_status vif_nll_T(const vst_points* pts, const vst_theta* theta, int m
   const int64_t chunk = std::max<int64_t>((n + kVifSyrkChunks - 1) / kVifSyrkChunks, 1);
   const int nchunk = (int)std::min<int64_t>(kVifSyrkChunks, (n + chunk - 1) / chunk);
   const int nb = (kk + 63) / 64;
+  // [W e]^T [W e] stays on the FP32/FP64 SIMT kernel in both forms: the
+  // Woodbury quadratic form e^T e - v^T M^{-1} v cancels two O(n) terms, and
+  // the tensor cores' internal FP32 summation (not round-to-nearest) left
+  // |dNLL|/n above 1e-6 at n = 30,000, k = 1000 even with double-float
+  // drains every 128 rows
   if (n > 0) {
     ProfileScope ps(kProfVifSyrk, st);
     syrk_kernel<T><<<dim3(nb, nb, nchunk), 256, 0, st>>>(WE, n, kk, chunk, part);

@@ -46,12 +46,15 @@ vst_status lowrank_tc(const vst_points* pts, const vst_theta* theta, const vst_i
 vst_status tc_product(const float* A, int64_t lda, int64_t n, const double* M, int bmode, int k, float* C,
                       int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st);
 
-// C = A^T B (FP64 k x k) for FP32 A, B [n][k] (row stride k) on the tensor
-// cores (vif_tc.cu): split-K over the n rows, FP32 partials per K segment
-// summed in FP64; tmp: tc_gram_bytes(n, k) bytes of device scratch
-size_t tc_gram_bytes(int64_t n, int64_t k);
-vst_status tc_gram(const float* A, const float* B, int64_t n, int k, double* C, int split_terms, void* tmp,
-                   WsHeader* hdr, cudaStream_t st);
+// C = A^T B (FP64 kc x kc) for FP32 A, B [n][kc] (row strides lda, ldb) on
+// the tensor cores (vif_tc.cu): split K over the n rows, double-float drains
+// of the tensor-memory accumulators, segments summed in FP64 in a fixed order.
+// tmp: the first tc_gram_part_offset(n, kc) bytes of a tc_gram_bytes(n, kc)
+// region, part: the rest (16 kc^2 doubles).
+size_t tc_gram_bytes(int64_t n, int64_t kc);
+size_t tc_gram_part_offset(int64_t n, int64_t kc);
+vst_status tc_gram(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t n, int kc, double* C,
+                   int split_terms, void* tmp, double* part, WsHeader* hdr, cudaStream_t st);
 
 // residual-correlation neighbours (vif_knn.cu); base: the whole workspace
 vst_status vif_knn(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,

@@ -699,8 +699,8 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
     else t1(term1_kernel<2, T>);
   }
   if constexpr (F32) {
-    s = tc_gram(reinterpret_cast<const float*>(PT(G.H)), reinterpret_cast<const float*>(U), n, k, P(G.J), terms,
-                gb + G.tcg, hdr, st);
+    s = tc_gram(reinterpret_cast<const float*>(PT(G.H)), k, reinterpret_cast<const float*>(U), k, n, k, P(G.J), terms,
+                gb + G.tcg, P(G.tcg + tc_gram_part_offset(n, k)), hdr, st);
     if (s != VST_OK) return s;
   } else {
     gemm_tn<T>(PT(G.H), k, U, k, n, k, k, false, P(G.Jpart), P(G.J), st);

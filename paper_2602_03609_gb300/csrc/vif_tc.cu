@@ -178,15 +178,6 @@ __global__ void split_t_kernel(const float* S, int64_t lds, int64_t n, int k, in
   }
 }
 
-// C[a][b] = sum over segments of the FP32 partials, in FP64 and a fixed order
-__global__ void seg_sum_kernel(const float* part, int nseg, int64_t kk, double* C) {
-  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < kk; id += (int64_t)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int q = 0; q < nseg; ++q) s += (double)part[q * kk + id];
-    C[id] = s;
-  }
-}
-
 // double-float coordinates of the inducing points
 __global__ void ind_coords_kernel(const double* xyk, int k, float4* zf) {
   const int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -261,15 +252,10 @@ struct SplitTerms<3> {
 // K range of a column tile: KMODE 0, B[c][p] = 0 for p > c (K up to the
 // tile's last column); 1, the whole K; 2, B[c][p] = 0 for p < c (K from the
 // tile's first column).  RPART: also the row sums of the squared outputs.
-// KMODE 3 is the split-K form of C = A^T B for A, B [n][k]: both operands
-// come as transposed parts [P][kp][n] (kp rows of K = n, padded to a
-// multiple of 64, passed as n); CTA b computes output tile b % tiles over the
-// K segment b / tiles of seg_kb blocks and writes its FP32 partial to
-// U + segment * k * k (rows and columns < k).
 template <int P, int BN, int STAGES, int KMODE = 0, bool RPART = true>
 __global__ void __launch_bounds__(128, 1)
     ugemm_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t n,
-                    int k, int kp, float* U, double* rpart, WsHeader* hdr, int seg_kb) {
+                    int k, int kp, float* U, double* rpart, WsHeader* hdr) {
   using S = TcShape<P, BN, STAGES>;
   extern __shared__ unsigned char tc_smem[];
   const uint32_t raw = umma::smem_u32(tc_smem);
@@ -284,30 +270,11 @@ __global__ void __launch_bounds__(128, 1)
   // consecutive CTAs share the A tile (N tile fastest), so that its reads
   // across the kp / BN column tiles come from L2
   const int ntile = kp / BN;
-  int64_t m0;
-  int c0, kb0, nkb;
-  int64_t a_rows = n;    // rows of one operand part in A's tensor map
-  int64_t out_rows = n;  // output rows, row stride k
-  float* out = U;
-  if constexpr (KMODE == 3) {
-    const int tiles = (kp / S::BM) * ntile;
-    const int tile = (int)(blockIdx.x % tiles);
-    const int seg = (int)(blockIdx.x / tiles);
-    m0 = (int64_t)(tile / ntile) * S::BM;
-    c0 = (tile % ntile) * BN;
-    const int total = (int)(n / S::BK);
-    kb0 = seg * seg_kb;
-    nkb = total - kb0 < seg_kb ? total - kb0 : seg_kb;
-    a_rows = kp;
-    out_rows = k;
-    out = U + (int64_t)seg * k * k;
-  } else {
-    m0 = (int64_t)(blockIdx.x / ntile) * S::BM;
-    c0 = (int)(blockIdx.x % ntile) * BN;
-    const int kend = KMODE == 0 ? (kp < c0 + BN ? kp : c0 + BN) : kp;
-    kb0 = KMODE == 2 ? c0 / S::BK : 0;
-    nkb = (kend + S::BK - 1) / S::BK - kb0;
-  }
+  const int64_t m0 = (int64_t)(blockIdx.x / ntile) * S::BM;
+  const int c0 = (int)(blockIdx.x % ntile) * BN;
+  const int kend = KMODE == 0 ? (kp < c0 + BN ? kp : c0 + BN) : kp;
+  const int kb0 = KMODE == 2 ? c0 / S::BK : 0;
+  const int nkb = (kend + S::BK - 1) / S::BK - kb0;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -347,7 +314,7 @@ __global__ void __launch_bounds__(128, 1)
         const uint32_t sa = base + s * S::STAGE_BYTES, sb = sa + P * S::A_BYTES;
 #pragma unroll
         for (int j = 0; j < P; ++j) {
-          umma::tma_load_2d(sa + j * S::A_BYTES, &tmA, (kb0 + kb) * S::BK, (int)(j * a_rows + m0), &full[s]);
+          umma::tma_load_2d(sa + j * S::A_BYTES, &tmA, (kb0 + kb) * S::BK, (int)(j * n + m0), &full[s]);
           umma::tma_load_2d(sb + j * S::B_BYTES, &tmB, (kb0 + kb) * S::BK, j * kp + c0, &full[s]);
         }
       }
@@ -413,8 +380,8 @@ __global__ void __launch_bounds__(128, 1)
         if (cc + q < k) df_fma_acc(sq, u, df{u, 0.f});
       }
     }
-    if (i < out_rows && cc < k) {
-      float* dst = out + i * k + cc;
+    if (i < n && cc < k) {
+      float* dst = U + i * k + cc;
       if (vec && cc + 32 <= k) {
 #pragma unroll
         for (int q = 0; q < 32; q += 4)
@@ -427,11 +394,251 @@ __global__ void __launch_bounds__(128, 1)
       }
     }
   }
-  if (RPART && i < out_rows) rpart[i * ntile + c0 / BN] = df_to_double(sq);
+  if (RPART && i < n) rpart[i * ntile + c0 / BN] = df_to_double(sq);
   if (!ok) report_error(hdr, VST_ETIMEOUT, m0);
   umma::fence_before_sync();
   __syncthreads();
   if (warp == 0) umma::tmem_dealloc(tmem, 2 * BN);
+}
+
+// ---- C = A^T B over the rows of A and B (split K, warp-specialised) ----
+//
+// The operands come as transposed BF16 parts [P][kp][np] (split_t_kernel):
+// row c of part j holds part j of column c over the np rows (zero padded), so
+// C[a][b] = sum_i At[a][i] Bt[b][i] is a K-major product with K = the row
+// index.  A CTA computes one 128 x 128 output tile over one K segment.
+// Warp 0 issues the TMA loads; warp 1 issues the MMAs into two TMEM buffers,
+// each a main accumulator (a0 b0) and a correction accumulator (the other
+// kept part products) of 128 columns; warps 4-11 drain a buffer every
+// kGramDrainKb K blocks into double-float sums held in registers (warp w
+// reads TMEM lanes 32 (w % 4) .. + 31 = tile rows, and columns
+// 64 ((w - 4) / 4) .. + 63) while the MMAs fill the other buffer.  Warps 2-3
+// only fill out the first warpgroup, which gives registers to the two
+// draining warpgroups (384 threads launch with 168 registers each, 64,512 in
+// all; 128 x 64 + 256 x 216 = 63,488).  The
+// tensor core's FP32 accumulation is not round-to-nearest, so its error
+// grows with the number of accumulation steps; a drain every 128 rows keeps
+// each run to 8 steps, and the double-float sums carry ~48 bits over the
+// whole segment.  Each CTA writes its tile (rows and columns < kc) in FP64
+// to out[segment]; gram_sum_kernel adds the segments in a fixed order.
+constexpr int kGramDrainKb = 2;
+constexpr int kGramMaxSeg = 16;
+
+template <int P, int STAGES>
+struct GramTcShape {
+  static constexpr int BM = 128, BN = 128, BK = 64;
+  static constexpr int A_BYTES = BM * BK * 2;
+  static constexpr int B_BYTES = BN * BK * 2;
+  static constexpr int STAGE_BYTES = P * (A_BYTES + B_BYTES);
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 256 + 1024;  // + barriers, alignment slack
+  static constexpr int THREADS = 384;
+  static constexpr int REGS_LOW = 64, REGS_HIGH = 216;
+  static_assert(128 * REGS_LOW + 256 * REGS_HIGH <= THREADS * 168, "register split");
+  static_assert(STAGE_BYTES % 1024 == 0, "stage alignment");
+  static_assert(SMEM <= 232448, "shared memory");
+  static_assert(BM * (BN + 1) * 8 <= STAGES * STAGE_BYTES, "output tile staging");
+};
+
+template <int P, int STAGES>
+__global__ void __launch_bounds__(384, 1)
+    gram_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t np,
+                   int kc, int kp, int nseg, double* out, WsHeader* hdr) {
+  using S = GramTcShape<P, STAGES>;
+  extern __shared__ unsigned char tc_smem[];
+  const uint32_t raw = umma::smem_u32(tc_smem);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = tc_smem + (base - raw);
+  uint64_t* full = reinterpret_cast<uint64_t*>(gbase + STAGES * S::STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accf = empty + STAGES;  // [2] buffer filled
+  uint64_t* acce = accf + 2;        // [2] buffer drained
+  uint64_t* done = acce + 2;        // every MMA finished
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int T = kp / S::BM;
+  const int ntiles = T * T;
+  const int tile = (int)(blockIdx.x % ntiles), seg = (int)(blockIdx.x / ntiles);
+  const int tm = tile / T, tn = tile % T;
+  // this segment's K blocks: the first (kbt % nseg) segments take one more
+  const int64_t kbt = np / S::BK;
+  const int64_t per = kbt / nseg, rem = kbt % nseg;
+  const int64_t kb0 = seg * per + (seg < rem ? seg : rem);
+  const int nkb = (int)(per + (seg < rem ? 1 : 0));
+  const int ndr = (nkb + kGramDrainKb - 1) / kGramDrainKb;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      umma::mbar_init(&full[s], 1);
+      umma::mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      umma::mbar_init(&accf[b], 1);
+      umma::mbar_init(&acce[b], 8);
+    }
+    umma::mbar_init(done, 1);
+    umma::fence_mbar_init();
+  }
+  if (warp == 0) {
+    umma::tmem_alloc(umma::smem_u32(tslot), 512);
+    umma::tmem_relinquish();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  bool ok = true;
+  auto warp_wait = [&](uint64_t* bar, uint32_t parity) {
+    bool d = true;
+    if (lane == 0) d = umma::mbar_wait(bar, parity, kWaitLimitNs);
+    return __shfl_sync(0xffffffffu, d ? 1 : 0, 0) != 0;
+  };
+
+  if (warp < 4) {
+    umma::regs_dec<S::REGS_LOW>();
+    if (warp == 0) {
+      // producer
+      int issued = 0;
+      for (int kb = 0; kb < nkb; ++kb) {
+        const int s = kb % STAGES;
+        const uint32_t use = (uint32_t)(kb / STAGES);
+        if (use > 0 && !warp_wait(&empty[s], (use - 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        if (lane == 0) {
+          umma::mbar_arrive_expect_tx(&full[s], S::STAGE_BYTES);
+          const uint32_t sa = base + s * S::STAGE_BYTES, sb = sa + P * S::A_BYTES;
+          const int x = (int)((kb0 + kb) * S::BK);
+  #pragma unroll
+          for (int j = 0; j < P; ++j) {
+            umma::tma_load_2d(sa + j * S::A_BYTES, &tmA, x, j * kp + tm * S::BM, &full[s]);
+            umma::tma_load_2d(sb + j * S::B_BYTES, &tmB, x, j * kp + tn * S::BN, &full[s]);
+          }
+        }
+        __syncwarp();
+        ++issued;
+      }
+      if (!ok) {
+        // let the loads still in flight land before the CTA's shared memory goes
+        for (int kb = issued - STAGES < 0 ? 0 : issued - STAGES; kb < issued; ++kb)
+          warp_wait(&full[kb % STAGES], (uint32_t)(kb / STAGES) & 1u);
+      }
+    } else if (warp == 1) {
+      // MMA issuer
+      constexpr uint32_t idesc = umma::idesc_bf16_f32(S::BM, S::BN);
+      int kb = 0;
+      for (int d = 0; d < ndr && ok; ++d) {
+        const int b = d & 1;
+        const uint32_t u = (uint32_t)(d >> 1);
+        if (u > 0 && !warp_wait(&acce[b], (u - 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        umma::fence_after_sync();
+        const uint32_t tb = tmem + (uint32_t)(b * 256);
+        const int nk = nkb - d * kGramDrainKb < kGramDrainKb ? nkb - d * kGramDrainKb : kGramDrainKb;
+        uint32_t acc_main = 0, acc_corr = 0;
+        for (int j = 0; j < nk; ++j, ++kb) {
+          const int s = kb % STAGES;
+          const uint32_t use = (uint32_t)(kb / STAGES);
+          if (!warp_wait(&full[s], use & 1u)) {
+            ok = false;
+            break;
+          }
+          umma::fence_after_sync();
+          if (lane == 0) {
+            const uint32_t sa = base + s * S::STAGE_BYTES, sb = sa + P * S::A_BYTES;
+  #pragma unroll
+            for (int kk = 0; kk < S::BK / 16; ++kk) {
+  #pragma unroll
+              for (int q = 0; q < SplitTerms<P>::N; ++q) {
+                const uint64_t ad = umma::desc_kmajor_sw128(sa + SplitTerms<P>::a(q) * S::A_BYTES + kk * 32);
+                const uint64_t bd = umma::desc_kmajor_sw128(sb + SplitTerms<P>::b(q) * S::B_BYTES + kk * 32);
+                if (q == 0) {
+                  umma::mma_bf16(tb, ad, bd, idesc, acc_main);
+                  acc_main = 1;
+                } else {
+                  umma::mma_bf16(tb + S::BN, ad, bd, idesc, acc_corr);
+                  acc_corr = 1;
+                }
+              }
+            }
+            umma::mma_commit(&empty[s]);
+          }
+          __syncwarp();
+        }
+        if (!ok) break;
+        if (lane == 0) umma::mma_commit(&accf[b]);
+        __syncwarp();
+      }
+      // every MMA this thread issued has finished before the tensor memory is freed
+      if (lane == 0) umma::mma_commit(done);
+      __syncwarp();
+      if (!warp_wait(done, 0)) ok = false;
+    }
+  } else {
+    umma::regs_inc<S::REGS_HIGH>();
+    // drain warps
+    const int q4 = warp & 3, half = (warp - 4) >> 2;
+    float hi[64], lo[64];
+#pragma unroll
+    for (int c = 0; c < 64; ++c) hi[c] = lo[c] = 0.f;
+    for (int d = 0; d < ndr; ++d) {
+      const int b = d & 1;
+      if (!warp_wait(&accf[b], (uint32_t)(d >> 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      umma::fence_after_sync();
+      const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * 256 + half * 64);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        uint32_t v[8], w[8];
+        umma::tmem_ld_32x32b_x8(ta + c * 8, v);
+        umma::tmem_ld_32x32b_x8(ta + S::BN + c * 8, w);
+        umma::tmem_wait_ld();
+        if (c == 7) {
+          // the buffer is free for the next MMAs once its last columns are read
+          umma::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) umma::mbar_arrive(&acce[b]);
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const df t = df_two_sum(hi[c * 8 + e], __uint_as_float(v[e]));
+          hi[c * 8 + e] = t.hi;
+          lo[c * 8 + e] += t.lo + __uint_as_float(w[e]);
+        }
+      }
+    }
+    // the tile through shared memory (the stages are idle once the last
+    // buffer has been filled), then out to global memory row by row, coalesced
+    double* tsm = reinterpret_cast<double*>(gbase);
+    const int r = q4 * 32 + lane;
+#pragma unroll
+    for (int c = 0; c < 64; ++c) tsm[r * (S::BN + 1) + half * 64 + c] = (double)hi[c] + (double)lo[c];
+    asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight drain warps
+    double* dst = out + (int64_t)seg * kc * kc;
+    for (int e = threadIdx.x - 128; e < S::BM * S::BN; e += 256) {
+      const int a = tm * S::BM + e / S::BN, bc = tn * S::BN + e % S::BN;
+      if (a < kc && bc < kc) dst[(int64_t)a * kc + bc] = tsm[(e / S::BN) * (S::BN + 1) + e % S::BN];
+    }
+  }
+  if (!ok) report_error(hdr, VST_ETIMEOUT, (int64_t)blockIdx.x);
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, 512);
+}
+
+// C = the sum of the nseg FP64 partials (fixed order)
+__global__ void gram_sum_kernel(const double* part, int nseg, int kc, double* C) {
+  const int64_t kk = (int64_t)kc * kc;
+  for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < kk; id += (int64_t)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nseg; ++q) s += part[q * kk + id];
+    C[id] = s;
+  }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
@@ -486,7 +693,7 @@ cudaError_t launch_gemm(const __nv_bfloat16* A, const __nv_bfloat16* B, int64_t 
   const dim3 grid((unsigned)tiles);
   {
     ProfileScope ps(kProfVifGemm, st);
-    kern<<<grid, 128, S::SMEM, st>>>(ta, tb, n, k, kp, U, rpart, hdr, 0);
+    kern<<<grid, 128, S::SMEM, st>>>(ta, tb, n, k, kp, U, rpart, hdr);
   }
   rsum_kernel<<<(unsigned)std::min<int64_t>((n + 255) / 256, 65535), 256, 0, st>>>(rpart, n, kp / BN, s1, r);
   return cudaGetLastError();
@@ -517,59 +724,69 @@ vst_status tc_product_P(const float* A, int64_t lda, int64_t n, const double* M,
   if (e != cudaSuccess) return cuda_fail(e, "tensor-core product attributes");
   const int64_t tiles = (n + S::BM - 1) / S::BM * (kp / BN);
   if (tiles > 0x7fffffff) return fail(VST_EINVAL, "too many tiles");
-  kern<<<(unsigned)tiles, 128, S::SMEM, st>>>(ta, tb, n, k, kp, C, nullptr, hdr, 0);
+  kern<<<(unsigned)tiles, 128, S::SMEM, st>>>(ta, tb, n, k, kp, C, nullptr, hdr);
   e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "tensor-core product");
 }
 
-// split-K shape of C = A^T B: output tiles, K blocks of 64 rows per segment
-// (enough segments for ~1024 CTAs, at most 32 blocks each) and segments
-struct GramShape {
-  int64_t np;
-  int tiles, seg_kb, nseg;
-};
-GramShape gram_shape(int64_t n, int64_t k, int P) {
-  GramShape g{};
-  const int64_t kp = vif_kp(k);
-  g.np = (n + 63) / 64 * 64;
-  const int BN = P == 2 ? 256 : 128;
-  g.tiles = (int)((kp / 128) * (kp / BN));
-  const int64_t kb = g.np / 64;
-  g.seg_kb = (int)std::min<int64_t>(32, std::max<int64_t>(1, (kb * g.tiles + 1023) / 1024));
-  g.nseg = (int)((kb + g.seg_kb - 1) / g.seg_kb);
-  return g;
+// segments of K for a grid of ntiles tiles: the count in 1..kGramMaxSeg
+// (at most one per K block) whose CTAs fill the SMs' waves best, the
+// smallest such count on ties
+int gram_nseg(int ntiles, int64_t kbt, int sms) {
+  int best = 1;
+  double best_eff = -1.0;
+  for (int s = 1; s <= kGramMaxSeg && s <= kbt; ++s) {
+    const int64_t c = (int64_t)ntiles * s;
+    const int64_t waves = (c + sms - 1) / sms;
+    const double eff = (double)c / (double)(waves * sms);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = s;
+    }
+  }
+  return best;
 }
 
-template <int P, int BN>
-vst_status tc_gram_P(const float* A, const float* B, int64_t n, int k, double* C, char* tmp, WsHeader* hdr,
-                     cudaStream_t st) {
-  using S = TcShape<P, BN, 2>;
-  const int kp = vif_kp(k);
-  const GramShape g = gram_shape(n, k, P);
-  const size_t part_elems = (size_t)P * kp * g.np;
+template <int P, int STAGES>
+vst_status tc_gram_P(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t n, int kc, double* C,
+                     char* tmp, double* part, WsHeader* hdr, cudaStream_t st) {
+  using S = GramTcShape<P, STAGES>;
+  const int kp = vif_kp(kc);
+  const int64_t np = (n + 63) / 64 * 64;
   __nv_bfloat16* At = reinterpret_cast<__nv_bfloat16*>(tmp);
-  __nv_bfloat16* Bt = At + part_elems;
-  // partials after the three-part operand region (tc_gram_bytes)
-  float* part = reinterpret_cast<float*>(tmp + ((size_t)4 * 3 * kp * g.np + 255) / 256 * 256);
-  const dim3 tgrid((unsigned)(g.np / 64), (unsigned)(kp / 64));
-  split_t_kernel<P><<<tgrid, 256, 0, st>>>(A, k, n, k, kp, g.np, At);
-  split_t_kernel<P><<<tgrid, 256, 0, st>>>(B, k, n, k, kp, g.np, Bt);
+  __nv_bfloat16* Bt = At + (size_t)P * kp * np;
+  const dim3 tgrid((unsigned)(np / 64), (unsigned)(kp / 64));
+  if (np / 64 > 0x7fffffff) return fail(VST_EINVAL, "too many rows");
+  split_t_kernel<P><<<tgrid, 256, 0, st>>>(A, lda, n, kc, kp, np, At);
+  split_t_kernel<P><<<tgrid, 256, 0, st>>>(B, ldb, n, kc, kp, np, Bt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "transposed split kernels");
   CUtensorMap ta, tb;
-  if (!make_map(&ta, At, (uint64_t)P * kp, (uint64_t)g.np, S::BM) ||
-      !make_map(&tb, Bt, (uint64_t)P * kp, (uint64_t)g.np, BN))
+  if (!make_map(&ta, At, (uint64_t)P * kp, (uint64_t)np, S::BM) ||
+      !make_map(&tb, Bt, (uint64_t)P * kp, (uint64_t)np, S::BN))
     return fail(VST_ECUDA, "cuTensorMapEncodeTiled unavailable or rejected the operand layout");
-  auto kern = ugemm_tc_kernel<P, BN, 2, 3, false>;
+  auto kern = gram_tc_kernel<P, STAGES>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
-  if (e != cudaSuccess) return cuda_fail(e, "tensor-core product attributes");
-  const int64_t ctas = (int64_t)g.tiles * g.nseg;
-  if (ctas > 0x7fffffff) return fail(VST_EINVAL, "too many tiles");
-  kern<<<(unsigned)ctas, 128, S::SMEM, st>>>(ta, tb, g.np, k, kp, part, nullptr, hdr, g.seg_kb);
-  const int64_t kk = (int64_t)k * k;
-  seg_sum_kernel<<<(unsigned)std::min<int64_t>((kk + 255) / 256, 8192), 256, 0, st>>>(part, g.nseg, kk, C);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core Gram attributes");
+  // the draining warpgroups' register increase is served from the registers
+  // the block launches with: refuse a build whose launch count is too small
+  cudaFuncAttributes fa{};
+  e = cudaFuncGetAttributes(&fa, kern);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core Gram attributes");
+  if ((int64_t)fa.numRegs * S::THREADS < 128 * S::REGS_LOW + 256 * S::REGS_HIGH)
+    return fail(VST_EINTERNAL, "tensor-core Gram: %d registers per thread at launch do not cover the split",
+                fa.numRegs);
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int T = kp / S::BM;
+  const int ntiles = T * T;
+  const int nseg = gram_nseg(ntiles, np / S::BK, std::max(1, sms));
+  kern<<<(unsigned)(ntiles * nseg), S::THREADS, S::SMEM, st>>>(ta, tb, np, kc, kp, nseg, part, hdr);
+  const int64_t kk = (int64_t)kc * kc;
+  gram_sum_kernel<<<(unsigned)std::min<int64_t>((kk + 255) / 256, 8192), 256, 0, st>>>(part, nseg, kc, C);
   e = cudaGetLastError();
-  return e == cudaSuccess ? VST_OK : cuda_fail(e, "tensor-core A^T B");
+  return e == cudaSuccess ? VST_OK : cuda_fail(e, "tensor-core Gram");
 }
 
 template <int P>
@@ -628,27 +845,29 @@ vst_status tc_product(const float* A, int64_t lda, int64_t n, const double* M, i
                     : tc_product_P<3, 128, 2>(A, lda, n, M, k, C, vbase, V, hdr, st);
 }
 
-// scratch of tc_gram: both transposed operands (three parts) and the FP32
-// partials of the largest segment count
-size_t tc_gram_bytes(int64_t n, int64_t k) {
-  if (n <= 0 || k <= 0) return 256;
-  const int64_t kp = vif_kp(k);
-  const int64_t np = (n + 63) / 64 * 64;
-  const size_t parts = (size_t)4 * 3 * kp * np;  // 2 operands x 3 parts x 2 bytes
-  const int nseg = std::max(gram_shape(n, k, 2).nseg, gram_shape(n, k, 3).nseg);
-  return (parts + 255) / 256 * 256 + (size_t)4 * nseg * k * k;
+// scratch of tc_gram: the two transposed operands (three parts each) and the
+// FP64 partials of up to kGramMaxSeg segments
+size_t tc_gram_bytes(int64_t n, int64_t kc) {
+  return tc_gram_part_offset(n, kc) + (size_t)8 * kGramMaxSeg * kc * kc;
+}
+size_t tc_gram_part_offset(int64_t n, int64_t kc) {
+  const int64_t kp = vif_kp(std::max<int64_t>(kc, 1));
+  const int64_t np = (std::max<int64_t>(n, 1) + 63) / 64 * 64;
+  return align256((size_t)2 * 3 * kp * np * 2);
 }
 
-// C = A^T B (FP64 k x k) for FP32 A, B [n][k] (row stride k) on the tensor
-// cores: transposed split parts, split-K tiles over the point index with FP32
-// partials per segment, partials summed in FP64; split_terms = 3 or 6;
-// tmp holds tc_gram_bytes(n, k) bytes.
-vst_status tc_gram(const float* A, const float* B, int64_t n, int k, double* C, int split_terms, void* tmp,
-                   WsHeader* hdr, cudaStream_t st) {
-  if (k <= 0) return VST_OK;
-  if (n <= 0) return cudaMemsetAsync(C, 0, sizeof(double) * k * k, st) == cudaSuccess ? VST_OK : VST_ECUDA;
+// C = A^T B (FP64 kc x kc) for FP32 A, B [n][kc] (row strides lda, ldb) on
+// the tensor cores: transposed split parts, split-K tiles over the rows with
+// double-float drains of the tensor-memory accumulators, segments summed in
+// FP64 in a fixed order.  split_terms = 3 or 6; tmp: the transposed parts
+// (tc_gram_part_offset bytes), part: kGramMaxSeg kc x kc doubles.
+vst_status tc_gram(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t n, int kc, double* C,
+                   int split_terms, void* tmp, double* part, WsHeader* hdr, cudaStream_t st) {
+  if (kc <= 0) return VST_OK;
+  if (n <= 0) return cudaMemsetAsync(C, 0, sizeof(double) * kc * kc, st) == cudaSuccess ? VST_OK : VST_ECUDA;
   char* t = static_cast<char*>(tmp);
-  return split_terms == 3 ? tc_gram_P<2, 256>(A, B, n, k, C, t, hdr, st) : tc_gram_P<3, 128>(A, B, n, k, C, t, hdr, st);
+  return split_terms == 3 ? tc_gram_P<2, 3>(A, lda, B, ldb, n, kc, C, t, part, hdr, st)
+                          : tc_gram_P<3, 2>(A, lda, B, ldb, n, kc, C, t, part, hdr, st);
 }
 
 // U (FP32, [n][k]) of the mixed form on the tensor cores; split_terms = 3 or 6.

@@ -150,3 +150,45 @@ def test_vif_nll_split_bf16_forms(env):
         v = vst.vecchia_nll(xy_d, t_d, th, m, nn_d, cnt_d, y_d, precision=prec, ws=ws, inducing=(xyk_d, tk_d))
         vst.vst_workspace_status(ws)
         assert abs(v.item() - v_o) / n <= tol, (prec, abs(v.item() - v_o) / n)
+
+
+def test_vif_grad_tensor_core_gram_many_drains(env):
+    """n = 20,000, k = 40: the mixed gradient's J = H^T U on the split-K
+    tensor-core Gram, where each CTA drains its two tensor-memory buffers ~10
+    times, against the FP64 gradient (which the oracle pins at small n):
+    |dg_j| <= 1e-4 |g_j| + 1e-6 n.  The mixed NLL of both split forms against
+    the oracle's Woodbury NLL, |dNLL|/n <= 1e-6.  Conditioning sets: the m
+    previous points (any predecessor sets define a Vecchia NLL); responses
+    standard normal."""
+    torch, vst = env
+    k, m = 40, 8
+    st = si.stations_uniform(200, 23)
+    xy, t = si.station_days(st, 100)
+    perm = si.time_stratified_order(t, 23)
+    xy, t = np.ascontiguousarray(xy[perm]), np.ascontiguousarray(t[perm])
+    n = t.shape[0]
+    th = oracle.theta_from_ranges(1.0, 0.12, 2.0, 0.5, 0.05)
+    X = np.concatenate([xy / 0.12, (t / 2.0)[:, None]], axis=1)
+    C = si.kmeanspp(X, k, 26, lloyd_iters=5)
+    xyk, tk = np.ascontiguousarray(C[:, :2] * 0.12), np.ascontiguousarray(C[:, 2] * 2.0)
+    y = si.standard_normal(n, 29)
+    cnt = np.minimum(np.arange(n), m).astype(np.int32)
+    nn = np.zeros((n, m), dtype=np.int32)
+    for j in range(m):
+        nn[:, j] = np.maximum(np.arange(n) - 1 - j, 0)
+    U, _ = ovif.lowrank(xy, t, xyk, tk, th)
+    v_o = ovif.nll(xy, t, th, U, m, nn, cnt, y)
+    xy_d, t_d, y_d, xyk_d, tk_d, nn_d, cnt_d = dev(torch, xy, t, y, xyk, tk, nn, cnt)
+    ind = (xyk_d, tk_d)
+    ws = vst.Workspace(n, m, k, vif_grad=True)
+    for prec in (vst.MIXED, vst.MIXED_BF16X3):
+        v = vst.vecchia_nll(xy_d, t_d, th, m, nn_d, cnt_d, y_d, precision=prec, ws=ws, inducing=ind)
+        vst.vst_workspace_status(ws)
+        print("dNLL/n", prec, abs(v.item() - v_o) / n)
+        assert abs(v.item() - v_o) / n <= 1e-6, (prec, abs(v.item() - v_o) / n)
+    _, g64 = vst.vecchia_nll_grad(xy_d, t_d, th, m, nn_d, cnt_d, y_d, precision=vst.FP64, ws=ws, inducing=ind)
+    _, gm = vst.vecchia_nll_grad(xy_d, t_d, th, m, nn_d, cnt_d, y_d, precision=vst.MIXED, ws=ws, inducing=ind)
+    vst.vst_workspace_status(ws)
+    g64, gm = g64.cpu().numpy(), gm.cpu().numpy()
+    print("grad mixed - fp64 per n", (gm - g64) / n)
+    assert np.all(np.abs(gm - g64) <= 1e-4 * np.abs(g64) + 1e-6 * n), (gm, g64)
