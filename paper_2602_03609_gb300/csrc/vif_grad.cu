@@ -586,7 +586,7 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
                    terms, vb, V, hdr, st);
     if (s != VST_OK) return s;
   } else {
-    gemm_nn<T>(WE, k + 1, MinvT, k, PT(G.Y), k, n, k, k, false, st);
+    gemm_nn(WE, k + 1, MinvT, k, PT(G.Y), k, n, k, k, false, st);
   }
   gemv_kernel<<<(k * 32 + 255) / 256, 256, 0, st>>>(P(G.Minv), v, k, P(G.wv));
   rowvec_kernel<T><<<(unsigned)gridw, 256, 0, st>>>(n, k, PT(G.Y), WE, U, v, P(G.wv), y, P(G.eps), P(G.beta),
@@ -675,7 +675,7 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
                    vb, V, hdr, st);
     if (s != VST_OK) return s;
   } else {
-    gemm_nn<T>(PT(G.GU), k, XT, k, PT(G.H), k, n, k, k, true, st);
+    gemm_nn(PT(G.GU), k, XT, k, PT(G.H), k, n, k, k, true, st);
   }
   const int nb1 = (int)std::min<int64_t>(n, 4096);
   {
@@ -703,7 +703,7 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
                 gb + G.tcg, P(G.tcg + tc_gram_part_offset(n, k)), hdr, st);
     if (s != VST_OK) return s;
   } else {
-    gemm_tn<T>(PT(G.H), k, U, k, n, k, k, false, P(G.Jpart), P(G.J), st);
+    gemm_tn(PT(G.H), k, U, k, n, k, k, false, P(G.Jpart), P(G.J), st);
   }
   // K' = L^T J, Psi, Omega = X^T (Psi X), term2 = <Omega, dSigma_kk>
   gemm_tn(Lkk, k, P(G.J), k, k, k, k, true, P(G.Jpart), P(G.Kp), st);
