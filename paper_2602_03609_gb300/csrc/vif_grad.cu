@@ -58,7 +58,7 @@ constexpr int kChunks = kDgemmChunks;
 
 struct GradLayout {
   size_t LinvM, Minv, Y, GU, H, abar, dbar, eps, beta, qd, wv, svec, spart, btil, roff, rcur, rent, bsum,
-      t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, ltab, ltabf, xyf, xykf, tcg, total;
+      t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, ltab, ltabf, xyf, xykf, svf, tcg, total;
 };
 
 GradLayout grad_layout(int64_t n, int m, int64_t k) {
@@ -102,6 +102,7 @@ GradLayout grad_layout(int64_t n, int m, int64_t k) {
   G.ltabf = take(16 * (size_t)kVifMaxDays * kk);
   G.xyf = take(8 * nn);
   G.xykf = take(8 * kk);
+  G.svf = take(8 * kk);
   G.tcg = take(tc_gram_bytes(n, k));
   G.total = off;
   return G;
@@ -253,18 +254,22 @@ __global__ void rsort_kernel(int64_t n, const int64_t* off, int2* ent) {
 // (in place over Y_i), F_i = (Y_i - eps_i s) / sqrt(D_i), gamma_i = Dbar_i
 // alpha_i + beta_i / 2, beta_i = sum_q b~_iq U_N(i)_q.  One warp per row; the
 // neighbours' U rows are streamed one at a time (contiguous, 32 columns per
-// lane in registers, blocks of 1024 columns).
+// lane in registers, blocks of 1024 columns).  The per-column update runs in
+// T: in the mixed form every operand and both outputs are FP32, and FP64
+// arithmetic there (about 11 FP64-pipe operations per column, 1/61 of the
+// FP32 rate) took ~20 ms of the kernel at n = 1.1M, k = 1000.  svf: s in T.
 template <typename T>
 __global__ void __launch_bounds__(256) phi_kernel(int64_t n, int m, int k, const int32_t* nn,
                                                   const int32_t* nn_cnt, const double* D, const double* dbar,
-                                                  const double* eps, const double* svec, const T* WE,
+                                                  const double* eps, const T* svf, const T* WE,
                                                   const double* btil, const T* U, T* Y, T* alpha) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w; i < n; i += nw) {
     const int cnt = min(max(nn_cnt[i], 0), m);
-    const double Di = D[i], sd = 1.0 / sqrt(Di), sq = sqrt(Di), db = dbar[i], ei = eps[i];
+    const double Di = D[i];
+    const T sd = (T)(1.0 / sqrt(Di)), sq = (T)sqrt(Di), db = (T)dbar[i], ei = (T)eps[i];
     const T* Wi = WE + i * (int64_t)(k + 1);
     for (int cb = 0; cb < k; cb += 1024) {
       T bt[32];
@@ -285,14 +290,21 @@ __global__ void __launch_bounds__(256) phi_kernel(int64_t n, int m, int k, const
       for (int u = 0; u < 32; ++u) {
         const int c = cb + u * 32 + lane;
         if (c < k) {
-          const double al = sq * (double)Wi[c];
-          const double F = ((double)Y[i * k + c] - ei * svec[c]) * sd;
-          Y[i * k + c] = (T)(F - 2.0 * fma(db, al, 0.5 * (double)bt[u]));
-          alpha[i * k + c] = (T)al;
+          const T al = sq * Wi[c];
+          const T F = (Y[i * k + c] - ei * svf[c]) * sd;
+          Y[i * k + c] = F - T(2) * fma(db, al, T(0.5) * bt[u]);
+          alpha[i * k + c] = al;
         }
       }
     }
   }
+}
+
+// dst = src rounded to T
+template <typename T>
+__global__ void to_type_kernel(const double* src, int count, T* dst) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < count) dst[q] = (T)src[q];
 }
 
 // G_U[r] = Phi_r - sum over the reverse entries (i, q) of r of
@@ -648,7 +660,8 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
     launch_reduce_partials(part0, w, part0 + kMaxPartialWarps * 8, w1, 0.0, P(G.grows) + 5, P(G.grows), st);
   }
   // Phi and alpha per row, then G_U through the reverse index
-  phi_kernel<T><<<(unsigned)gridw, 256, 0, st>>>(n, m, k, nn, nn_cnt, D, P(G.dbar), P(G.eps), P(G.svec), WE,
+  to_type_kernel<T><<<(k + 255) / 256, 256, 0, st>>>(P(G.svec), k, PT(G.svf));
+  phi_kernel<T><<<(unsigned)gridw, 256, 0, st>>>(n, m, k, nn, nn_cnt, D, P(G.dbar), P(G.eps), PT(G.svf), WE,
                                                  P(G.btil), U, PT(G.Y), PT(G.H));
   {
     int64_t* off = reinterpret_cast<int64_t*>(gb + G.roff);
