@@ -133,3 +133,28 @@ def test_gradient_all_predecessors_is_exact_gp_gradient():
     v0, g0 = oracle.dense_nll(xy, t, th, y, grad=True)
     assert v == pytest.approx(v0, rel=1e-11)
     np.testing.assert_allclose(g, g0, rtol=1e-8, atol=1e-9 * np.abs(g0).max())
+
+
+def test_gradient_variance_scaling_identity():
+    # scaling sigma1^2 and the nugget by lambda scales Sigma_nk and Sigma_kk, so
+    # U by sqrt(lambda), the residual and its factor's D_i by lambda, and leaves
+    # A_i and the neighbour sets unchanged: Sigma~_VIF(lambda) = lambda
+    # Sigma~_VIF, hence at lambda = 1
+    #   sigma1^2 dNLL/dsigma1^2 + sigma^2 dNLL/dsigma^2 = n/2 - y^T Sigma~_VIF^{-1} y / 2
+    # (y^T Sigma~_VIF^{-1} y from the densely formed matrix)
+    xy, t, th, xyk, tk, y = setup(n_st=16, n_days=4, k=10, order="random")
+    n = t.shape[0]
+    U, r = vif.lowrank(xy, t, xyk, tk, th)
+    nn, cnt, _, _ = vif.knn(xy, t, th, U, r, 5)
+    _, g = vif.nll_grad(xy, t, th, xyk, tk, 5, nn, cnt, y)
+    S = vif.dense_sigma(xy, t, th, U, 5, nn, cnt)
+    rhs = 0.5 * n - 0.5 * y @ np.linalg.solve(S, y)
+    lhs = th[0] * g[0] + th[4] * g[4]
+    assert lhs == pytest.approx(rhs, rel=1e-9, abs=1e-9 * n)
+    # the same with the FITC special case (m = 0)
+    nn0 = np.zeros((n, 0), dtype=np.int32)
+    cnt0 = np.zeros(n, dtype=np.int32)
+    _, g0 = vif.nll_grad(xy, t, th, xyk, tk, 0, nn0, cnt0, y)
+    S0 = vif.dense_sigma(xy, t, th, U, 0, nn0, cnt0)
+    assert th[0] * g0[0] + th[4] * g0[4] == pytest.approx(0.5 * n - 0.5 * y @ np.linalg.solve(S0, y), rel=1e-9,
+                                                          abs=1e-9 * n)
