@@ -302,7 +302,8 @@ def vecchia_nll(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, out=None, ws=Non
 def vecchia_nll_grad(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, nll=None, grad=None, ws=None, stream=None,
                      inducing=None):
     """NLL and its gradient w.r.t. (sigma1sq, c, a, gamma, nugget); CUDA tensors.
-    With inducing=(xyk, tk): the VIF likelihood (Sect. 4.3), FP64 only."""
+    With inducing=(xyk, tk): the VIF likelihood (Sect. 4.3), FP64 or mixed
+    (a workspace passed in must then be sized with vif_grad=True)."""
     n = t.shape[0]
     ind, k = _inducing(inducing)
     nll = nll if nll is not None else torch.empty(1, dtype=torch.float64, device=t.device)

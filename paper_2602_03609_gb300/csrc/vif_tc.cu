@@ -1,5 +1,8 @@
-// VIF low rank on the tensor cores (mixed form): U = Sigma_nk L^{-T}
-// (Sect. 4.3) as a BF16 tcgen05 GEMM with split operands.
+// The VIF's dense products on the tensor cores (mixed form), BF16 tcgen05
+// GEMMs with split operands: the low rank U = Sigma_nk L^{-T} (Sect. 4.3), the
+// gradient's n x k products Y = W M^{-1} and H = G_U L^{-1} (tc_product), and
+// its contraction over the points J = H^T U (tc_gram, a warp-specialised
+// split-K kernel described above gram_tc_kernel).
 //
 // Each FP32 operand value v is split into P BF16 parts, v ~ v_0 + v_1 + ...,
 // v_0 = bf16(v), v_j = bf16(v - v_0 - ... - v_{j-1}).  The product of two
