@@ -189,9 +189,10 @@ vst_status vecchia_nll(const vst_points* pts, const vst_theta* theta, int m,
  * through the Woodbury terms, the residual blocks and the low-rank part
  * U = Sigma_nk L^{-T} (L L^T = Sigma_kk); nll is the value vecchia_nll returns
  * for the same precision.  VST_FP64: FP64 throughout.  VST_MIXED /
- * VST_MIXED_BF16X3: the mixed NLL's FP32 low rank, W and residual Gram, FP32
- * n x k products (double-float chunk sums), FP64 reductions over the points
- * and FP64 k x k algebra. */
+ * VST_MIXED_BF16X3: the mixed NLL's FP32 low rank, W and residual Gram, the
+ * dense products (n x k by k x k, and the k x k contraction over the points)
+ * on split-BF16 tensor cores with FP32 accumulation, FP64 reductions over the
+ * points and FP64 k x k algebra. */
 vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m,
                             const vst_inducing* ind, const int32_t* nn, const int32_t* nn_cnt,
                             const double* y, int precision, double* nll, double* grad,

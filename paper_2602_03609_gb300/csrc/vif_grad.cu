@@ -545,9 +545,10 @@ size_t vif_grad_extra_bytes(int64_t n, int m, int64_t k) { return grad_layout(n,
 
 // VIF NLL and gradient.  T = double: the FP64 NLL and FP64 throughout.
 // T = float: the mixed NLL (U, W and the residual Gram in FP32 from the
-// tensor-core path; A_i, D_i refined, M in FP64), the n x k products Y, G_U
-// and H in FP32 (FP32 products, double-float chunk sums), every n-long
-// reduction and the k x k algebra in FP64.  The workspace is ws_layout(n, m,
+// tensor-core path; A_i, D_i refined, M in FP64), the products Y = W M^{-1},
+// H = G_U L^{-1} and J = H^T U on the split-BF16 tensor cores (J with
+// double-float drains of its accumulators), the gathers in FP32, every other
+// n-long reduction and the k x k algebra in FP64.  The workspace is ws_layout(n, m,
 // k) followed by the gradient scratch (vif_grad_extra_bytes).
 template <typename T>
 vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,

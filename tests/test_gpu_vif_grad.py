@@ -92,7 +92,7 @@ def test_vif_grad_all_predecessors_is_exact_gp_gradient(env):
 
 
 # mixed forms: FP32 low rank, W and residual Gram from the tensor-core NLL,
-# FP32 n x k products with double-float chunk sums, FP64 n-long reductions.
+# the dense products on the split-BF16 tensor cores, FP64 n-long reductions.
 # The mixed NLL meets |dNLL| / n <= 1e-6; each of the n terms of a gradient
 # component carries errors of the same FP32 origin, so the bar is
 # |dg_j| <= 1e-6 n (+ 1e-4 |g_j|); observed <= 7e-8 n on these cases.
