@@ -56,6 +56,17 @@ def test_workspace_size_monotone(vst):
     assert vst.vst_workspace_size(0, 0) > 0
 
 
+def test_vif_grad_workspace_holds_the_tensor_core_scratch(vst):
+    # the mixed VIF gradient's J = H^T U: both operands transposed into three
+    # BF16 parts [3][kp][np] (kp = k rounded up to 256, np = n rounded up to
+    # 64) and up to 16 FP64 k x k segment partials, beyond the NLL's workspace
+    for n, m, k in ((1000, 10, 24), (30000, 30, 1000), (1108140, 30, 1000), (5, 4, 257)):
+        kp = (k + 255) // 256 * 256
+        np_ = (n + 63) // 64 * 64
+        extra = vst.vst_workspace_size_vif_grad(n, m, k) - vst.vst_workspace_size(n, m, k)
+        assert extra >= 2 * 3 * kp * np_ * 2 + 16 * k * k * 8, (n, m, k)
+
+
 def test_host_validation_without_gpu(vst):
     L = vst.lib()
     th = vst._Theta(*vst.vst_theta_from_ranges(1, 0.1, 3, 0.5, 0.05))
