@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(384, 1)
           umma::mbar_arrive_expect_tx(&full[s], S::STAGE_BYTES);
           const uint32_t sa = base + s * S::STAGE_BYTES, sb = sa + P * S::A_BYTES;
           const int x = (int)((kb0 + kb) * S::BK);
-  #pragma unroll
+#pragma unroll
           for (int j = 0; j < P; ++j) {
             umma::tma_load_2d(sa + j * S::A_BYTES, &tmA, x, j * kp + tm * S::BM, &full[s]);
             umma::tma_load_2d(sb + j * S::B_BYTES, &tmB, x, j * kp + tn * S::BN, &full[s]);
@@ -552,9 +552,9 @@ __global__ void __launch_bounds__(384, 1)
           umma::fence_after_sync();
           if (lane == 0) {
             const uint32_t sa = base + s * S::STAGE_BYTES, sb = sa + P * S::A_BYTES;
-  #pragma unroll
+#pragma unroll
             for (int kk = 0; kk < S::BK / 16; ++kk) {
-  #pragma unroll
+#pragma unroll
               for (int q = 0; q < SplitTerms<P>::N; ++q) {
                 const uint64_t ad = umma::desc_kmajor_sw128(sa + SplitTerms<P>::a(q) * S::A_BYTES + kk * 32);
                 const uint64_t bd = umma::desc_kmajor_sw128(sb + SplitTerms<P>::b(q) * S::B_BYTES + kk * 32);
