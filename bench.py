@@ -690,6 +690,10 @@ def run_ours(args):
         "accuracy": {"nll_fp64": v64, "nll_mixed": vmx, "dnll_per_n": abs(vmx - v64) / w.n,
                      "grad_fp64": g64.tolist(), "grad_mixed": gmx.tolist(),
                      "grad_rel_err": (np.abs(gmx - g64) / np.maximum(np.abs(g64), 1e-300)).tolist(),
+                     # per component against the bar |dg_j| <= 1e-4 |g_j| + 1e-6 n
+                     "grad_abs_err": np.abs(gmx - g64).tolist(),
+                     "grad_bar": (1e-4 * np.abs(g64) + 1e-6 * w.n).tolist(),
+                     "grad_within_bar": bool(np.all(np.abs(gmx - g64) <= 1e-4 * np.abs(g64) + 1e-6 * w.n)),
                      "fallback_rows": info_mx["n_fallback"]},
         "neighbor_search": {"value": w.n / (knn_ms * 1e-3), "unit": "queries/s", "ms": knn_ms,
                             "query_kernel_ms": kms / max(kl, 1), "tie_rows": info_knn["n_tie"]},

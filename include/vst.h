@@ -198,6 +198,47 @@ vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m
                             const double* y, int precision, double* nll, double* grad,
                             void* workspace, size_t ws_bytes, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Per-call options of the _ex entry points below.  A NULL pointer, or a
+ * zero-initialised struct, selects every default.
+ *  tau            VST_MIXED: a row is redone in FP64 when the condition
+ *                 estimate of its local (|N(i)|+1)-block, (max_j L_jj /
+ *                 min_j L_jj)^2 over the pivots of its FP32 Cholesky factor,
+ *                 exceeds tau (rows whose FP32 Cholesky fails or whose D_i is
+ *                 not positive are always redone).  <= 0: the default 1e4.
+ *                 The number of such rows is vst_ws_info.n_fallback.
+ *  row_begin,     plain Vecchia only: the sums run over the rows
+ *  row_end        row_begin <= i < row_end (0 <= row_begin <= row_end <= n;
+ *                 row_end == 0 means n).  The arrays keep their full length n
+ *                 (a row may condition on any earlier point) and nll is
+ *                 (row_end - row_begin)/2 log(2 pi) + the rows' terms, so
+ *                 contiguous ranges that cover 0..n-1 give results that add up
+ *                 to the full NLL and gradient (rows are independent given the
+ *                 neighbour sets: ranges can be evaluated on separate GPUs and
+ *                 summed, one reduction of six values).
+ *  fallback_rows  optional uint8 DEVICE output indexed by row (length n, or
+ *                 n_total for the batched call): 1 for a row the mixed form
+ *                 redid in FP64, else 0.  Only rows in the range are written.
+ *  wait_limit     vecchia_sample_ex: polls of a bounded device-side wait (on
+ *                 a predecessor row) before it gives up and records
+ *                 VST_ETIMEOUT (the row's value is then NaN); 0: the default
+ *                 of about one second.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  double tau;
+  int64_t row_begin;
+  int64_t row_end;
+  uint8_t* fallback_rows;
+  int64_t wait_limit;
+} vst_options;
+
+/* vecchia_nll_grad with options (plain Vecchia: ind must be NULL or k == 0;
+ * otherwise VST_EINVAL).  opts: tau, row_begin/row_end, fallback_rows. */
+vst_status vecchia_nll_grad_ex(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind,
+                               const int32_t* nn, const int32_t* nn_cnt, const double* y, int precision,
+                               const vst_options* opts, double* nll, double* grad, void* workspace,
+                               size_t ws_bytes, void* stream);
+
 /* Vecchia prediction at n_pred new points (the predictive distribution of
  * Sect. 3.1 under the Vecchia approximation of Sect. 4.1 with the
  * correlation-based neighbours of Sect. 4.4.1): every prediction point p
@@ -271,6 +312,14 @@ vst_status vecchia_nll_grad_batched(int nsets, int64_t n_total, const int64_t* o
                                     const double* y, int precision, double* nll, double* grad,
                                     void* workspace, size_t ws_bytes, void* stream);
 
+/* vecchia_nll_grad_batched with options: tau and fallback_rows (indexed by
+ * the concatenated row index); row_begin and row_end must be 0. */
+vst_status vecchia_nll_grad_batched_ex(int nsets, int64_t n_total, const int64_t* offsets,
+                                       const vst_theta* thetas, double nu, const double* xy,
+                                       const double* t, int m, const int32_t* nn, const int32_t* nn_cnt,
+                                       const double* y, int precision, const vst_options* opts, double* nll,
+                                       double* grad, void* workspace, size_t ws_bytes, void* stream);
+
 /* A CUDA graph holding one vecchia_nll_grad_batched evaluation with the
  * given (device) buffers, captured once and replayed by vst_graph_launch on
  * any stream.  Replays read the buffers' current contents, so parameters,
@@ -317,6 +366,10 @@ void vst_autotune_clear(void);
 vst_status vecchia_sample(const vst_points* pts, const vst_theta* theta, int m,
                           const int32_t* nn, const int32_t* nn_cnt, const double* z, double* y,
                           void* workspace, size_t ws_bytes, void* stream);
+/* vecchia_sample with options: wait_limit (the other fields must be 0). */
+vst_status vecchia_sample_ex(const vst_points* pts, const vst_theta* theta, int m, const int32_t* nn,
+                             const int32_t* nn_cnt, const double* z, double* y, const vst_options* opts,
+                             void* workspace, size_t ws_bytes, void* stream);
 
 /* Measurement hooks (not part of the method).  While enabled, the library
  * records a CUDA event pair on the launching stream around every launch of
@@ -342,15 +395,22 @@ int vst_profile_read(int kernel_class, int64_t* launches, double* total_ms);
  * on a latency-critical path, where cudaMalloc's implicit device-wide
  * synchronisation and possible failure are not acceptable.
  *
- * vecchia_nll_grad_noalloc computes exactly what vecchia_nll_grad computes
- * (same arguments, minus the workspace) but takes its scratch memory from a
- * file-scope device array of about 10 MiB (its exact size is returned by
- * vst_noalloc_scratch_bytes()) that every GPU loading the library holds
- * until the process exits.  It allocates nothing: no cudaMalloc/cudaFree and
- * no allocating library routine.
+ * vecchia_nll_grad_noalloc computes what vecchia_nll_grad computes for plain
+ * Vecchia (no inducing points: the call has no inducing-point argument), with
+ * the same arguments minus the workspace, in any precision that call accepts
+ * (VST_MIXED_BF16X3 is VST_MIXED here) and with the same launch shape (the
+ * autotuner's cached shape, if any).  Its scratch memory is one file-scope
+ * device array of 77,644,032 bytes (about 74 MiB; vst_noalloc_scratch_bytes()
+ * returns the exact size) that every GPU loading the library holds until the
+ * process exits: a 256-byte header, the FP64 and FP32 lag tables (32 KiB +
+ * 16 KiB), two buffers of per-warp partial sums (2 x 4 MiB), one fallback flag
+ * byte per point and one 32-byte mixed-form record per point (2^21 points
+ * each).  It allocates nothing: no cudaMalloc/cudaFree and no allocating
+ * library routine.
  *  - n may not exceed VST_NOALLOC_MAX_N (2^21 points); larger n returns
  *    VST_EINVAL with a message -- use vecchia_nll_grad with a workspace.
- *  - The first call on each device looks up the array's device address
+ *  - The first call on each device (and the first call after the device's
+ *    context was reset) looks up the array's device address
  *    (cudaGetSymbolAddress, with that device current); make that first call
  *    before capturing the stream into a CUDA graph.
  *  - Every call shares the one array and overwrites it (each call resets the

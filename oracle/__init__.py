@@ -119,6 +119,28 @@ def cov_matrix(xy1, t1, xy2, t2, theta) -> np.ndarray:
     return out
 
 
+def cond_estimates(xy, t, theta, nn, nn_cnt, rows=None) -> np.ndarray:
+    """Condition estimate of each row's local block, the quantity the mixed
+    form's FP64-fallback rule compares with its threshold (a reading for the
+    mixed-precision control, which the paper does not have): the response
+    covariance Sigma~ of the positions (N(i) in the order of nn[i], then i)
+    with the nugget on the diagonal (Sect. 3.1, Eq. (2)), its Cholesky factor's
+    pivots L_jj, and (max_j L_jj / min_j L_jj)^2.  numpy's Cholesky of the
+    oracle's covariance matrix; rows with no neighbour give 1."""
+    xy, t, th = _f64(xy), _f64(t), _f64(theta)
+    rows = np.arange(t.shape[0]) if rows is None else np.asarray(rows)
+    out = np.ones(rows.shape[0])
+    for q, i in enumerate(rows):
+        c = int(nn_cnt[i])
+        if c == 0:
+            continue
+        idx = np.concatenate([np.asarray(nn[i][:c], dtype=np.int64), [i]])
+        K = cov_matrix(xy[idx], t[idx], xy[idx], t[idx], th) + th[4] * np.eye(c + 1)
+        d = np.diag(np.linalg.cholesky(K))
+        out[q] = (d.max() / d.min()) ** 2
+    return out
+
+
 def knn(xy, t, theta, m, rows=None, threads=None):
     """Brute-force correlation neighbours.  Returns (nn int32 [r,m] (-1 pad),
     nn_cnt int32 [r], rho_m [r], rho_m1 [r]) for the requested rows (all by default)."""

@@ -32,6 +32,7 @@ __all__ = [
     "BatchedWorkspace", "vecchia_nll_grad_batched", "BatchedGraph", "vst_autotune_nll_grad",
     "vst_autotune_nll_grad_batched", "vst_autotune_clear", "MIXED_BF16X3", "vif_lowrank_u",
     "vecchia_predict", "vst_workspace_size_predict", "PredictWorkspace", "sts_kmeanspp",
+    "vecchia_nll_grad_ex", "vecchia_nll_grad_batched_ex", "vecchia_sample_ex", "vst_noalloc_scratch_bytes",
 ]
 
 FP64 = 0
@@ -72,6 +73,11 @@ class WsInfo(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
 
 
+class _Options(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("row_begin", ctypes.c_int64), ("row_end", ctypes.c_int64),
+                ("fallback_rows", ctypes.c_void_p), ("wait_limit", ctypes.c_int64)]
+
+
 class TuneResult(ctypes.Structure):
     _fields_ = [("blocks_per_sm", ctypes.c_int), ("row_chunk", ctypes.c_int), ("ms", ctypes.c_float)]
 
@@ -108,6 +114,12 @@ def lib():
         L.vecchia_nll_grad.restype = ctypes.c_int
         L.vecchia_nll_grad.argtypes = [PT, TH, ctypes.c_int, IN, _P, _P, _P, ctypes.c_int, _P, _P, _P,
                                        ctypes.c_size_t, _P]
+        OP = ctypes.POINTER(_Options)
+        L.vecchia_nll_grad_ex.restype = ctypes.c_int
+        L.vecchia_nll_grad_ex.argtypes = [PT, TH, ctypes.c_int, IN, _P, _P, _P, ctypes.c_int, OP, _P, _P, _P,
+                                          ctypes.c_size_t, _P]
+        L.vecchia_sample_ex.restype = ctypes.c_int
+        L.vecchia_sample_ex.argtypes = [PT, TH, ctypes.c_int, _P, _P, _P, _P, OP, _P, ctypes.c_size_t, _P]
         L.vst_workspace_size_kmeans.restype = ctypes.c_size_t
         L.vst_workspace_size_kmeans.argtypes = [ctypes.c_int64]
         L.vst_sts_kmeanspp.restype = ctypes.c_int
@@ -140,6 +152,8 @@ def lib():
                  _P, ctypes.c_size_t]
         L.vecchia_nll_grad_batched.restype = ctypes.c_int
         L.vecchia_nll_grad_batched.argtypes = bargs + [_P]
+        L.vecchia_nll_grad_batched_ex.restype = ctypes.c_int
+        L.vecchia_nll_grad_batched_ex.argtypes = bargs[:12] + [OP] + bargs[12:] + [_P]
         L.vst_graph_capture_nll_grad_batched.restype = ctypes.c_int
         L.vst_graph_capture_nll_grad_batched.argtypes = bargs + [ctypes.POINTER(ctypes.c_void_p)]
         L.vst_graph_launch.restype = ctypes.c_int
@@ -318,6 +332,31 @@ def vecchia_nll_grad(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, nll=None, g
     return nll, grad
 
 
+def _options(tau=0.0, row_begin=0, row_end=0, fallback_rows=None, wait_limit=0):
+    return _Options(float(tau), int(row_begin), int(row_end), _ptr(fallback_rows, torch.uint8, "fallback_rows"),
+                    int(wait_limit))
+
+
+def vecchia_nll_grad_ex(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, tau=0.0, row_begin=0, row_end=0,
+                        fallback_rows=None, nll=None, grad=None, ws=None, stream=None):
+    """vecchia_nll_grad (plain Vecchia) with options: tau (the mixed form's
+    condition threshold, 0 = default 1e4), the row range [row_begin, row_end)
+    (row_end = 0: n) and fallback_rows (a CUDA uint8 [n] tensor receiving 1 for
+    each row redone in FP64)."""
+    n = t.shape[0]
+    nll = nll if nll is not None else torch.empty(1, dtype=torch.float64, device=t.device)
+    grad = grad if grad is not None else torch.empty(5, dtype=torch.float64, device=t.device)
+    ws = _ws(ws, n, m)
+    pts = _points(xy, t)
+    opt = _options(tau, row_begin, row_end, fallback_rows)
+    _check(lib().vecchia_nll_grad_ex(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), None,
+                                     _ptr(nn, torch.int32, "nn"), _ptr(nn_cnt, torch.int32, "nn_cnt"),
+                                     _ptr(y, torch.float64, "y"), int(precision), ctypes.byref(opt),
+                                     _ptr(nll, torch.float64, "nll"), _ptr(grad, torch.float64, "grad"), ws.ptr,
+                                     ws.nbytes, _stream(stream)))
+    return nll, grad
+
+
 def vif_lowrank_u(xy, t, theta, inducing, precision=FP64, U=None, r=None, ws=None, stream=None):
     """VIF low rank (Sect. 4.3): U = Sigma_nk L^{-T} [n, k] and the residual
     variances r = sigma1sq - ||U_i||^2 [n]; CUDA float64 tensors."""
@@ -435,6 +474,20 @@ def vecchia_nll_grad_batched(offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, preci
     return nll, grad
 
 
+def vecchia_nll_grad_batched_ex(offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, precision=FP64, tau=0.0,
+                                fallback_rows=None, nll=None, grad=None, ws=None, stream=None):
+    """vecchia_nll_grad_batched with options: tau and fallback_rows (CUDA uint8
+    [n_total])."""
+    nsets = offsets.numel() - 1
+    nll = nll if nll is not None else torch.empty(nsets, dtype=torch.float64, device=t.device)
+    grad = grad if grad is not None else torch.empty((nsets, 5), dtype=torch.float64, device=t.device)
+    ws = ws if ws is not None else BatchedWorkspace(nsets, t.shape[0], m)
+    args = _batched_args(offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, precision, nll, grad, ws)
+    opt = _options(tau, 0, 0, fallback_rows)
+    _check(lib().vecchia_nll_grad_batched_ex(*args[:12], ctypes.byref(opt), *args[12:], _stream(stream)))
+    return nll, grad
+
+
 class BatchedGraph:
     """A captured CUDA graph of one batched evaluation (vst_graph_*)."""
 
@@ -496,8 +549,9 @@ NOALLOC_MAX_N = 1 << 21
 
 def vecchia_nll_grad_noalloc(xy, t, theta, m, nn, nn_cnt, y, precision=FP64, nll=None, grad=None, stream=None):
     """vecchia_nll_grad without a workspace, for callers that cannot allocate
-    device memory (the library's own ~10 MiB static device scratch is used;
-    n <= NOALLOC_MAX_N; calls that overlap on the GPU race on that scratch).
+    device memory (the library's own static device scratch of about 74 MiB,
+    vst_noalloc_scratch_bytes(), is used; plain Vecchia only; n <=
+    NOALLOC_MAX_N; calls that overlap on the GPU race on that scratch).
     nll/grad, if given, must be preallocated CUDA float64 tensors."""
     n = t.shape[0]
     nll = nll if nll is not None else torch.empty(1, dtype=torch.float64, device=t.device)
@@ -530,6 +584,26 @@ def vecchia_sample(xy, t, theta, m, nn, nn_cnt, z, y=None, ws=None, stream=None)
                                 _ptr(nn_cnt, torch.int32, "nn_cnt"), _ptr(z, torch.float64, "z"),
                                 _ptr(y, torch.float64, "y"), ws.ptr, ws.nbytes, _stream(stream)))
     return y
+
+
+def vecchia_sample_ex(xy, t, theta, m, nn, nn_cnt, z, wait_limit=0, y=None, ws=None, stream=None):
+    """vecchia_sample with a limit on the polls of its bounded device waits
+    (wait_limit; 0 = the default of about one second)."""
+    n = t.shape[0]
+    y = y if y is not None else torch.empty(n, dtype=torch.float64, device=t.device)
+    ws = _ws(ws, n, m)
+    pts = _points(xy, t)
+    opt = _options(wait_limit=wait_limit)
+    _check(lib().vecchia_sample_ex(ctypes.byref(pts), ctypes.byref(_th(theta)), int(m), _ptr(nn, torch.int32, "nn"),
+                                   _ptr(nn_cnt, torch.int32, "nn_cnt"), _ptr(z, torch.float64, "z"),
+                                   _ptr(y, torch.float64, "y"), ctypes.byref(opt), ws.ptr, ws.nbytes,
+                                   _stream(stream)))
+    return y
+
+
+def vst_noalloc_scratch_bytes() -> int:
+    """Size of the static device scratch of vecchia_nll_grad_noalloc."""
+    return int(lib().vst_noalloc_scratch_bytes())
 
 
 def vst_workspace_status(ws, stream=None, raise_on_error=True):

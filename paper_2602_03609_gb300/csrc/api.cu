@@ -190,10 +190,34 @@ vst_status check_common(const vst_points* pts, const vst_theta* theta, int m, co
   return VST_OK;
 }
 
+vst_status resolve_options(const vst_options* o, int64_t n, bool allow_range, CallOpts* out) {
+  CallOpts c;
+  c.row_end = n;
+  if (o) {
+    if (!(o->tau == o->tau)) return fail(VST_EINVAL, "options: tau is NaN");
+    if (o->tau > 0) c.tau = o->tau < 3.0e38 ? (float)o->tau : 3.0e38f;
+    const int64_t b = o->row_begin, e = o->row_end > 0 ? o->row_end : n;
+    if (b != 0 || e != n) {
+      if (!allow_range) return fail(VST_EINVAL, "options: a row range is not supported by this call");
+      if (b < 0 || b > e || e > n)
+        return fail(VST_EINVAL, "options: row range [%lld, %lld) not within [0, %lld]", (long long)b,
+                    (long long)e, (long long)n);
+    }
+    if (o->row_end < 0) return fail(VST_EINVAL, "options: row_end=%lld is negative", (long long)o->row_end);
+    if (o->wait_limit < 0) return fail(VST_EINVAL, "options: wait_limit is negative");
+    c.row_begin = b;
+    c.row_end = e;
+    c.fallback_rows = o->fallback_rows;
+    c.wait_limit = o->wait_limit;
+  }
+  *out = c;
+  return VST_OK;
+}
+
 // Runs the row kernels (mixed + FP64 fallback, or FP64) and the reduction.
 vst_status run_rows(const vst_points* pts, const vst_theta* theta, int m, const int32_t* nn,
                     const int32_t* nn_cnt, const double* y, int precision, int mode, double* nll,
-                    double* grad, double* A, double* D, void* ws, cudaStream_t st) {
+                    double* grad, double* A, double* D, void* ws, cudaStream_t st, const CallOpts* opt) {
   WsLayout L = ws_layout(pts->n, m, 0);
   char* base = static_cast<char*>(ws);
   WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
@@ -202,7 +226,9 @@ vst_status run_rows(const vst_points* pts, const vst_theta* theta, int m, const 
   double* part0 = reinterpret_cast<double*>(base + L.partial);
   double* part1 = part0 + kMaxPartialWarps * 8;
   uint8_t* flag = reinterpret_cast<uint8_t*>(base + L.flag);
-  const int64_t n = pts->n;
+  // rows [rb, re): the per-row arrays are addressed from rb (RowArgs::out0),
+  // the points (neighbours of any earlier row) from 0
+  const int64_t rb = opt ? opt->row_begin : 0, re = opt ? opt->row_end : pts->n;
   const DevTheta th = dev_theta(theta);
   const int nu = nu_code(theta->nu);
   const bool mixed = precision == VST_MIXED;
@@ -210,7 +236,7 @@ vst_status run_rows(const vst_points* pts, const vst_theta* theta, int m, const 
   init_header_kernel<<<1, 1, 0, st>>>(hdr);
   lag_table_kernel<<<dim3((kLagTab + 127) / 128, 1), 128, 0, st>>>(nullptr, th, lagd, lagf);
   PrepPt* prep = reinterpret_cast<PrepPt*>(base + L.prep);
-  if (mixed) launch_prep_points(n, pts->xy, pts->t, mode == kModeFactor ? nullptr : y, prep, flag, st);
+  if (mixed) launch_prep_points(re, pts->xy, pts->t, mode == kModeFactor ? nullptr : y, prep, flag, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "launch");
 
@@ -218,25 +244,26 @@ vst_status run_rows(const vst_points* pts, const vst_theta* theta, int m, const 
   g.xy = pts->xy;
   g.t = pts->t;
   g.y = y;
-  g.nn = nn;
-  g.nn_cnt = nn_cnt;
-  g.n = n;
+  g.nn = nn ? nn + rb * m : nn;
+  g.nn_cnt = nn_cnt ? nn_cnt + rb : nn_cnt;
+  g.n = re;
+  g.out0 = rb;
   g.m = m;
   g.th = th;
   g.lagd = lagd;
   g.lagf = lagf;
-  g.A = A;
-  g.D = D;
+  g.A = A ? A + rb * m : A;
+  g.D = D ? D + rb : D;
   g.flag = flag;
   g.hdr = hdr;
-  g.tau = 1.0e4f;
+  g.tau = opt ? opt->tau : kDefaultTau;
   g.offsets = nullptr;
   g.prep = prep;
   const int pm = m + 1;
   apply_launch_shape(g, 0, precision, nu, pm);
   forced_launch_shape(g);
   int64_t w0 = 0, w1 = 0;
-  if (n > 0) {
+  if (re > rb) {
     g.partial = part0;
     g.fallback_only = 0;
     {
@@ -255,11 +282,17 @@ vst_status run_rows(const vst_points* pts, const vst_theta* theta, int m, const 
     }
   }
   if (mode != kModeFactor) {
-    const double c = 0.5 * (double)n * std::log(2.0 * M_PI);
+    const double c = 0.5 * (double)(re - rb) * std::log(2.0 * M_PI);
     reduce_partials_kernel<<<1, 256, 0, st>>>(part0, w0, part1, w1, c, nll,
                                                mode == kModeNllGrad ? grad : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "reduce kernel");
+  }
+  if (opt && opt->fallback_rows && re > rb) {
+    // the flags of rows rb.. sit at flag[0..) (indexed like the per-row arrays)
+    e = mixed ? cudaMemcpyAsync(opt->fallback_rows + rb, flag, (size_t)(re - rb), cudaMemcpyDeviceToDevice, st)
+              : cudaMemsetAsync(opt->fallback_rows + rb, 0, (size_t)(re - rb), st);
+    if (e != cudaSuccess) return cuda_fail(e, "fallback rows");
   }
   return VST_OK;
 }
@@ -381,6 +414,22 @@ vst_status vecchia_nll_grad(const vst_points* pts, const vst_theta* theta, int m
   }
   return run_rows(pts, theta, m, nn, nn_cnt, y, plain_precision(precision), kModeNllGrad, nll, grad, nullptr,
                   nullptr, ws, (cudaStream_t)stream);
+}
+
+vst_status vecchia_nll_grad_ex(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind,
+                               const int32_t* nn, const int32_t* nn_cnt, const double* y, int precision,
+                               const vst_options* opts, double* nll, double* grad, void* ws, size_t ws_bytes,
+                               void* stream) {
+  if (ind && ind->k > 0) return fail(VST_EINVAL, "vecchia_nll_grad_ex: plain Vecchia only (no inducing points)");
+  vst_status s = check_common(pts, theta, m, nn, nn_cnt, ws, ws_bytes, 0);
+  if (s != VST_OK) return s;
+  if (!valid_precision(precision)) return fail(VST_EINVAL, "bad precision %d", precision);
+  if (!nll || !grad || (pts->n > 0 && !y)) return fail(VST_EINVAL, "y/nll/grad is NULL");
+  CallOpts o;
+  s = resolve_options(opts, pts->n, true, &o);
+  if (s != VST_OK) return s;
+  return run_rows(pts, theta, m, nn, nn_cnt, y, plain_precision(precision), kModeNllGrad, nll, grad, nullptr,
+                  nullptr, ws, (cudaStream_t)stream, &o);
 }
 
 vst_status vst_workspace_status(const void* ws, void* stream, vst_ws_info* info) {

@@ -24,9 +24,6 @@ vst_status fail(vst_status s, const char* fmt, ...);
 vst_status cuda_fail(cudaError_t e, const char* where);
 int nu_code(double nu);
 void launch_init_header(WsHeader* h, cudaStream_t st);
-vst_status run_rows(const vst_points* pts, const vst_theta* theta, int m, const int32_t* nn,
-                    const int32_t* nn_cnt, const double* y, int precision, int mode, double* nll,
-                    double* grad, double* A, double* D, void* ws, cudaStream_t st);
 __global__ void lag_table_kernel(const DevTheta* thetas, DevTheta th1, LagD* d, LagF* f);
 
 // ---------------------------------------------------------------------------
@@ -183,7 +180,7 @@ static vst_status batched_setup(int nsets, int64_t n_total, const int64_t* offse
 }
 
 static vst_status launch_batched_rows(RowArgs& g, int nu, int precision, int m, int nsets, const int64_t* offsets,
-                                      double* nll, double* grad, cudaStream_t st) {
+                                      double* nll, double* grad, cudaStream_t st, uint8_t* fallback_rows) {
   const bool mixed = precision == VST_MIXED;
   apply_launch_shape(g, 1, precision, nu, m + 1);
   if (g_force_bps > 0) g.blocks_per_sm = g_force_bps;
@@ -206,7 +203,13 @@ static vst_status launch_batched_rows(RowArgs& g, int nu, int precision, int m, 
   }
   seg_reduce_kernel<<<nsets, 256, 0, st>>>(nsets, g.n, offsets, g.row_out, g.flag, mixed ? 1 : 0, nll, grad);
   e = cudaGetLastError();
-  return e == cudaSuccess ? VST_OK : cuda_fail(e, "segmented reduction");
+  if (e != cudaSuccess) return cuda_fail(e, "segmented reduction");
+  if (fallback_rows && g.n > 0) {
+    e = mixed ? cudaMemcpyAsync(fallback_rows, g.flag, (size_t)g.n, cudaMemcpyDeviceToDevice, st)
+              : cudaMemsetAsync(fallback_rows, 0, (size_t)g.n, st);
+    if (e != cudaSuccess) return cuda_fail(e, "fallback rows");
+  }
+  return VST_OK;
 }
 
 }  // namespace vst
@@ -221,9 +224,12 @@ extern "C" size_t vst_workspace_size_batched(int nsets, int64_t n_total, int m) 
 static vst_status batched_entry(int nsets, int64_t n_total, const int64_t* offsets, const vst_theta* thetas,
                                 double nu, const double* xy, const double* t, int m, const int32_t* nn,
                                 const int32_t* nn_cnt, const double* y, int precision, double* nll, double* grad,
-                                void* ws, size_t ws_bytes, cudaStream_t st) {
+                                void* ws, size_t ws_bytes, cudaStream_t st, const vst_options* opts = nullptr) {
   const int nuc = nu_code(nu);
   if (nuc < 0) return fail(VST_EINVAL, "nu=%g: only 0.5, 1.5, 2.5 are supported", nu);
+  CallOpts o;
+  vst_status so = resolve_options(opts, n_total, false, &o);
+  if (so != VST_OK) return so;
   vst_status s = batched_setup(nsets, n_total, offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, precision, nll, grad,
                                ws, ws_bytes, st);
   if (s != VST_OK) return s;
@@ -239,7 +245,7 @@ static vst_status batched_entry(int nsets, int64_t n_total, const int64_t* offse
   g.m = m;
   g.flag = reinterpret_cast<uint8_t*>(base + L.flag);
   g.hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
-  g.tau = 1.0e4f;
+  g.tau = o.tau;
   g.offsets = offsets;
   g.thetas = reinterpret_cast<DevTheta*>(base + L.th);
   g.lagd_sets = reinterpret_cast<LagD*>(base + L.lagd);
@@ -247,7 +253,7 @@ static vst_status batched_entry(int nsets, int64_t n_total, const int64_t* offse
   g.nsets = nsets;
   g.row_out = reinterpret_cast<double*>(base + L.rows);
   g.prep = reinterpret_cast<const PrepPt*>(base + L.prep);
-  return launch_batched_rows(g, nuc, precision, m, nsets, offsets, nll, grad, st);
+  return launch_batched_rows(g, nuc, precision, m, nsets, offsets, nll, grad, st, o.fallback_rows);
 }
 
 extern "C" vst_status vecchia_nll_grad_batched(int nsets, int64_t n_total, const int64_t* offsets,
@@ -257,6 +263,16 @@ extern "C" vst_status vecchia_nll_grad_batched(int nsets, int64_t n_total, const
                                                void* ws, size_t ws_bytes, void* stream) {
   return batched_entry(nsets, n_total, offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, precision, nll, grad, ws,
                        ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" vst_status vecchia_nll_grad_batched_ex(int nsets, int64_t n_total, const int64_t* offsets,
+                                                  const vst_theta* thetas, double nu, const double* xy,
+                                                  const double* t, int m, const int32_t* nn, const int32_t* nn_cnt,
+                                                  const double* y, int precision, const vst_options* opts,
+                                                  double* nll, double* grad, void* ws, size_t ws_bytes,
+                                                  void* stream) {
+  return batched_entry(nsets, n_total, offsets, thetas, nu, xy, t, m, nn, nn_cnt, y, precision, nll, grad, ws,
+                       ws_bytes, (cudaStream_t)stream, opts);
 }
 
 // ---------------------------------------------------------------------------

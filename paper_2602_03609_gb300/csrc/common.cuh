@@ -17,6 +17,9 @@
 namespace vst {
 
 constexpr int kLagTab = 1024;          // integer lags 0..kLagTab-1 are tabulated
+// mixed form: default threshold of the condition estimate (max_j L_jj /
+// min_j L_jj)^2 above which a row is redone in FP64
+constexpr float kDefaultTau = 1.0e4f;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Parameters as the kernels see them (by value in the kernel arguments).

@@ -2,6 +2,8 @@
 // cannot allocate device memory.  Its scratch memory (status header, lag
 // tables, per-warp partial sums, FP64-fallback row flags) lives in one
 // file-scope device array instead of a caller-provided workspace.
+#include <cuda.h>  // CUresult / CUcontext types of the driver entry point looked up below
+
 #include <mutex>
 
 #include "kernels.h"
@@ -18,6 +20,8 @@ void launch_lag_table(const DevTheta& th, LagD* d, LagF* f, cudaStream_t st);
 void launch_init_header(WsHeader* h, cudaStream_t st);
 void launch_reduce_partials(const double* p0, int64_t w0, const double* p1, int64_t w1, double nll_const,
                             double* nll, double* grad, cudaStream_t st);
+void apply_launch_shape(RowArgs& g, int batched, int precision, int nu, int pm);
+void forced_launch_shape(RowArgs& g);
 
 namespace {
 
@@ -36,25 +40,56 @@ static_assert(kLagFOff % 256 == 0 && kPartOff % 256 == 0 && kFlagOff % 256 == 0 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};  // id of the context the address belongs to (0: unknown)
+
+// cuCtxGetId through the runtime's driver entry point (no link against the
+// driver library); NULL if the driver does not provide it
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+CtxGetIdFn ctx_get_id_fn() {
+  static const CtxGetIdFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (CtxGetIdFn) nullptr;
+    return reinterpret_cast<CtxGetIdFn>(p);
+  }();
+  return fn;
+}
+// id of the current context (unique for the life of the process), 0 if unknown
+unsigned long long current_ctx_id() {
+  const CtxGetIdFn f = ctx_get_id_fn();
+  unsigned long long id = 0;
+  if (f == nullptr || f(nullptr, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 }  // namespace
 
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Device address of the scratch array on the current device (looked up once
-// per device; the host-side symbol itself is not a device address).
+// Device address of the scratch array on the current device.  The host-side
+// symbol itself is not a device address: the address is looked up
+// (cudaGetSymbolAddress, with the device current) on the first call on each
+// device and cached together with the id of the context it belongs to.  A
+// later call in another context on that device (after cudaDeviceReset, the
+// module is loaded again, possibly at another address) looks it up again;
+// so does every call when the context id cannot be read.
 static vst_status scratch_address(char** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
   if (dev < 0 || dev >= kMaxDevices) return fail(VST_EINVAL, "device %d out of range", dev);
   std::lock_guard<std::mutex> lock(g_mu);
-  if (g_scratch_ptr[dev] == nullptr) {
+  const unsigned long long ctx = current_ctx_id();
+  if (g_scratch_ptr[dev] == nullptr || ctx == 0 || ctx != g_scratch_ctx[dev]) {
     void* p = nullptr;
     e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
     g_scratch_ptr[dev] = p;
+    // the lookup makes the device's primary context current if none was
+    g_scratch_ctx[dev] = ctx != 0 ? ctx : current_ctx_id();
   }
   *out = static_cast<char*>(g_scratch_ptr[dev]);
   return VST_OK;
@@ -78,7 +113,8 @@ extern "C" vst_status vecchia_nll_grad_noalloc(const vst_points* pts, const vst_
   if (m < 0 || m > VST_MAX_M) return fail(VST_EINVAL, "m=%d out of range [0, %d]", m, VST_MAX_M);
   vst_status s = check_theta(theta);
   if (s != VST_OK) return s;
-  if (precision != VST_FP64 && precision != VST_MIXED) return fail(VST_EINVAL, "bad precision %d", precision);
+  if (!valid_precision(precision)) return fail(VST_EINVAL, "bad precision %d", precision);
+  precision = plain_precision(precision);  // VST_MIXED_BF16X3 only differs for VIF
   if (n > 0 && (!pts->xy || !pts->t || !y || !nn_cnt || (m > 0 && !nn))) return fail(VST_EINVAL, "NULL array");
   if (!nll || !grad) return fail(VST_EINVAL, "nll/grad is NULL");
   char* base = nullptr;
@@ -116,10 +152,12 @@ extern "C" vst_status vecchia_nll_grad_noalloc(const vst_points* pts, const vst_
   g.lagf = lagf;
   g.flag = flag;
   g.hdr = hdr;
-  g.tau = 1.0e4f;
+  g.tau = kDefaultTau;
   g.offsets = nullptr;
   g.prep = prep;
   const int nu = nu_code(theta->nu);
+  apply_launch_shape(g, 0, precision, nu, m + 1);
+  forced_launch_shape(g);
   int64_t w0 = 0, w1 = 0;
   if (n > 0) {
     g.partial = part0;

@@ -154,7 +154,7 @@ extern "C" vst_status vecchia_predict(const vst_points* train, const vst_theta* 
   g.D = D;
   g.flag = flag;
   g.hdr = hdr;
-  g.tau = 1.0e4f;
+  g.tau = kDefaultTau;
   g.prep = prep;
   g.out0 = n_train;
   g.partial = reinterpret_cast<double*>(base + L.partial);

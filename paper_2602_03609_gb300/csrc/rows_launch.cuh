@@ -2,6 +2,9 @@
 // unit so the heavy fully unrolled kernels compile in parallel.
 #pragma once
 
+#include <algorithm>
+#include <atomic>
+
 #include "kernels.h"
 
 namespace vst {
@@ -10,25 +13,31 @@ template <typename T, int NU, int PM, int MODE>
 static cudaError_t launch_one(const RowArgs& g, cudaStream_t st, int64_t* warps_out) {
   auto kern = rows_kernel<T, NU, PM, MODE, kRowWarps>;
   const size_t smem = rows_smem_bytes<T, PM, kRowWarps>();
-  static int grid = 0;  // resident blocks x SMs, computed once per kernel
-  if (grid == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRowWarps * 32, smem);
+  // per device: resident blocks per SM << 16 | SM count, found on the first
+  // launch on that device (a relaxed atomic: two threads racing the first
+  // launch store the same value)
+  constexpr int kDevCache = 64;
+  static std::atomic<int> shape_cache[kDevCache];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  int packed = (dev >= 0 && dev < kDevCache) ? shape_cache[dev].load(std::memory_order_relaxed) : 0;
+  if (packed == 0) {
+    int sms = 0, per_sm = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    if (per_sm < 1) per_sm = 1;
-    int64_t gmax = kMaxPartialWarps / kRowWarps;
-    grid = (int)std::min<int64_t>((int64_t)per_sm * sms, gmax);
+    if (smem > 48 * 1024) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRowWarps * 32, smem);
+    if (e != cudaSuccess) return e;
+    packed = (std::max(1, std::min(per_sm, 255)) << 16) | std::max(1, std::min(sms, 65535));
+    if (dev >= 0 && dev < kDevCache) shape_cache[dev].store(packed, std::memory_order_relaxed);
   }
-  static int per_sm_max = 0, sms_count = 0;
-  if (per_sm_max == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms_count, cudaDevAttrMultiProcessorCount, dev);
-    per_sm_max = std::max(1, grid / std::max(1, sms_count));
-  }
+  const int per_sm = packed >> 16, sms_count = packed & 0xffff;
+  const int grid = (int)std::min<int64_t>((int64_t)per_sm * sms_count, kMaxPartialWarps / kRowWarps);
+  const int per_sm_max = std::max(1, grid / sms_count);
   int launch_grid = grid;
   if (g.blocks_per_sm > 0 && g.blocks_per_sm < per_sm_max) launch_grid = g.blocks_per_sm * sms_count;
   kern<<<launch_grid, kRowWarps * 32, smem, st>>>(g);

@@ -17,15 +17,12 @@ vst_status fail(vst_status s, const char* fmt, ...);
 vst_status cuda_fail(cudaError_t e, const char* where);
 vst_status check_common(const vst_points* pts, const vst_theta* theta, int m, const int32_t* nn,
                         const int32_t* nn_cnt, void* ws, size_t ws_bytes, int64_t k);
-vst_status run_rows(const vst_points* pts, const vst_theta* theta, int m, const int32_t* nn,
-                    const int32_t* nn_cnt, const double* y, int precision, int mode, double* nll,
-                    double* grad, double* A, double* D, void* ws, cudaStream_t st);
 
 constexpr long long kSpinLimit = 1ll << 22;  // about a second of polling with backoff
 
 __global__ void sample_kernel(int64_t n, int m, const int32_t* nn, const int32_t* nn_cnt, const double* A,
                               const double* D, const double* z, double* y, int32_t* ready,
-                              unsigned long long* counter, WsHeader* hdr) {
+                              unsigned long long* counter, WsHeader* hdr, long long spin_limit) {
   const int lane = threadIdx.x & 31;
   for (;;) {
     unsigned long long row = 0;
@@ -42,7 +39,7 @@ __global__ void sample_kernel(int64_t n, int m, const int32_t* nn, const int32_t
         cuda::atomic_ref<int32_t, cuda::thread_scope_device> f(ready[j]);
         long long spins = 0;
         while (f.load(cuda::memory_order_acquire) == 0) {
-          if (++spins > kSpinLimit) { timed_out = true; break; }
+          if (++spins > spin_limit) { timed_out = true; break; }
           __nanosleep(256);
         }
         term = A[i * m + lane] * __ldcg(y + j);
@@ -66,11 +63,16 @@ __global__ void sample_kernel(int64_t n, int m, const int32_t* nn, const int32_t
 
 using namespace vst;
 
-extern "C" vst_status vecchia_sample(const vst_points* pts, const vst_theta* theta, int m, const int32_t* nn,
-                                     const int32_t* nn_cnt, const double* z, double* y, void* ws,
-                                     size_t ws_bytes, void* stream) {
+extern "C" vst_status vecchia_sample_ex(const vst_points* pts, const vst_theta* theta, int m, const int32_t* nn,
+                                        const int32_t* nn_cnt, const double* z, double* y, const vst_options* opts,
+                                        void* ws, size_t ws_bytes, void* stream) {
   vst_status s = check_common(pts, theta, m, nn, nn_cnt, ws, ws_bytes, 0);
   if (s != VST_OK) return s;
+  CallOpts o;
+  s = resolve_options(opts, pts->n, false, &o);
+  if (s != VST_OK) return s;
+  if (opts && (opts->tau != 0 || opts->fallback_rows))
+    return fail(VST_EINVAL, "vecchia_sample_ex: only wait_limit applies");
   if (pts->n > 0 && (!z || !y)) return fail(VST_EINVAL, "z/y is NULL");
   const int64_t n = pts->n;
   if (n == 0) return VST_OK;
@@ -92,8 +94,15 @@ extern "C" vst_status vecchia_sample(const vst_points* pts, const vst_theta* the
   WsHeader* hdr = reinterpret_cast<WsHeader*>(base + L.hdr);
   {
     ProfileScope ps(kProfSample, st);
-    sample_kernel<<<sms * 4, 256, 0, st>>>(n, m, nn, nn_cnt, A, D, z, y, ready, counter, hdr);
+    sample_kernel<<<sms * 4, 256, 0, st>>>(n, m, nn, nn_cnt, A, D, z, y, ready, counter, hdr,
+                                           o.wait_limit > 0 ? (long long)o.wait_limit : kSpinLimit);
   }
   e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "sample kernel");
+}
+
+extern "C" vst_status vecchia_sample(const vst_points* pts, const vst_theta* theta, int m, const int32_t* nn,
+                                     const int32_t* nn_cnt, const double* z, double* y, void* ws,
+                                     size_t ws_bytes, void* stream) {
+  return vecchia_sample_ex(pts, theta, m, nn, nn_cnt, z, y, nullptr, ws, ws_bytes, stream);
 }

@@ -940,7 +940,7 @@ static vst_status vif_factor_T(const vst_points* pts, const vst_theta* theta, in
   g.D = Dout;
   g.flag = flag;
   g.hdr = hdr;
-  g.tau = 1.0e4f;
+  g.tau = kDefaultTau;
   g.partial = reinterpret_cast<double*>(base + L.partial);
   g.prep = prep;
   g.lagdf = lagdf;

@@ -629,7 +629,7 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
     g.lagf = lagf;
     g.flag = reinterpret_cast<uint8_t*>(base + L.flag);
     g.hdr = hdr;
-    g.tau = 1.0e4f;
+    g.tau = kDefaultTau;
     g.partial = reinterpret_cast<double*>(base + L.partial);
     if constexpr (F32) g.gram_f = reinterpret_cast<const float*>(vb + V.gram);
     else g.gram_d = reinterpret_cast<const double*>(vb + V.gram);

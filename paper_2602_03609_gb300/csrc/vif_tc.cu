@@ -457,6 +457,7 @@ __global__ void __launch_bounds__(384, 1)
   uint64_t* acce = accf + 2;        // [2] buffer drained
   uint64_t* done = acce + 2;        // every MMA finished
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile uint32_t* drain_fail = tslot + 1;  // a drain warp's wait ran out
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int T = kp / S::BM;
@@ -480,6 +481,7 @@ __global__ void __launch_bounds__(384, 1)
       umma::mbar_init(&acce[b], 8);
     }
     umma::mbar_init(done, 1);
+    *drain_fail = 0u;
     umma::fence_mbar_init();
   }
   if (warp == 0) {
@@ -616,16 +618,23 @@ __global__ void __launch_bounds__(384, 1)
       }
     }
     // the tile through shared memory (the stages are idle once the last
-    // buffer has been filled), then out to global memory row by row, coalesced
-    double* tsm = reinterpret_cast<double*>(gbase);
-    const int r = q4 * 32 + lane;
-#pragma unroll
-    for (int c = 0; c < 64; ++c) tsm[r * (S::BN + 1) + half * 64 + c] = (double)hi[c] + (double)lo[c];
+    // buffer has been filled), then out to global memory row by row,
+    // coalesced.  If any drain warp's wait ran out, loads or MMAs may still
+    // be using the stages: the eight warps agree on that first and then skip
+    // the staging and the store (the call reports VST_ETIMEOUT).
+    if (!ok && lane == 0) *drain_fail = 1u;
     asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight drain warps
-    double* dst = out + (int64_t)seg * kc * kc;
-    for (int e = threadIdx.x - 128; e < S::BM * S::BN; e += 256) {
-      const int a = tm * S::BM + e / S::BN, bc = tn * S::BN + e % S::BN;
-      if (a < kc && bc < kc) dst[(int64_t)a * kc + bc] = tsm[(e / S::BN) * (S::BN + 1) + e % S::BN];
+    if (*drain_fail == 0u) {
+      double* tsm = reinterpret_cast<double*>(gbase);
+      const int r = q4 * 32 + lane;
+#pragma unroll
+      for (int c = 0; c < 64; ++c) tsm[r * (S::BN + 1) + half * 64 + c] = (double)hi[c] + (double)lo[c];
+      asm volatile("bar.sync 1, 256;" ::: "memory");
+      double* dst = out + (int64_t)seg * kc * kc;
+      for (int e = threadIdx.x - 128; e < S::BM * S::BN; e += 256) {
+        const int a = tm * S::BM + e / S::BN, bc = tn * S::BN + e % S::BN;
+        if (a < kc && bc < kc) dst[(int64_t)a * kc + bc] = tsm[(e / S::BN) * (S::BN + 1) + e % S::BN];
+      }
     }
   }
   if (!ok) report_error(hdr, VST_ETIMEOUT, (int64_t)blockIdx.x);

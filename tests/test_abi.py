@@ -38,6 +38,16 @@ def test_exports_every_declared_symbol(vst):
         assert hasattr(L, nm), nm
 
 
+def test_noalloc_scratch_size_matches_its_layout(vst):
+    # header 256 B, FP64 and FP32 lag tables (1024 lags x 32 B and x 16 B),
+    # two per-warp partial buffers (65,536 warps x 8 doubles), one flag byte
+    # and one 32-byte mixed-form record per point (2^21 points)
+    n = vst.NOALLOC_MAX_N
+    assert n == 1 << 21
+    expect = 256 + 1024 * 32 + 1024 * 16 + 2 * 65536 * 8 * 8 + n + 32 * n
+    assert vst.vst_noalloc_scratch_bytes() == expect == 77_644_032
+
+
 def test_theta_from_ranges_matches_oracle(vst):
     for args in [(1, 0.1, 3, 0.5, 0.05, 0.4, 0.2, 1.5), (2, 0.08, 5, 0.9, 0.1, 0.7, 0.1, 0.5),
                  (1, 0.3, 1, 0.1, 0.2, 0.4, 0.2, 2.5)]:

@@ -2,10 +2,9 @@
 
 Tolerances: neighbour sets bit-exact except listed cut-off ties (< 1e-12
 relative); FP64: |dNLL|/n <= 1e-10, A and D to 1e-9 absolute / relative,
-gradient to 1e-8 relative; mixed precision: |dNLL|/n <= 1e-6, with the
-gradient held to 1e-3 relative of the sum of absolute per-row gradient terms
-(FP32 covariance entries carry ~1e-7 relative error, amplified by the local
-condition number, ~1e3 here)."""
+gradient to 1e-8 relative; mixed precision: |dNLL|/n <= 1e-6 and, per
+gradient component, |dg_j| <= 1e-4 |g_j| + 1e-6 n (the NLL's per-point bar
+carried to each n-term sum of the gradient, plus a relative part)."""
 import numpy as np
 import pytest
 
@@ -82,10 +81,9 @@ def test_mixed_nll_grad_tiny(tiny, vst, torch, nu):
     ws = vst.Workspace(w.n, w.m)
     v, g = vst.vecchia_nll_grad(tiny["xy"], tiny["t"], th, w.m, nn_d, cnt_d, tiny["yd"], precision=vst.MIXED, ws=ws)
     vst.vst_workspace_status(ws)
-    vo, go, gt = oracle.nll_grad(w.xy, w.t, th, w.m, nn, cnt, tiny["y"], terms=True)
+    vo, go = oracle.nll_grad(w.xy, w.t, th, w.m, nn, cnt, tiny["y"])
     assert abs(v.item() - vo) / w.n <= 1e-6
-    scale = np.abs(gt).sum(0)
-    assert np.all(np.abs(g.cpu().numpy() - go) <= 1e-3 * scale)
+    assert np.all(np.abs(g.cpu().numpy() - go) <= 1e-4 * np.abs(go) + 1e-6 * w.n)
     A, D = vst.vecchia_factor(tiny["xy"], tiny["t"], th, w.m, nn_d, cnt_d, precision=vst.MIXED)
     A_o, D_o = oracle.factor(w.xy, w.t, th, w.m, nn, cnt)
     np.testing.assert_allclose(D.cpu().numpy(), D_o, rtol=1e-5)
@@ -158,7 +156,7 @@ def test_box_uniform_20k(box, vst, torch):
     vmx, gmx = vst.vecchia_nll_grad(box["xy"], box["t"], th, w.m, nn_d, cnt_d, box["yd"], precision=vst.MIXED, ws=ws)
     info = vst.vst_workspace_status(ws)
     assert abs(vmx.item() - vo) / w.n <= 1e-6
-    assert np.all(np.abs(gmx.cpu().numpy() - go) <= 1e-3 * np.abs(gt).sum(0))
+    assert np.all(np.abs(gmx.cpu().numpy() - go) <= 1e-4 * np.abs(go) + 1e-6 * w.n)
     # whitening identity with the oracle's factor
     ref = 0.5 * w.n * np.log(2 * np.pi) + 0.5 * np.log(box["D"]).sum() + 0.5 * (w.z ** 2).sum()
     assert abs(v64.item() - ref) / w.n <= 1e-10

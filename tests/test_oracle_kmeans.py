@@ -20,6 +20,39 @@ def test_counts_multiply_to_m():
         assert abs(ms * mt - m) <= 0.3 * m
 
 
+def test_counts_printed_formula():
+    # Algorithm 3 (Sect. 4.4.2): m_s = round(sqrt(m n / |T|^2)) spatial and
+    # m_t = round(sqrt(m |T|^2 / n)) temporal centres.  At n = 1,108,140,
+    # |T| = 365, m = 1000: m n / |T|^2 = 8317.7 -> 91 and m |T|^2 / n = 120.2
+    # -> 11; swapping the two formulas gives (11, 91) and fails.
+    assert okm.counts(1_108_140, 365, 1000) == (91, 11)
+    # more data per time point than time points: more spatial centres
+    assert okm.counts(2_000, 10, 100) == (45, 2)
+    # round = floor(x + 1/2): sqrt(m n / |T|^2) = 2.5 exactly rounds up
+    assert okm.counts(625, 10, 1) == (3, 0)
+
+
+def test_kmeanspp_second_centre_follows_d2():
+    # kMeans++ seeding (Arthur and Vassilvitskii 2007): after the first centre,
+    # the next one is drawn with probability proportional to the squared
+    # distance D^2 to the nearest chosen centre.  Points on a line at 0, 1, 3:
+    # with the first centre at 0, D^2 = (0, 1, 9), so the point at 1 is chosen
+    # with probability 0.1 (D weighting would give 0.25, uniform 0.5).
+    P = np.array([[0.0, 0.0], [1.0, 0.0], [3.0, 0.0]])
+    hits, total = 0, 0
+    for seed in range(3000):
+        C = okm.kmeanspp(P, 2, seed, 0)
+        if C[0, 0] != 0.0:
+            continue
+        total += 1
+        assert C[1, 0] in (1.0, 3.0)
+        hits += C[1, 0] == 1.0
+    assert total > 700
+    frac = hits / total
+    # binomial standard deviation at p = 0.1 and ~1000 draws is ~0.01
+    assert abs(frac - 0.1) < 0.04, frac
+
+
 def test_every_point_a_centre_when_k_equals_n():
     P = np.random.default_rng(4).random((40, 2))
     C = okm.kmeanspp(P, 40, 123, 0)

@@ -150,3 +150,28 @@ def test_knn_exact_ties_pick_smaller_index():
     assert nn[3, 0] == 0
     assert rm[3] == rm1[3]
     assert 3 in oracle.tie_rows(rm, rm1)
+
+
+def test_cond_estimate_closed_form_and_bounds():
+    # two points: the block [[s, c], [c, s]] (s = sigma1^2 + nugget, c the
+    # covariance) has pivots sqrt(s) and sqrt(s - c^2 / s), so the estimate
+    # (max L_jj / min L_jj)^2 is s^2 / (s^2 - c^2)
+    th = oracle.theta_from_ranges(1.0, 0.1, 3.0, 0.5, 0.05)
+    xy = np.array([[0.3, 0.4], [0.33, 0.38]])
+    t = np.array([2.0, 3.0])
+    c = oracle.cov(th, float(np.hypot(0.03, 0.02)), 1.0)
+    s = th[0] + th[4]
+    est = oracle.cond_estimates(xy, t, th, np.array([[-1], [0]], dtype=np.int32), np.array([0, 1], dtype=np.int32))
+    assert est[0] == 1.0
+    assert est[1] == pytest.approx(s * s / (s * s - c * c), rel=1e-12)
+    # larger blocks: each squared pivot is a Schur complement, which lies
+    # between the extreme eigenvalues, so 1 <= estimate <= cond_2(block)
+    w = si.tiny_uniform(m=10)
+    nn, cnt, _, _ = oracle.knn(w.xy, w.t, th, w.m)
+    rows = np.arange(20, 2000, 97)
+    est = oracle.cond_estimates(w.xy, w.t, th, nn, cnt, rows)
+    for q, i in enumerate(rows):
+        idx = np.concatenate([nn[i][:cnt[i]], [i]])
+        K = oracle.cov_matrix(w.xy[idx], w.t[idx], w.xy[idx], w.t[idx], th) + th[4] * np.eye(idx.shape[0])
+        ev = np.linalg.eigvalsh(K)
+        assert 1.0 < est[q] <= ev[-1] / ev[0] * (1 + 1e-9)
