@@ -36,6 +36,7 @@
 // instantiation.
 #pragma once
 
+#include <climits>
 #include <type_traits>
 
 #include "common.cuh"
@@ -110,6 +111,9 @@ struct WarpSm {
   alignas(16) Pos<T> pos[PM];
   alignas(16) float q1[MIXED ? NPAIR : 1];          // mixed: P x M'(x) per pair
   alignas(16) double xe[MIXED ? 1 : NPAIR][2];      // FP64: (x, e^-x) per pair
+  // tiled pair loops: P x M'(x) of the diagonal-block pairs (FP64: then their
+  // covariance, the FP64 factor overwrites K)
+  alignas(16) T qd[(MIXED ? 2 : 4) * PM];
   double tt[PM];                                    // times (non-integer lag path)
 };
 
@@ -123,6 +127,10 @@ template <typename T, int PM>
 struct BlockSm {
   uint32_t pairs[PM * (PM + 1) / 2];
   int npairs;
+  // tiled pair loops: the pairs r > c inside the 8 diagonal blocks of size
+  // PM / 8 (as r | c << 8 | q << 16, q = the slot of their P x M'(x))
+  uint32_t dpairs[2 * PM];
+  int ndpairs;
   alignas(16) typename std::conditional<std::is_same<T, float>::value, LagF, LagD>::type lag[kLagSmem];
 };
 
@@ -216,12 +224,221 @@ __device__ __forceinline__ void st16(T* p, const T (&v)[VEC]) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Tiled pair loops of the NLL and plain-gradient instantiations.  The strict
+// lower triangle of the PM x PM block is cut into 8 x 8 blocks of TS = PM / 8
+// positions.  Lane l < 28 owns the off-diagonal block (R, C), R > C,
+// l = R (R - 1) / 2 + C: it holds the TS + TS positions in registers,
+// evaluates the TS x TS pairs without any table decode or validity branch
+// (a pair with an unused position gets 0) and stores row and column vectors
+// of K.  Its TS^2 values P x M'(x) (FP64: and the covariance) stay in the
+// warp's scratch at [u][lane] for the adjoint pass, which reads them back in
+// the same order.  The pairs inside the 8 diagonal blocks (TS (TS - 1) / 2
+// each) go through a small table, at most two per lane.
+template <int PM> struct TileShape {
+  static constexpr int TS = PM / 8;
+  static constexpr int NT = TS * TS;       // pairs per off-diagonal block
+  static constexpr int ND = 8 * TS * (TS - 1) / 2;  // diagonal-block pairs
+};
+
+__device__ __forceinline__ void tile_of_lane(int lane, int& R, int& C) {
+  int r = 1;
+  while ((r + 1) * r / 2 <= lane) ++r;
+  R = r;
+  C = lane - r * (r - 1) / 2;
+}
+
+// TS consecutive elements, vectorised where the width allows
+template <typename T, int TS>
+__device__ __forceinline__ void st_row(T* p, const T (&v)[TS]) {
+  if constexpr (sizeof(T) * TS == 16) {
+    st16<T, 16 / (int)sizeof(T)>(p, v);
+  } else if constexpr (sizeof(T) * TS == 32) {
+    T a[TS / 2], b[TS / 2];
+#pragma unroll
+    for (int u = 0; u < TS / 2; ++u) { a[u] = v[u]; b[u] = v[u + TS / 2]; }
+    st16<T, TS / 2>(p, a);
+    st16<T, TS / 2>(p + TS / 2, b);
+  } else if constexpr (std::is_same<T, float>::value && TS == 2) {
+    *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < TS; ++u) p[u] = v[u];
+  }
+}
+template <typename T, int TS>
+__device__ __forceinline__ void ld_row(T (&v)[TS], const T* p) {
+  if constexpr (sizeof(T) * TS == 16) {
+    ld16<T, 16 / (int)sizeof(T)>(v, p);
+  } else if constexpr (sizeof(T) * TS == 32) {
+    T a[TS / 2], b[TS / 2];
+    ld16<T, TS / 2>(a, p);
+    ld16<T, TS / 2>(b, p + TS / 2);
+#pragma unroll
+    for (int u = 0; u < TS / 2; ++u) { v[u] = a[u]; v[u + TS / 2] = b[u]; }
+  } else if constexpr (std::is_same<T, float>::value && TS == 2) {
+    const float2 q = *reinterpret_cast<const float2*>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+  } else {
+#pragma unroll
+    for (int u = 0; u < TS; ++u) v[u] = p[u];
+  }
+}
+
+// covariance and P x M'(x) of one pair (mixed: FP32 with the exp2 unit; FP64)
+template <typename T, int NU>
+__device__ __forceinline__ void pair_cov(T dx, T dy, T P, T G, T& v, T& q) {
+  const T d2 = dx * dx + dy * dy;
+  if constexpr (std::is_same<T, float>::value) {
+    const float h = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
+    const float x = G * h;
+    const float E = __expf(-x);
+    v = P * matern_M<NU, float>(x, E);
+    q = P * matern_xdM<NU, float>(x, E);
+  } else {
+    const double x = G * sqrt(d2);
+    const double E = exp(-x);
+    v = P * matern_M<NU, double>(x, E);
+    q = P * matern_xdM<NU, double>(x, E);
+  }
+}
+
+// lag factors of a pair: from the row's table when FAST (all times integer
+// days and every lag of the block inside the table), else the general lookup
+template <typename T, bool FAST, typename LagS>
+__device__ __forceinline__ void pair_lag(const DevTheta& th, const LagD* lagd, const LagF* lagf, const LagS* tab,
+                                         bool allint, int tdr, int tdc, double ttr, double ttc, T& P, T& G, T& Qa,
+                                         T& L) {
+  if constexpr (FAST) {
+    const LagS f = tab[abs(tdr - tdc)];
+    P = (T)f.P; G = (T)f.G; Qa = (T)f.Qa; L = (T)f.L;
+  } else {
+    lag_lookup<T>(th, lagd, lagf, tab, allint, tdr, tdc, ttr, ttc, P, G, Qa, L);
+  }
+}
+
+template <typename T, int NU, int PM, bool FAST, typename LagS>
+__device__ __forceinline__ void cov_tiled(const DevTheta& th, const LagD* lagd, const LagF* lagf, const LagS* tab,
+                                          bool allint, const BlockSm<T, PM>* bs, WarpSm<T, PM>& s, int tR, int tC,
+                                          int lane) {
+  constexpr int TS = TileShape<PM>::TS;
+  constexpr bool MIXED = std::is_same<T, float>::value;
+  T* qt = MIXED ? reinterpret_cast<T*>(&s.q1[0]) : reinterpret_cast<T*>(&s.xe[0][0]);
+  if (lane < 28) {
+    Pos<T> pc[TS];
+#pragma unroll
+    for (int u = 0; u < TS; ++u) pc[u] = s.pos[tC * TS + u];
+    T kv[TS][TS];
+#pragma unroll
+    for (int a = 0; a < TS; ++a) {
+      const Pos<T> pr = s.pos[tR * TS + a];
+#pragma unroll
+      for (int b = 0; b < TS; ++b) {
+        T P, G, Qa, L, v, q;
+        pair_lag<T, FAST>(th, lagd, lagf, tab, allint, pr.td, pc[b].td, s.tt[tR * TS + a], s.tt[tC * TS + b], P, G,
+                          Qa, L);
+        pair_cov<T, NU>(pr.ox - pc[b].ox, pr.oy - pc[b].oy, P, G, v, q);
+        const bool ok = (pr.valid & pc[b].valid) != 0;
+        kv[a][b] = ok ? v : T(0);
+        qt[(a * TS + b) * 32 + lane] = ok ? q : T(0);
+        if constexpr (!MIXED) qt[(TS * TS + a * TS + b) * 32 + lane] = kv[a][b];
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < TS; ++a) st_row<T, TS>(&s.K[tR * TS + a][tC * TS], kv[a]);
+#pragma unroll
+    for (int b = 0; b < TS; ++b) {
+      T col[TS];
+#pragma unroll
+      for (int a = 0; a < TS; ++a) col[a] = kv[a][b];
+      st_row<T, TS>(&s.K[tC * TS + b][tR * TS], col);
+    }
+  }
+  for (int q = lane; q < bs->ndpairs; q += 32) {
+    const uint32_t rc = bs->dpairs[q];
+    const int r = rc & 0xff, c = (rc >> 8) & 0xff;
+    const Pos<T> pr = s.pos[r], pc = s.pos[c];
+    T P, G, Qa, L, v, qq;
+    pair_lag<T, FAST>(th, lagd, lagf, tab, allint, pr.td, pc.td, s.tt[r], s.tt[c], P, G, Qa, L);
+    pair_cov<T, NU>(pr.ox - pc.ox, pr.oy - pc.oy, P, G, v, qq);
+    const bool ok = (pr.valid & pc.valid) != 0;
+    v = ok ? v : T(0);
+    s.K[r][c] = v;
+    s.K[c][r] = v;
+    s.qd[q] = ok ? qq : T(0);
+    if constexpr (!MIXED) s.qd[2 * PM + q] = v;
+  }
+}
+
+// sum over the pairs of W_pq dSigma~_pq / dtheta, W = c1 a~ a~^T - c2 (a~ b~^T
+// + b~ a~^T) / 2, for the off-diagonal pairs (the caller adds the diagonal)
+template <typename T, int NU, int PM, bool FAST, typename LagS>
+__device__ __forceinline__ void adj_tiled(const DevTheta& th, const LagD* lagd, const LagF* lagf, const LagS* tab,
+                                          bool allint, const BlockSm<T, PM>* bs, WarpSm<T, PM>& s, int tR, int tC,
+                                          int lane, T c1, T hc2, T pexp, T hg, T& g0, T& g1, T& g2, T& g3) {
+  constexpr int TS = TileShape<PM>::TS;
+  constexpr bool MIXED = std::is_same<T, float>::value;
+  const T* qt = MIXED ? reinterpret_cast<const T*>(&s.q1[0]) : reinterpret_cast<const T*>(&s.xe[0][0]);
+  if (lane < 28) {
+    T ac[TS], bc[TS];
+    int tc[TS];
+#pragma unroll
+    for (int u = 0; u < TS; ++u) {
+      ac[u] = s.ab[tC * TS + u][0];
+      bc[u] = s.ab[tC * TS + u][1];
+      tc[u] = s.pos[tC * TS + u].td;
+    }
+#pragma unroll
+    for (int a = 0; a < TS; ++a) {
+      const T ara = s.ab[tR * TS + a][0], bra = s.ab[tR * TS + a][1];
+      const int tra = s.pos[tR * TS + a].td;
+      T kv[TS];
+      if constexpr (MIXED) {
+        ld_row<T, TS>(kv, &s.K[tR * TS + a][tC * TS]);
+      } else {
+#pragma unroll
+        for (int b = 0; b < TS; ++b) kv[b] = qt[(TS * TS + a * TS + b) * 32 + lane];
+      }
+      const T ra = c1 * ara - hc2 * bra, rb = -hc2 * ara;
+#pragma unroll
+      for (int b = 0; b < TS; ++b) {
+        T P, G, Qa, L;
+        pair_lag<T, FAST>(th, lagd, lagf, tab, allint, tra, tc[b], s.tt[tR * TS + a], s.tt[tC * TS + b], P, G, Qa,
+                          L);
+        const T Kv = kv[b], Xv = qt[(a * TS + b) * 32 + lane];
+        // w = ar (c1 ac - hc2 bc) - hc2 br ac, doubled (both (r, c) and (c, r))
+        const T w2 = T(2) * fma(ra, ac[b], rb * bc[b]);
+        g0 = fma(w2, Kv, g0);
+        g1 = fma(w2, Xv, g1);
+        g2 = fma(w2 * Qa, -pexp * Kv - hg * Xv, g2);
+        g3 = fma(-w2 * L, Kv + T(0.5) * Xv, g3);
+      }
+    }
+  }
+  for (int q = lane; q < bs->ndpairs; q += 32) {
+    const uint32_t rc = bs->dpairs[q];
+    const int r = rc & 0xff, c = (rc >> 8) & 0xff;
+    T P, G, Qa, L;
+    pair_lag<T, FAST>(th, lagd, lagf, tab, allint, s.pos[r].td, s.pos[c].td, s.tt[r], s.tt[c], P, G, Qa, L);
+    const T ar = s.ab[r][0], br = s.ab[r][1], ac = s.ab[c][0], bc = s.ab[c][1];
+    const T Kv = MIXED ? s.K[r][c] : s.qd[2 * PM + q], Xv = s.qd[q];
+    const T w2 = T(2) * (ar * (c1 * ac - hc2 * bc) - hc2 * br * ac);
+    g0 = fma(w2, Kv, g0);
+    g1 = fma(w2, Xv, g1);
+    g2 = fma(w2 * Qa, -pexp * Kv - hg * Xv, g2);
+    g3 = fma(-w2 * L, Kv + T(0.5) * Xv, g3);
+  }
+}
+
 // Process one row; all 32 lanes call it together.
 template <typename T, int NU, int PM, int MODE>
 __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, const LagD* lagd,
                                          const LagF* lagf, const BlockSm<T, PM>* bs, bool lag_smem,
                                          WarpSm<T, PM>& s, int64_t i, int64_t row0, int lane,
-                                         RowAcc<T>& acc) {
+                                         RowAcc<T>& acc, int tR, int tC) {
+  // the NLL and plain-gradient instantiations use the tiled pair loops
+  constexpr bool TILED = (MODE == kModeNll || MODE == kModeNllGrad);
   constexpr bool MIXED = std::is_same<T, float>::value;
   constexpr int LAST = PM - 1;
   constexpr int VEC = 16 / (int)sizeof(T);
@@ -295,6 +512,18 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     }
   }
   const T yv = MIXED ? (T)yl.hi : (T)rj;  // y in T (solves)
+  // tiled loops: every lag of the block inside the shared lag table
+  bool fast = false;
+  if constexpr (TILED) {
+    const int td = s.pos[lane < PM ? lane : 0].td;  // this lane's own record (written above)
+    int tmx = (lane < PM && valid) ? td : INT_MIN, tmn = (lane < PM && valid) ? td : INT_MAX;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      tmx = max(tmx, __shfl_xor_sync(kFull, tmx, o));
+      tmn = min(tmn, __shfl_xor_sync(kFull, tmn, o));
+    }
+    fast = lag_smem && allint && (int64_t)tmx - (int64_t)tmn < kLagSmem;
+  }
   __syncwarp();
 
   // ---- 2. local covariance, lower triangle distributed over the lanes
@@ -306,8 +535,12 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
   (void)vif;
   const auto* lags = lag_smem ? bs->lag : nullptr;
   const int npairs = bs->npairs;
+  if constexpr (TILED) {
+    if (fast) cov_tiled<T, NU, PM, true>(th, lagd, lagf, bs->lag, allint, bs, s, tR, tC, lane);
+    else cov_tiled<T, NU, PM, false>(th, lagd, lagf, lags, allint, bs, s, tR, tC, lane);
+  }
 #pragma unroll 2
-  for (int q = lane; q < npairs; q += 32) {
+  for (int q = lane; q < (TILED ? 0 : npairs); q += 32) {
     const uint32_t rce = bs->pairs[q];
     const int r = rce & 0xff, c = (rce >> 8) & 0xff, e = (int)(rce >> 16);
     T v;
@@ -639,8 +872,14 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     T gd = 0, g0 = 0, g1 = 0, g2 = 0, g3 = 0;
     const T pexp = MIXED ? (T)th.pf : (T)th.p, hg = MIXED ? (T)th.hgf : (T)(0.5 * th.gamma);
     const T hc2 = T(0.5) * c2;
+    if constexpr (TILED) {
+      if (fast) adj_tiled<T, NU, PM, true>(th, lagd, lagf, bs->lag, allint, bs, s, tR, tC, lane, c1, hc2, pexp, hg, g0,
+                                           g1, g2, g3);
+      else adj_tiled<T, NU, PM, false>(th, lagd, lagf, lags, allint, bs, s, tR, tC, lane, c1, hc2, pexp, hg, g0, g1,
+                                       g2, g3);
+    }
 #pragma unroll 2
-    for (int q = lane; q < npairs; q += 32) {
+    for (int q = lane; q < (TILED ? 0 : npairs); q += 32) {
       const uint32_t rce = bs->pairs[q];
       const int r = rce & 0xff, c = (rce >> 8) & 0xff, e = (int)(rce >> 16);
       const Pos<T> pr = s.pos[r], pc = s.pos[c];
@@ -722,6 +961,15 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) rows_kernel(RowArgs g)
       count += __popc(mask);
     }
     if (lane == 0) bs->npairs = count;
+    // pairs r > c inside the 8 diagonal blocks of TS = PM / 8 positions
+    if (lane == 0) {
+      constexpr int TS = TileShape<PM>::TS;
+      int nd = 0;
+      for (int b = 0; b < 8; ++b)
+        for (int r = 1; r < TS; ++r)
+          for (int c = 0; c < r; ++c) bs->dpairs[nd++] = (uint32_t)((b * TS + r) | ((b * TS + c) << 8));
+      bs->ndpairs = nd;
+    }
   }
   if (g.offsets == nullptr) {
     for (int u = threadIdx.x; u < kLagSmem; u += WARPS * 32) {
@@ -731,6 +979,8 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) rows_kernel(RowArgs g)
   }
   __syncthreads();
   const BlockSm<T, PM>* bsc = bs;
+  int tR = 0, tC = 0;
+  tile_of_lane(lane, tR, tC);
   const int64_t warp = (int64_t)blockIdx.x * WARPS + wib;
   const int64_t total = (int64_t)gridDim.x * WARPS;
   RowAcc<T> acc;
@@ -746,7 +996,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) rows_kernel(RowArgs g)
         const int64_t end = base + chunk < n ? base + chunk : n;
         for (int64_t i = base; i < end; ++i) {
           if (g.fallback_only && g.flag[i - g.out0] == 0) continue;
-          row_body<T, NU, PM, MODE>(g, g.th, g.lagd, g.lagf, bsc, true, s, i, 0, lane, acc);
+          row_body<T, NU, PM, MODE>(g, g.th, g.lagd, g.lagf, bsc, true, s, i, 0, lane, acc, tR, tC);
         }
       }
     }
@@ -774,7 +1024,7 @@ __global__ void __launch_bounds__(WARPS * 32, 16 / WARPS) rows_kernel(RowArgs g)
         acc.zero();
         row_body<T, NU, PM, MODE>(g, g.thetas[set], g.lagd_sets + (int64_t)set * kLagTab,
                                   g.lagf_sets + (int64_t)set * kLagTab, bsc, false, s, gi - row0, row0, lane,
-                                  acc);
+                                  acc, tR, tC);
         // per-row results: FP64 rows as double[6]; mixed rows as double-float
         // pairs float2[6] (same 48 bytes), combined by the segmented reduction
         const bool skip = g.flag != nullptr && !g.fallback_only && g.flag[gi];
