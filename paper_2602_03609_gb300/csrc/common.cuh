@@ -137,6 +137,20 @@ __device__ __forceinline__ float df_diff(float ah, float al, float bh, float bl)
   const df t = df_two_sum(ah, -bh);
   return t.hi + (t.lo + (al - bl));
 }
+// Two independent double-float sums (hi + lo, componentwise) on packed FP32
+// pairs: hi + lo -= a * b exactly up to the final additions, the product
+// split by one fused multiply-add (TwoProduct) and the sum by TwoSum.
+__device__ __forceinline__ void df2_dot_sub(float2& hi, float2& lo, float2 a, float2 b) {
+  const float2 p = __fmul2_rn(make_float2(-a.x, -a.y), b);
+  const float2 pe = __ffma2_rn(make_float2(-a.x, -a.y), b, make_float2(-p.x, -p.y));
+  const float2 sm = __fadd2_rn(hi, p);
+  const float2 bb = __fadd2_rn(sm, make_float2(-hi.x, -hi.y));
+  const float2 t = __fadd2_rn(sm, make_float2(-bb.x, -bb.y));
+  const float2 e1 = __fadd2_rn(hi, make_float2(-t.x, -t.y));
+  const float2 e2 = __fadd2_rn(p, make_float2(-bb.x, -bb.y));
+  lo = __fadd2_rn(lo, __fadd2_rn(__fadd2_rn(e1, e2), pe));
+  hi = sm;
+}
 __device__ __forceinline__ df df_split(double v) {
   const float hi = (float)v;
   return {hi, (float)(v - (double)hi)};

@@ -660,9 +660,24 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     for (int q = ((k + 1) / VEC) * VEC; q < PM; q += VEC) {
       T cv[VEC];
       ld16<T, VEC>(cv, &s.col[q]);
+      if constexpr (MIXED) {
+        // packed FP32 pairs (q + u, q + u + 1): one instruction updates both
 #pragma unroll
-      for (int u = 0; u < VEC; ++u)
-        if (q + u > k) a[q + u] = fma(-v, cv[u], a[q + u]);
+        for (int u = 0; u < VEC; u += 2) {
+          if (q + u > k) {
+            const float2 r = __ffma2_rn(make_float2(-v, -v), make_float2(cv[u], cv[u + 1]),
+                                        make_float2(a[q + u], a[q + u + 1]));
+            a[q + u] = r.x;
+            a[q + u + 1] = r.y;
+          } else if (q + u + 1 > k) {
+            a[q + u + 1] = fma(-v, cv[u + 1], a[q + u + 1]);
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u)
+          if (q + u > k) a[q + u] = fma(-v, cv[u], a[q + u]);
+      }
     }
     __syncwarp();
   }
@@ -736,8 +751,18 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       if (lane == k) { aj = ak; bj = bk; }
       if (lane < k) {
         const T lkj = Lsm[k][lane];
-        acc_a = fma(-lkj, ak, acc_a);
-        if (need_b) acc_b = fma(-lkj, bk, acc_b);
+        if constexpr (MIXED) {
+          if (need_b) {
+            const float2 r = __ffma2_rn(make_float2(-lkj, -lkj), make_float2(ak, bk), make_float2(acc_a, acc_b));
+            acc_a = r.x;
+            acc_b = r.y;
+          } else {
+            acc_a = fma(-lkj, ak, acc_a);
+          }
+        } else {
+          acc_a = fma(-lkj, ak, acc_a);
+          if (need_b) acc_b = fma(-lkj, bk, acc_b);
+        }
       }
     }
   }
@@ -759,16 +784,19 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     __syncwarp();
     df res = {0.0f, 0.0f};
     if (lane < LAST) {
-      res.hi = s.K[lane][LAST];
+      // two interleaved double-float sums (even and odd q) on packed FP32
+      // pairs; v0[LAST] = 0, so the last pair's second term is exactly 0
+      float2 hi = make_float2(s.K[lane][LAST], 0.0f), lo = make_float2(0.0f, 0.0f);
 #pragma unroll
-      for (int q = 0; q < LAST; q += 4) {
+      for (int q = 0; q < PM; q += 4) {
         float kv[4], av[4];
         ld16<float, 4>(kv, &s.K[lane][q]);
         ld16<float, 4>(av, &s.v0[q]);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (q + u < LAST) df_fma_acc(res, -kv[u], df{av[u], 0.0f});
+        df2_dot_sub(hi, lo, make_float2(kv[0], kv[1]), make_float2(av[0], av[1]));
+        df2_dot_sub(hi, lo, make_float2(kv[2], kv[3]), make_float2(av[2], av[3]));
       }
+      res = df_two_sum(hi.x, hi.y);
+      res.lo += lo.x + lo.y;
       if (valid && !vif) res.lo = fmaf(-th.dg_lo, aj, res.lo);
     }
     // with a Gram (VIF) every entry of K, the diagonal included, is the FP64
