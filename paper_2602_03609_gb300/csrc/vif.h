@@ -1,6 +1,7 @@
 // Internal declarations of the VIF path (vif.cu).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -55,6 +56,10 @@ size_t tc_gram_bytes(int64_t n, int64_t kc);
 size_t tc_gram_part_offset(int64_t n, int64_t kc);
 vst_status tc_gram(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t n, int kc, double* C,
                    int split_terms, void* tmp, double* part, WsHeader* hdr, cudaStream_t st);
+
+// 2-D TMA map of a row-major BF16 matrix rows x cols (cols contiguous, a
+// multiple of 8), box 64 columns x box_rows rows, 128-byte swizzle (vif_tc.cu)
+bool tc_make_map_bf16(CUtensorMap* map, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows);
 
 // residual-correlation neighbours (vif_knn.cu); base: the whole workspace
 vst_status vif_knn(const vst_points* pts, const vst_theta* theta, int m, const vst_inducing* ind, int nu,

@@ -7,11 +7,12 @@
 // The search is exact but filtered:
 //   1. a lower bound tau_i of the m-th largest |rho_ij|: the smallest |rho|
 //      (FP64) over m actual predecessors, the plain-correlation neighbours;
-//   2. a pass over all pairs j < i in 128 x 64 tiles, FP32 dot products and
-//      covariance, that keeps every j whose |rho| can reach tau_i: the test
-//      carries a rigorous bound on the FP32 error (accumulation of k
-//      products, rounding of U, the covariance functions and the coordinate
-//      offsets), so every j with |rho_ij| >= tau_i (1 - 2e-12) is kept;
+//   2. a pass over all pairs j < i on the tensor cores (U U^T in BF16 tiles
+//      of 128 x 256, FP32 accumulation, rfilter_tc_kernel below) that keeps
+//      every j whose |rho| can reach tau_i: the test carries a rigorous
+//      bound on the error of the BF16 dot product, of the FP32 covariance
+//      functions and of the coordinate offsets, so every j with |rho_ij| >=
+//      tau_i (1 - 2e-12) is kept;
 //   3. the kept candidates ranked in FP64, the top m + 1 kept in order.
 // A row whose candidates overflow the kVifCand slots takes the m-th best of
 // the stored ones (exact, so still a lower bound) as its threshold and is
@@ -23,9 +24,13 @@
 // dropped j has |rho_ij| < tau_i (1 - 2e-12) <= the m-th value (1 - 2e-12).
 #include <algorithm>
 #include <climits>
+#include <cmath>
+
+#include <cuda_bf16.h>
 
 #include "kernels.h"
 #include "profile.h"
+#include "umma.cuh"
 #include "vif.h"
 #include "workspace.h"
 
@@ -33,6 +38,7 @@ namespace vst {
 
 vst_status fail(vst_status s, const char* fmt, ...);
 vst_status cuda_fail(cudaError_t e, const char* where);
+void launch_lag_table(const DevTheta& th, LagD* d, LagF* f, cudaStream_t st);
 vst_status plain_knn(const double* xy, const double* t, int64_t n, const vst_theta* theta, int m, int32_t* nn,
                      int32_t* nn_cnt, int64_t* tie_rows, int64_t tie_cap, char* base, const WsLayout& L,
                      WsHeader* hdr, int64_t n_cand, int64_t row0, cudaStream_t st);
@@ -171,136 +177,347 @@ __device__ __forceinline__ float cov32_err(const DevTheta& th, float dx, float d
   return C;
 }
 
-// ---- stage 2: candidates.  Tiles of 128 rows x 64 columns covering j < i
-// (row tile ti, column tiles 0..2 ti + 1); 256 threads, 4 x 8 products per
-// thread, K step 16.  Each 16-term chunk is summed in FP32 and added to a
-// double-float accumulator, so the dot product's error is below
-// 24 u |U_i| |U_j| (Cauchy-Schwarz on 18 u sum |U_ic U_jc|, plus the
-// rounding of U to FP32 and of the final value).
+// ---- stage 2 on the tensor cores.  The dot products U_i . U_j of the pairs
+// j < i are the lower triangle of U U^T, a dense contraction over the k
+// inducing points: BF16 tcgen05 tiles of 128 rows i x 256 columns j, K = k
+// padded to 64, FP32 accumulation in tensor memory, with the threshold test
+// fused into the epilogue.  Error of the BF16 dot: each U entry is rounded
+// once to BF16 (relative 2^-9), a product of two rounded entries is exact in
+// FP32, so the rounding contributes at most (2^-8 + 2^-18) sum_c |U_ic U_jc|;
+// the tensor core's FP32 accumulation adds at most k 2^-22 of the same sum
+// (a few ulps per MMA step, counted per term), and sum |U_ic U_jc| <=
+// |U_i| |U_j|.  A pair is then kept under the same rule as the FP32 tile pass
+// with this dot bound.  Most pairs are dismissed by a cheap test first:
+// |dot| + bound + Cmax < tau_i s_i s_j, with Cmax = sigma1^2 psi(u_min)^-(delta
+// + gamma) >= C_ij over the tile (u_min the smallest lag between the tiles'
+// time ranges, M_nu <= 1); the rest evaluate C_ij and its error bound.
+//
+// Work: row tiles I of 128 rows and column tiles J of 256 with 256 J <=
+// 128 I (every tile holds pairs j < i), grouped by 16 row tiles; inside a
+// group the column tiles in increasing order, for each the group's row tiles
+// (I >= 2 J).  A persistent CTA per SM takes the items round-robin, so the
+// CTAs at work share a group's A tiles and a few B tiles in L2.
+// Roles (320 threads): warp 0 issues the TMA loads (4-stage ring of 64-wide K
+// blocks, 48 KiB each), warp 1 the MMAs (M = 128, N = 256, K = 16) into two
+// TMEM accumulators of 256 columns (tile t in buffer t % 2), warps 2-9 the
+// epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (= tile rows) and
+// columns 128 ((w - 2) / 4) .. + 127, and the 256 epilogue threads load the
+// tile's column records into shared memory (double-buffered by tile) first.
+constexpr int kRfBM = 128, kRfBN = 256, kRfBK = 64, kRfStages = 4, kRfGroup = 16;
+constexpr int kRfThreads = 320;
+constexpr uint64_t kRfWaitNs = 2000000000ull;  // 2 s per wait
+struct RfShape {
+  static constexpr int A_BYTES = kRfBM * kRfBK * 2;
+  static constexpr int B_BYTES = kRfBN * kRfBK * 2;
+  static constexpr int STAGE = A_BYTES + B_BYTES;
+  static constexpr int COL_BYTES = 2 * kRfBN * (16 + 4);  // float4 (x, y, t, s) + nu per column, 2 buffers
+  static constexpr int BAR_BYTES = 256;
+  static constexpr int SMEM = kRfStages * STAGE + COL_BYTES + BAR_BYTES + 1024;
+  static_assert(STAGE % 1024 == 0, "stage alignment");
+  static_assert(SMEM <= 232448, "shared memory");
+};
+
+struct RfArgs {
+  int64_t n;
+  int k, kb;            // inducing points, 64-wide K blocks
+  int T;                // row tiles
+  int ngroups;
+  const int64_t* gcum;  // [ngroups + 1] items before each group
+  const double2* tb128; // per row tile: (t_min, t_max)
+  const double2* tb256; // per column tile
+  const int* times_exact;
+  const LagF* lagf;     // FP32 lag table (P = sigma1^2 psi^-(delta+gamma))
+  float epsd;           // relative bound of the BF16 dot product
+};
+
+__device__ __forceinline__ void rf_item(const RfArgs& R, int64_t w, int& I, int& J) {
+  int lo = 0, hi = R.ngroups;  // largest G with gcum[G] <= w
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (R.gcum[mid] <= w) lo = mid; else hi = mid;
+  }
+  const int G = lo;
+  int64_t r = w - R.gcum[G];
+  const int I0 = G * kRfGroup, I1 = min(I0 + kRfGroup, R.T);
+  const int F = I1 - I0, Jf = I0 / 2;
+  if (r < (int64_t)(Jf + 1) * F) {
+    J = (int)(r / F);
+    I = I0 + (int)(r % F);
+    return;
+  }
+  r -= (int64_t)(Jf + 1) * F;
+  int j = Jf + 1;
+  for (;;) {
+    const int c = I1 - 2 * j;
+    if (r < c) break;
+    r -= c;
+    ++j;
+  }
+  J = j;
+  I = 2 * j + (int)r;
+}
+
 template <int NU>
-__global__ void __launch_bounds__(256) filter_kernel(KnnArgsV A, int64_t ntiles) {
-  constexpr int BI = 128, BJ = 64, BK = 16;
-  __shared__ __align__(16) float As[BK][BI + 4];
-  __shared__ __align__(16) float Bs[BK][BJ + 4];
-  __shared__ float rx[BI], ry[BI], rt[BI], cx[BJ], cy[BJ], ct[BJ];
-  __shared__ float4 rinfo[BI];
-  __shared__ float cs[BJ], cnu[BJ];
-  const int tid = threadIdx.x, tx = tid & 7, ty = tid >> 3;
-  const float sig = (float)A.th.sigma1sq, cpar = (float)A.th.c;
-  const float dotc = 24.0f * 1.05f * kU;
-  for (int64_t b = blockIdx.x; b < ntiles; b += gridDim.x) {
-    // b = ti (ti + 1) + tj, 0 <= tj <= 2 ti + 1
-    int64_t ti = (int64_t)((sqrt(4.0 * (double)b + 1.0) - 1.0) * 0.5);
-    while (ti * (ti + 1) > b) --ti;
-    while ((ti + 1) * (ti + 2) <= b) ++ti;
-    const int64_t tj = b - ti * (ti + 1);
-    const int64_t i0 = ti * BI, j0 = tj * BJ;
-    __syncthreads();
-    bool tok = true;
-    if (tid < BI) {
-      // coordinates and times as FP32 offsets from the tile's first row
-      // (computed in FP64); the time offsets must be exact in FP32 (integer
-      // days below 2^24), else the tile keeps every pair
-      const double X0 = A.xy[2 * i0], Y0 = A.xy[2 * i0 + 1], T0 = A.t[i0];
-      const int64_t i = i0 + tid;
-      const bool vi = i < A.n;
-      const double dti = vi ? A.t[i] - T0 : 0.0;
-      tok = dti == floor(dti) && fabs(dti) < 16777216.0;
-      rx[tid] = vi ? (float)(A.xy[2 * i] - X0) : 0.f;
-      ry[tid] = vi ? (float)(A.xy[2 * i + 1] - Y0) : 0.f;
-      rt[tid] = (float)dti;
-      rinfo[tid] = vi ? A.rowinfo[i] : make_float4(3.0e38f, 0.f, 0.f, 0.f);
-    } else if (tid < BI + BJ) {
-      const double X0 = A.xy[2 * i0], Y0 = A.xy[2 * i0 + 1], T0 = A.t[i0];
-      const int jl = tid - BI;
-      const int64_t j = j0 + jl;
-      const bool vj = j < A.n;
-      const double dtj = vj ? A.t[j] - T0 : 0.0;
-      tok = dtj == floor(dtj) && fabs(dtj) < 16777216.0;
-      cx[jl] = vj ? (float)(A.xy[2 * j] - X0) : 0.f;
-      cy[jl] = vj ? (float)(A.xy[2 * j + 1] - Y0) : 0.f;
-      ct[jl] = (float)dtj;
-      const float4 ci = vj ? A.rowinfo[j] : make_float4(0.f, 0.f, 0.f, 0.f);
-      cs[jl] = ci.y;
-      cnu[jl] = ci.z;
+__global__ void __launch_bounds__(kRfThreads, 1)
+    rfilter_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, KnnArgsV A,
+                      RfArgs R) {
+  extern __shared__ unsigned char rf_smem[];
+  const uint32_t raw = umma::smem_u32(rf_smem);
+  const uint32_t base = (raw + 1023u) & ~1023u;
+  unsigned char* gbase = rf_smem + (base - raw);
+  float4* colA = reinterpret_cast<float4*>(gbase + kRfStages * RfShape::STAGE);  // [2][256]
+  float* colB = reinterpret_cast<float*>(colA + 2 * kRfBN);                    // [2][256]
+  uint64_t* full = reinterpret_cast<uint64_t*>(gbase + kRfStages * RfShape::STAGE + RfShape::COL_BYTES);
+  uint64_t* empty = full + kRfStages;
+  uint64_t* accf = empty + kRfStages;  // [2] accumulator filled
+  uint64_t* acce = accf + 2;           // [2] accumulator drained (8 epilogue warps)
+  uint64_t* done = acce + 2;           // every MMA of this CTA finished
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  volatile uint32_t* epi_fail = tslot + 1;  // an epilogue warp's wait ran out
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t items = R.gcum[R.ngroups];
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kRfStages; ++s) {
+      umma::mbar_init(&full[s], 1);
+      umma::mbar_init(&empty[s], 1);
     }
-    const int times_exact = __syncthreads_and(tok);
-    float hi[4][8], lo[4][8];
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int v = 0; v < 8; ++v) hi[u][v] = lo[u][v] = 0.f;
-    for (int kb = 0; kb < A.k; kb += BK) {
-      __syncthreads();
-      for (int q = tid; q < BK * (BI + BJ); q += 256) {
-        const int kk = q & (BK - 1), rr = q >> 4;
-        if (rr < BI) {
-          const int64_t i = i0 + rr;
-          As[kk][rr] = (i < A.n && kb + kk < A.k) ? A.Uf[i * A.k + kb + kk] : 0.f;
-        } else {
-          const int64_t j = j0 + rr - BI;
-          Bs[kk][rr - BI] = (j < A.n && kb + kk < A.k) ? A.Uf[j * A.k + kb + kk] : 0.f;
-        }
-      }
-      __syncthreads();
-      float acc[4][8];
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 8; ++v) acc[u][v] = 0.f;
-#pragma unroll
-      for (int kk = 0; kk < BK; ++kk) {
-        const float4 a0 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
-        const float4 b0 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8]);
-        const float4 b1 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 8 + 4]);
-        const float av[4] = {a0.x, a0.y, a0.z, a0.w};
-        const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int v = 0; v < 8; ++v) acc[u][v] = fmaf(av[u], bv[v], acc[u][v]);
-      }
-#pragma unroll
-      for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 8; ++v) {
-          const df t = df_two_sum(hi[u][v], acc[u][v]);
-          hi[u][v] = t.hi;
-          lo[u][v] += t.lo;
-        }
+    for (int b = 0; b < 2; ++b) {
+      umma::mbar_init(&accf[b], 1);
+      umma::mbar_init(&acce[b], 8);
     }
+    umma::mbar_init(done, 1);
+    *epi_fail = 0u;
+    umma::fence_mbar_init();
+  }
+  if (warp == 0) {
+    umma::tmem_alloc(umma::smem_u32(tslot), 512);
+    umma::tmem_relinquish();
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t tmem = *tslot;
+  bool ok = true;
+  auto warp_wait = [&](uint64_t* bar, uint32_t parity) {
+    bool d = true;
+    if (lane == 0) d = umma::mbar_wait(bar, parity, kRfWaitNs);
+    return __shfl_sync(0xffffffffu, d ? 1 : 0, 0) != 0;
+  };
+
+  if (warp == 0) {
+    // producer
+    int64_t cnt = 0;
+    for (int64_t w = blockIdx.x; w < items && ok; w += gridDim.x) {
+      int I, J;
+      rf_item(R, w, I, J);
+      for (int kb = 0; kb < R.kb; ++kb, ++cnt) {
+        const int s = (int)(cnt % kRfStages);
+        const uint32_t use = (uint32_t)(cnt / kRfStages);
+        if (use > 0 && !warp_wait(&empty[s], (use - 1) & 1u)) {
+          ok = false;
+          break;
+        }
+        if (lane == 0) {
+          umma::mbar_arrive_expect_tx(&full[s], RfShape::STAGE);
+          const uint32_t sa = base + s * RfShape::STAGE, sb = sa + RfShape::A_BYTES;
+          umma::tma_load_2d(sa, &tmA, kb * kRfBK, I * kRfBM, &full[s]);
+          umma::tma_load_2d(sb, &tmB, kb * kRfBK, J * kRfBN, &full[s]);
+        }
+        __syncwarp();
+      }
+    }
+    if (!ok) {
+      // let the loads still in flight land before the CTA's shared memory goes
+      for (int64_t c = cnt - kRfStages < 0 ? 0 : cnt - kRfStages; c < cnt; ++c)
+        warp_wait(&full[c % kRfStages], (uint32_t)(c / kRfStages) & 1u);
+    }
+  } else if (warp == 1) {
+    // MMA issuer
+    constexpr uint32_t idesc = umma::idesc_bf16_f32(kRfBM, kRfBN);
+    int64_t cnt = 0, it = 0;
+    for (int64_t w = blockIdx.x; w < items && ok; w += gridDim.x, ++it) {
+      const int b = (int)(it & 1);
+      if (it >= 2 && !warp_wait(&acce[b], (uint32_t)((it >> 1) - 1) & 1u)) {
+        ok = false;
+        break;
+      }
+      umma::fence_after_sync();
+      const uint32_t tb = tmem + (uint32_t)(b * kRfBN);
+      for (int kb = 0; kb < R.kb; ++kb, ++cnt) {
+        const int s = (int)(cnt % kRfStages);
+        if (!warp_wait(&full[s], (uint32_t)(cnt / kRfStages) & 1u)) {
+          ok = false;
+          break;
+        }
+        umma::fence_after_sync();
+        if (lane == 0) {
+          const uint32_t sa = base + s * RfShape::STAGE, sb = sa + RfShape::A_BYTES;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int il = ty * 4 + u;
-      const int64_t i = i0 + il;
-      if (i >= A.n) continue;
-      const float4 ri = rinfo[il];
-      if (ri.w != 0.0f) continue;  // searched by the second pass
-      const float xi = rx[il], yi = ry[il], tiv = rt[il];
+          for (int kk = 0; kk < kRfBK / 16; ++kk)
+            umma::mma_bf16(tb, umma::desc_kmajor_sw128(sa + kk * 32), umma::desc_kmajor_sw128(sb + kk * 32), idesc,
+                           (kb | kk) != 0 ? 1u : 0u);
+          umma::mma_commit(&empty[s]);
+        }
+        __syncwarp();
+      }
+      if (!ok) break;
+      if (lane == 0) umma::mma_commit(&accf[b]);
+      __syncwarp();
+    }
+    // every MMA this thread issued has finished before the tensor memory is freed
+    if (lane == 0) umma::mma_commit(done);
+    __syncwarp();
+    if (!warp_wait(done, 0)) ok = false;
+  } else {
+    // epilogue: 8 warps, 256 threads
+    const int et = threadIdx.x - 64;
+    const int q4 = warp & 3, half = (warp - 2) >> 2;
+    const int r = q4 * 32 + lane;
+    const float sig = (float)A.th.sigma1sq, cpar = (float)A.th.c;
+    const int texact = *R.times_exact;
+    int64_t it = 0;
+    for (int64_t w = blockIdx.x; w < items; w += gridDim.x, ++it) {
+      int I, J;
+      rf_item(R, w, I, J);
+      const int b = (int)(it & 1);
+      const int64_t i0 = (int64_t)I * kRfBM, j0 = (int64_t)J * kRfBN;
+      const double X0 = A.xy[2 * i0], Y0 = A.xy[2 * i0 + 1];
+      // this thread's column record: offsets from the row tile's first point
+      {
+        const int64_t j = j0 + et;
+        float4 ca = make_float4(0.f, 0.f, 0.f, 0.f);
+        float cb = 0.f;
+        if (j < A.n) {
+          const float4 ij = A.rowinfo[j];
+          ca = make_float4((float)(A.xy[2 * j] - X0), (float)(A.xy[2 * j + 1] - Y0), (float)A.t[j], ij.y);
+          cb = ij.z;
+        }
+        colA[b * kRfBN + et] = ca;
+        colB[b * kRfBN + et] = cb;
+      }
+      // bound of C over the tile pair from the two time ranges
+      float cmax = sig;
+      if (texact) {
+        const double2 ti = R.tb128[I], tj = R.tb256[J];
+        const double u = fmax(0.0, fmax(ti.x - tj.y, tj.x - ti.y));
+        const int lag = (int)fmin(u, (double)(kLagTab - 1));
+        cmax = R.lagf[lag].P * (1.0f + 1.0e-5f) + 1.0e-30f;
+      }
+      const int64_t i = i0 + r;
+      float4 ri = make_float4(0.f, 0.f, 0.f, 1.f);
+      float xi = 0.f, yi = 0.f, tiv = 0.f;
+      if (i < A.n) {
+        ri = A.rowinfo[i];
+        xi = (float)(A.xy[2 * i] - X0);
+        yi = (float)(A.xy[2 * i + 1] - Y0);
+        tiv = (float)A.t[i];
+      }
+      const bool rowon = i < A.n && ri.w == 0.0f;
       const float offi = fabsf(xi) + fabsf(yi);
+      const float eu = R.epsd * ri.z;
+      // the eight warps pass the same barriers: a warp whose wait ran out
+      // says so here, and all of them stop together after the barrier
+      if (!ok && lane == 0) *epi_fail = 1u;
+      asm volatile("bar.sync 1, 256;" ::: "memory");  // column records written
+      if (*epi_fail != 0u) break;
+      if (!warp_wait(&accf[b], (uint32_t)(it >> 1) & 1u)) {
+        ok = false;
+        continue;
+      }
+      umma::fence_after_sync();
+      const uint32_t ta = tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * kRfBN + half * 128);
+#pragma unroll 1
+      for (int ch = 0; ch < 4; ++ch) {
+        uint32_t v[32];
+        __syncwarp();
+        umma::tmem_ld_32x32b_x32(ta + ch * 32, v);
+        umma::tmem_wait_ld();
+        if (ch == 3) {
+          // the buffer is free for the MMAs once its last columns are read
+          umma::fence_before_sync();
+          __syncwarp();
+          if (lane == 0) umma::mbar_arrive(&acce[b]);
+        }
+        if (!rowon) continue;
+        const int cb0 = half * 128 + ch * 32;
 #pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        const int jl = tx * 8 + v;
-        const int64_t j = j0 + jl;
-        if (j >= i) continue;
-        float rel;
-        const float C = cov32_err<NU>(A.th, xi - cx[jl], yi - cy[jl], tiv - ct[jl], rel);
-        const float R = fabsf(C - (hi[u][v] + lo[u][v]));
-        // covariance: functions, and the coordinate offsets (|dC/dx| <= C,
-        // G <= c, |dh| <= 2u (|x_i| + |y_i| + |x_j| + |y_j|)); dot product;
-        // an underflow floor
-        const float offs = offi + fabsf(cx[jl]) + fabsf(cy[jl]);
-        const float bound = 1.1f * fabsf(C) * (rel * kU + cpar * 2.0f * kU * offs) + dotc * ri.z * cnu[jl] +
-                            1.0e-33f * sig;
-        const float rhs = ri.x * cs[jl];
-        // keep if |R| + bound >= tau_i s_i s_j; the extra half bound and the
-        // 4u terms cover the rounding of this test
-        if (!times_exact || R + 1.5f * bound + 4.0f * kU * (R + fabsf(rhs)) >= rhs) {
-          const int slot = atomicAdd(&A.ccount[i], 1);
-          if (slot < kVifCand) A.cand[i * kVifCand + slot] = (int32_t)j;
+        for (int q = 0; q < 32; ++q) {
+          const int c = cb0 + q;
+          const int64_t j = j0 + c;
+          if (j >= i) continue;
+          const float4 cm = colA[b * kRfBN + c];
+          const float nuj = colB[b * kRfBN + c];
+          const float dot = __uint_as_float(v[q]);
+          const float rhs = ri.x * cm.w;
+          const float db = eu * nuj;
+          if ((fabsf(dot) + db + cmax) * (1.0f + 16.0f * kU) < rhs) continue;
+          bool keep = !texact;
+          if (!keep) {
+            float rel;
+            const float C = cov32_err<NU>(A.th, xi - cm.x, yi - cm.y, tiv - cm.z, rel);
+            const float Rv = fabsf(C - dot);
+            const float offs = offi + fabsf(cm.x) + fabsf(cm.y);
+            const float bound = 1.1f * fabsf(C) * (rel * kU + cpar * 2.0f * kU * offs) + db + 1.0e-33f * sig;
+            keep = Rv + 1.5f * bound + 4.0f * kU * (Rv + fabsf(rhs)) >= rhs;
+          }
+          if (keep) {
+            const int slot = atomicAdd(&A.ccount[i], 1);
+            if (slot < kVifCand) A.cand[i * kVifCand + slot] = (int32_t)j;
+          }
         }
       }
     }
+  }
+  if (!ok) report_error(A.hdr, VST_ETIMEOUT, (int64_t)blockIdx.x);
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(tmem, 512);
+}
+
+// items before each group of kRfGroup row tiles (one thread)
+__global__ void rf_groups_kernel(int T, int ngroups, int64_t* gcum) {
+  int64_t acc = 0;
+  for (int G = 0; G < ngroups; ++G) {
+    gcum[G] = acc;
+    const int I0 = G * kRfGroup, I1 = min(I0 + kRfGroup, T);
+    for (int I = I0; I < I1; ++I) acc += I / 2 + 1;
+  }
+  gcum[ngroups] = acc;
+}
+
+// per tile of `rows` consecutive points: (t_min, t_max); one warp per tile
+__global__ void tile_times_kernel(const double* t, int64_t n, int rows, int64_t ntiles, double2* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (tile >= ntiles) return;
+  double mn = 1.0e300, mx = -1.0e300;
+  for (int64_t q = tile * rows + lane; q < min(n, (tile + 1) * rows); q += 32) {
+    mn = fmin(mn, t[q]);
+    mx = fmax(mx, t[q]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fmin(mn, __shfl_xor_sync(kFull, mn, o));
+    mx = fmax(mx, __shfl_xor_sync(kFull, mx, o));
+  }
+  if (lane == 0) out[tile] = make_double2(mn, mx);
+}
+
+// 1 if every time is an integer day with |t| < 2^24 (exact in FP32)
+__global__ void times_exact_kernel(const double* t, int64_t n, int* flag) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const double v = t[q];
+    if (!(v == floor(v) && fabs(v) < 16777216.0)) atomicAnd(flag, 0);
+  }
+}
+
+// U (FP64 [n][k]) -> BF16 [n][k64] (k64 = k rounded up to 64, zero padded)
+__global__ void u_bf16_kernel(const double* U, int64_t n, int k, int k64, __nv_bfloat16* Ub) {
+  const int64_t total = n * (int64_t)k64;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = q / k64;
+    const int c = (int)(q - i * k64);
+    Ub[q] = c < k ? __double2bfloat16(U[i * k + c]) : __float2bfloat16(0.0f);
   }
 }
 
@@ -497,18 +714,66 @@ void launch_rows_per_warp(K kern, const KnnArgsV& A, cudaStream_t st, size_t byt
   kern<<<std::max(1, per) * sms, W * 32, smem, st>>>(A);
 }
 
+// stage 2 on the tensor cores (rfilter_tc_kernel) with its inputs: U in BF16
+// after the FP32 copy in the operand region, per-tile time ranges, the item
+// counts per group and the times flag in the (idle) residual-Gram region
 template <int NU>
-vst_status knn_stages(const KnnArgsV& A, cudaStream_t st) {
-  constexpr int W = 4;
-  launch_rows_per_warp(tau_kernel<NU, W>, A, st);
-  const int64_t T = (A.n + 127) / 128;
-  const int64_t ntiles = T * (T + 1);  // 128-row tiles x 64-column tiles with j < i
-  int dev = 0, sms = 0, per = 0;
+vst_status tc_filter(const KnnArgsV& A, char* vb, const VifLayout& V, const LagF* lagf, cudaStream_t st) {
+  const int64_t n = A.n;
+  const int k = A.k, k64 = (k + 63) / 64 * 64;
+  __nv_bfloat16* Ub = reinterpret_cast<__nv_bfloat16*>(vb + V.Ap + align256(sizeof(float) * (size_t)n * k));
+  const int T = (int)((n + kRfBM - 1) / kRfBM), T2 = (int)((n + kRfBN - 1) / kRfBN);
+  const int ngroups = (T + kRfGroup - 1) / kRfGroup;
+  char* sc = vb + V.gram;
+  int64_t* gcum = reinterpret_cast<int64_t*>(sc);
+  double2* tb128 = reinterpret_cast<double2*>(sc + align256(sizeof(int64_t) * (ngroups + 1)));
+  double2* tb256 = tb128 + T;
+  int* texact = reinterpret_cast<int*>(tb256 + T2);
+  int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, filter_kernel<NU>, 256, 0);
-  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(1, per) * sms * 8);
-  filter_kernel<NU><<<(unsigned)grid, 256, 0, st>>>(A, ntiles);
+  cudaError_t e = cudaMemsetAsync(texact, 0xff, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  times_exact_kernel<<<sms * 4, 256, 0, st>>>(A.t, n, texact);
+  tile_times_kernel<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(A.t, n, kRfBM, T, tb128);
+  tile_times_kernel<<<(unsigned)((T2 * 32 + 255) / 256), 256, 0, st>>>(A.t, n, kRfBN, T2, tb256);
+  rf_groups_kernel<<<1, 1, 0, st>>>(T, ngroups, gcum);
+  u_bf16_kernel<<<sms * 8, 256, 0, st>>>(A.U, n, k, k64, Ub);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "filter set-up kernels");
+  CUtensorMap ta, tb;
+  if (!tc_make_map_bf16(&ta, Ub, (uint64_t)n, (uint64_t)k64, kRfBM) ||
+      !tc_make_map_bf16(&tb, Ub, (uint64_t)n, (uint64_t)k64, kRfBN))
+    return fail(VST_ECUDA, "residual filter: tensor map encoding failed");
+  RfArgs R{};
+  R.n = n;
+  R.k = k;
+  R.kb = k64 / kRfBK;
+  R.T = T;
+  R.ngroups = ngroups;
+  R.gcum = gcum;
+  R.tb128 = tb128;
+  R.tb256 = tb256;
+  R.times_exact = texact;
+  R.lagf = lagf;
+  // BF16 rounding of both factors plus the FP32 accumulation, 5% margin
+  R.epsd = (float)(1.05 * (std::ldexp(1.0, -8) + std::ldexp(1.0, -18) + (double)k64 * std::ldexp(1.0, -22)));
+  auto kern = rfilter_tc_kernel<NU>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, RfShape::SMEM);
+  if (e != cudaSuccess) return cuda_fail(e, "residual filter attributes");
+  kern<<<sms, kRfThreads, RfShape::SMEM, st>>>(ta, tb, A, R);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? VST_OK : cuda_fail(e, "residual filter kernel");
+}
+
+template <int NU>
+vst_status knn_stages(const KnnArgsV& A, char* vb, const VifLayout& V, const LagF* lagf, cudaStream_t st) {
+  constexpr int W = 4;
+  launch_rows_per_warp(tau_kernel<NU, W>, A, st);
+  if (A.n > 1) {
+    const vst_status s = tc_filter<NU>(A, vb, V, lagf, st);
+    if (s != VST_OK) return s;
+  }
   launch_rows_per_warp(rerank_kernel<NU, W>, A, st);
   {
     const size_t smem = (sizeof(double) + sizeof(float)) * A.k;
@@ -567,8 +832,14 @@ vst_status vif_knn(const vst_points* pts, const vst_theta* theta, int m, const v
   if (e != cudaSuccess) return cuda_fail(e, "memset");
   narrow_kernel<<<(unsigned)std::min<int64_t>((n * k + 255) / 256, 65535), 256, 0, st>>>(A.U, n * k,
                                                                                          const_cast<float*>(A.Uf));
+  // FP32 lag table (its amplitudes bound the covariance of a tile pair)
+  LagD* lagd = reinterpret_cast<LagD*>(base + L.lagd);
+  LagF* lagf = reinterpret_cast<LagF*>(base + L.lagf);
+  launch_lag_table(A.th, lagd, lagf, st);
   ProfileScope ps(kProfKnn, st);
-  return nu == 0 ? knn_stages<0>(A, st) : nu == 1 ? knn_stages<1>(A, st) : knn_stages<2>(A, st);
+  return nu == 0   ? knn_stages<0>(A, vb, V, lagf, st)
+         : nu == 1 ? knn_stages<1>(A, vb, V, lagf, st)
+                   : knn_stages<2>(A, vb, V, lagf, st);
 }
 
 }  // namespace vst

@@ -846,6 +846,10 @@ vst_status lowrank_tc_P(const vst_points* pts, const vst_theta* theta, const vst
 // FP64 k x k matrix M (bmode 1: M itself; 2: M^T of a lower-triangular M),
 // split_terms = 3 or 6 as in the mixed NLL.  Uses the NLL's operand-part
 // buffers, free once U is formed.
+bool tc_make_map_bf16(CUtensorMap* map, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows) {
+  return make_map(map, ptr, rows, cols, box_rows);
+}
+
 vst_status tc_product(const float* A, int64_t lda, int64_t n, const double* M, int bmode, int k, float* C,
                       int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st) {
   if (n <= 0) return VST_OK;

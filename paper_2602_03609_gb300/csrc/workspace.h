@@ -67,7 +67,9 @@ inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
   L.dinfo = take(sizeof(int64_t) * 4);
   L.dtab = take(sizeof(float) * 2 * kk * (size_t)kVifMaxDays);
   const size_t kp = (size_t)vif_kp((int64_t)kk);
-  L.Ap = take(2 * (size_t)kVifMaxParts * nn * kp);
+  // (the residual neighbour search keeps U in FP32 and then in BF16 [n][k
+  // rounded up to 64] here; the 1 KiB covers the alignment between the two)
+  L.Ap = take(2 * (size_t)kVifMaxParts * nn * kp + 1024);
   L.Bp = take(2 * (size_t)kVifMaxParts * kp * kp);
   L.zf = take(16 * kk);
   L.rpart = take(sizeof(double) * nn * (kp / 128));
