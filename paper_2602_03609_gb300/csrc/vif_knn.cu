@@ -67,6 +67,9 @@ struct KnnArgsV {
   int64_t* tie_rows;
   int64_t tie_cap;
   WsHeader* hdr;
+  // rerank over a list of rows instead of all rows (nullptr: all)
+  const int32_t* rlist;
+  int64_t rlist_n;
 };
 
 // FP64 |rho_ij| of row i (U_i in shared memory) for up to 32 predecessors,
@@ -152,6 +155,14 @@ __global__ void narrow_kernel(const double* U, int64_t count, float* Uf) {
     Uf[q] = (float)U[q];
 }
 
+// the FP32 parameters the covariance below uses
+struct CovF {
+  float alpha, a, p, s1, c, gamma;
+};
+__device__ __forceinline__ CovF cov_f(const DevTheta& th) {
+  return CovF{(float)th.alpha, (float)th.a, (float)th.p, (float)th.sigma1sq, (float)th.c, (float)th.gamma};
+}
+
 // covariance of Eq. (2) in FP32 (the same steps as the mixed form's cov32)
 // and a bound on its relative error in units of u = 2^-24, from the error
 // bounds of the FP32 functions (log2f 2 ulp, exp2f / expf / rsqrtf 3 ulp,
@@ -159,22 +170,26 @@ __global__ void narrow_kernel(const double* U, int64_t count, float* Uf) {
 // psi^-p grows with p |log2 psi| and the |2 alpha log2|u|| of the inner
 // power), the Matern argument x = G h (its relative error enters C times x)
 template <int NU>
-__device__ __forceinline__ float cov32_err(const DevTheta& th, float dx, float dy, float u, float& rel) {
+__device__ __forceinline__ float cov32_err(const CovF& th, float dx, float dy, float u, float& rel) {
   const float au = fabsf(u);
   const float l2 = au > 0.f ? log2f(au) : 0.f;
-  const float arg = 2.0f * (float)th.alpha * l2;
-  const float psi = au > 0.f ? fmaf((float)th.a, exp2f(arg), 1.0f) : 1.0f;
+  const float arg = 2.0f * th.alpha * l2;
+  const float psi = au > 0.f ? fmaf(th.a, exp2f(arg), 1.0f) : 1.0f;
   const float lp = log2f(psi);
-  const float P = (float)th.sigma1sq * exp2f(-(float)th.p * lp);
-  const float G = (float)th.c * exp2f(-0.5f * (float)th.gamma * lp);
+  const float P = th.s1 * exp2f(-th.p * lp);
+  const float G = th.c * exp2f(-0.5f * th.gamma * lp);
   const float d2 = dx * dx + dy * dy;
   const float x = G * (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f);
   const float C = P * matern_M<NU, float>(x, expf(-x));
   const float core = 4.3f * fabsf(arg) + 8.1f + 4.2f * fabsf(lp);
-  const float relP = fabsf((float)th.p) * core + 8.0f;
-  const float relx = 0.5f * fabsf((float)th.gamma) * core + 19.0f;
+  const float relP = fabsf(th.p) * core + 8.0f;
+  const float relx = 0.5f * fabsf(th.gamma) * core + 19.0f;
   rel = 1.25f * (relP + x * relx + 10.0f) + 16.0f;
   return C;
+}
+template <int NU>
+__device__ __forceinline__ float cov32_err(const DevTheta& th, float dx, float dy, float u, float& rel) {
+  return cov32_err<NU>(cov_f(th), dx, dy, u, rel);
 }
 
 // ---- stage 2 on the tensor cores.  The dot products U_i . U_j of the pairs
@@ -203,14 +218,14 @@ __device__ __forceinline__ float cov32_err(const DevTheta& th, float dx, float d
 // epilogue: warp w reads TMEM lanes 32 (w % 4) .. + 31 (= tile rows) and
 // columns 128 ((w - 2) / 4) .. + 127, and the 256 epilogue threads load the
 // tile's column records into shared memory (double-buffered by tile) first.
-constexpr int kRfBM = 128, kRfBN = 256, kRfBK = 64, kRfStages = 4, kRfGroup = 16;
+constexpr int kRfBM = kKnnTileRows, kRfBN = kKnnTileCols, kRfBK = 64, kRfStages = 4, kRfGroup = kKnnGroup;
 constexpr int kRfThreads = 320;
 constexpr uint64_t kRfWaitNs = 2000000000ull;  // 2 s per wait
 struct RfShape {
   static constexpr int A_BYTES = kRfBM * kRfBK * 2;
   static constexpr int B_BYTES = kRfBN * kRfBK * 2;
   static constexpr int STAGE = A_BYTES + B_BYTES;
-  static constexpr int COL_BYTES = 2 * kRfBN * (16 + 4);  // float4 (x, y, t, s) + nu per column, 2 buffers
+  static constexpr int COL_BYTES = 2 * kRfBN * (8 + 16);  // per column (s, nu) and (x, y, t, s), 2 buffers
   static constexpr int BAR_BYTES = 256;
   static constexpr int SMEM = kRfStages * STAGE + COL_BYTES + BAR_BYTES + 1024;
   static_assert(STAGE % 1024 == 0, "stage alignment");
@@ -228,9 +243,24 @@ struct RfArgs {
   const int* times_exact;
   const LagF* lagf;     // FP32 lag table (P = sigma1^2 psi^-(delta+gamma))
   float epsd;           // relative bound of the BF16 dot product
+  // gathered mode (rows != nullptr): the A operand holds the U rows of the
+  // listed rows (nrows of them, tile I = list entries 128 I ..); items are
+  // (I, J) for I < nt and J < nj, J from the last column tile down
+  const int32_t* rows;
+  int64_t nrows;
+  int nt, nj;
+  const double2* tbg;   // per gathered row tile: (t_min, t_max)
 };
 
 __device__ __forceinline__ void rf_item(const RfArgs& R, int64_t w, int& I, int& J) {
+  if (R.rows) {
+    // the latest columns first: a row's most correlated predecessors tend to
+    // be recent (time-stratified order), and the candidates that fit in the
+    // row's slots give the next round its threshold
+    I = (int)(w % R.nt);
+    J = R.nj - 1 - (int)(w / R.nt);
+    return;
+  }
   int lo = 0, hi = R.ngroups;  // largest G with gcum[G] <= w
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -257,6 +287,31 @@ __device__ __forceinline__ void rf_item(const RfArgs& R, int64_t w, int& I, int&
   I = 2 * j + (int)r;
 }
 
+// Exact test of one pair that passed the cheap test: FP32 covariance with its
+// error bound, the BF16 dot's bound, and the same keep rule as the FP32
+// passes; appends j to row i's candidates.  Not inlined: one copy of the code
+// serves the 32 columns of a chunk.
+template <int NU>
+__device__ __noinline__ void rf_exact(CovF cf, float dot, float4 cm, float nuj, float xi, float yi, float ti,
+                                      float offi, float thr, float eu, int texact, int64_t i, int j, int32_t* ccount,
+                                      int32_t* cand) {
+  const float rhs = thr * cm.w;
+  const float db = eu * nuj;
+  bool keep = !texact;
+  if (!keep) {
+    float rel;
+    const float C = cov32_err<NU>(cf, xi - cm.x, yi - cm.y, ti - cm.z, rel);
+    const float Rv = fabsf(C - dot);
+    const float offs = offi + fabsf(cm.x) + fabsf(cm.y);
+    const float bound = 1.1f * fabsf(C) * (rel * kU + cf.c * 2.0f * kU * offs) + db + 1.0e-33f * cf.s1;
+    keep = Rv + 1.5f * bound + 4.0f * kU * (Rv + fabsf(rhs)) >= rhs;
+  }
+  if (keep) {
+    const int slot = atomicAdd(&ccount[i], 1);
+    if (slot < kVifCand) cand[i * kVifCand + slot] = (int32_t)j;
+  }
+}
+
 template <int NU>
 __global__ void __launch_bounds__(kRfThreads, 1)
     rfilter_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, KnnArgsV A,
@@ -265,8 +320,8 @@ __global__ void __launch_bounds__(kRfThreads, 1)
   const uint32_t raw = umma::smem_u32(rf_smem);
   const uint32_t base = (raw + 1023u) & ~1023u;
   unsigned char* gbase = rf_smem + (base - raw);
-  float4* colA = reinterpret_cast<float4*>(gbase + kRfStages * RfShape::STAGE);  // [2][256]
-  float* colB = reinterpret_cast<float*>(colA + 2 * kRfBN);                    // [2][256]
+  float4* colX = reinterpret_cast<float4*>(gbase + kRfStages * RfShape::STAGE);  // [2][256] (x, y, t, s)
+  float2* colS = reinterpret_cast<float2*>(colX + 2 * kRfBN);                  // [2][256] (s, nu)
   uint64_t* full = reinterpret_cast<uint64_t*>(gbase + kRfStages * RfShape::STAGE + RfShape::COL_BYTES);
   uint64_t* empty = full + kRfStages;
   uint64_t* accf = empty + kRfStages;  // [2] accumulator filled
@@ -276,7 +331,7 @@ __global__ void __launch_bounds__(kRfThreads, 1)
   volatile uint32_t* epi_fail = tslot + 1;  // an epilogue warp's wait ran out
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t items = R.gcum[R.ngroups];
+  const int64_t items = R.rows ? (int64_t)R.nt * R.nj : R.gcum[R.ngroups];
   if (threadIdx.x == 0) {
     for (int s = 0; s < kRfStages; ++s) {
       umma::mbar_init(&full[s], 1);
@@ -374,37 +429,39 @@ __global__ void __launch_bounds__(kRfThreads, 1)
     const int et = threadIdx.x - 64;
     const int q4 = warp & 3, half = (warp - 2) >> 2;
     const int r = q4 * 32 + lane;
-    const float sig = (float)A.th.sigma1sq, cpar = (float)A.th.c;
+    const float sig = (float)A.th.sigma1sq;
+    const CovF cf = cov_f(A.th);
     const int texact = *R.times_exact;
     int64_t it = 0;
     for (int64_t w = blockIdx.x; w < items; w += gridDim.x, ++it) {
       int I, J;
       rf_item(R, w, I, J);
       const int b = (int)(it & 1);
-      const int64_t i0 = (int64_t)I * kRfBM, j0 = (int64_t)J * kRfBN;
+      const int64_t i0 = R.rows ? (int64_t)R.rows[(int64_t)I * kRfBM] : (int64_t)I * kRfBM, j0 = (int64_t)J * kRfBN;
       const double X0 = A.xy[2 * i0], Y0 = A.xy[2 * i0 + 1];
       // this thread's column record: offsets from the row tile's first point
       {
         const int64_t j = j0 + et;
         float4 ca = make_float4(0.f, 0.f, 0.f, 0.f);
-        float cb = 0.f;
+        float2 cs = make_float2(0.f, 0.f);
         if (j < A.n) {
           const float4 ij = A.rowinfo[j];
           ca = make_float4((float)(A.xy[2 * j] - X0), (float)(A.xy[2 * j + 1] - Y0), (float)A.t[j], ij.y);
-          cb = ij.z;
+          cs = make_float2(ij.y, ij.z);
         }
-        colA[b * kRfBN + et] = ca;
-        colB[b * kRfBN + et] = cb;
+        colX[b * kRfBN + et] = ca;
+        colS[b * kRfBN + et] = cs;
       }
       // bound of C over the tile pair from the two time ranges
       float cmax = sig;
       if (texact) {
-        const double2 ti = R.tb128[I], tj = R.tb256[J];
+        const double2 ti = R.rows ? R.tbg[I] : R.tb128[I], tj = R.tb256[J];
         const double u = fmax(0.0, fmax(ti.x - tj.y, tj.x - ti.y));
         const int lag = (int)fmin(u, (double)(kLagTab - 1));
         cmax = R.lagf[lag].P * (1.0f + 1.0e-5f) + 1.0e-30f;
       }
-      const int64_t i = i0 + r;
+      const int64_t gi = (int64_t)I * kRfBM + r;  // gathered mode: list entry
+      const int64_t i = R.rows ? (gi < R.nrows ? (int64_t)R.rows[gi] : A.n) : i0 + r;
       float4 ri = make_float4(0.f, 0.f, 0.f, 1.f);
       float xi = 0.f, yi = 0.f, tiv = 0.f;
       if (i < A.n) {
@@ -416,6 +473,7 @@ __global__ void __launch_bounds__(kRfThreads, 1)
       const bool rowon = i < A.n && ri.w == 0.0f;
       const float offi = fabsf(xi) + fabsf(yi);
       const float eu = R.epsd * ri.z;
+      const int climit = (int)(i - j0);  // columns c < climit have j < i
       // the eight warps pass the same barriers: a warp whose wait ran out
       // says so here, and all of them stop together after the barrier
       if (!ok && lane == 0) *epi_fail = 1u;
@@ -439,32 +497,23 @@ __global__ void __launch_bounds__(kRfThreads, 1)
           __syncwarp();
           if (lane == 0) umma::mbar_arrive(&acce[b]);
         }
-        if (!rowon) continue;
+        // cheap test for the 32 columns, a bit per column that may qualify
         const int cb0 = half * 128 + ch * 32;
+        uint32_t mask = 0u;
 #pragma unroll
         for (int q = 0; q < 32; ++q) {
-          const int c = cb0 + q;
-          const int64_t j = j0 + c;
-          if (j >= i) continue;
-          const float4 cm = colA[b * kRfBN + c];
-          const float nuj = colB[b * kRfBN + c];
-          const float dot = __uint_as_float(v[q]);
-          const float rhs = ri.x * cm.w;
-          const float db = eu * nuj;
-          if ((fabsf(dot) + db + cmax) * (1.0f + 16.0f * kU) < rhs) continue;
-          bool keep = !texact;
-          if (!keep) {
-            float rel;
-            const float C = cov32_err<NU>(A.th, xi - cm.x, yi - cm.y, tiv - cm.z, rel);
-            const float Rv = fabsf(C - dot);
-            const float offs = offi + fabsf(cm.x) + fabsf(cm.y);
-            const float bound = 1.1f * fabsf(C) * (rel * kU + cpar * 2.0f * kU * offs) + db + 1.0e-33f * sig;
-            keep = Rv + 1.5f * bound + 4.0f * kU * (Rv + fabsf(rhs)) >= rhs;
-          }
-          if (keep) {
-            const int slot = atomicAdd(&A.ccount[i], 1);
-            if (slot < kVifCand) A.cand[i * kVifCand + slot] = (int32_t)j;
-          }
+          const float2 sn = colS[b * kRfBN + cb0 + q];
+          const float rhs = ri.x * sn.x;
+          const float ub = fabsf(__uint_as_float(v[q])) + fmaf(eu, sn.y, cmax);
+          mask |= (ub * (1.0f + 16.0f * kU) >= rhs && cb0 + q < climit) ? (1u << q) : 0u;
+        }
+        if (!rowon) mask = 0u;
+        if (__any_sync(kFull, mask != 0u)) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q)
+            if (mask & (1u << q))
+              rf_exact<NU>(cf, __uint_as_float(v[q]), colX[b * kRfBN + cb0 + q], colS[b * kRfBN + cb0 + q].y, xi, yi,
+                           tiv, offi, ri.x, eu, texact, i, (int)j0 + cb0 + q, A.ccount, A.cand);
         }
       }
     }
@@ -501,6 +550,78 @@ __global__ void tile_times_kernel(const double* t, int64_t n, int rows, int64_t 
     mx = fmax(mx, __shfl_xor_sync(kFull, mx, o));
   }
   if (lane == 0) out[tile] = make_double2(mn, mx);
+}
+
+// (t_min, t_max) of each tile of 128 listed rows; one warp per tile
+__global__ void tile_times_list_kernel(const double* t, const int32_t* rows, int64_t nrows, int64_t ntiles,
+                                       double2* out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t tile = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (tile >= ntiles) return;
+  double mn = 1.0e300, mx = -1.0e300;
+  for (int64_t q = tile * kRfBM + lane; q < min(nrows, (tile + 1) * kRfBM); q += 32) {
+    const double v = t[rows[q]];
+    mn = fmin(mn, v);
+    mx = fmax(mx, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = fmin(mn, __shfl_xor_sync(kFull, mn, o));
+    mx = fmax(mx, __shfl_xor_sync(kFull, mx, o));
+  }
+  if (lane == 0) out[tile] = make_double2(mn, mx);
+}
+
+// Rows of a list of the previous round: those without a defined residual
+// correlation (w != 0) appended to zlist (cnt[4]); those whose candidates
+// overflowed, now with a tighter threshold, to the gathered round's list, or
+// after the last round appended to the exhaustive list; counts and the
+// largest gathered row in cnt[0..2].  One block.
+__global__ void fb_split_kernel(const int32_t* fb, const unsigned long long* fbcount, const float4* rowinfo,
+                                int last, int32_t* glist, int32_t* xlist, int32_t* zlist, unsigned long long* cnt) {
+  const int64_t nfb = (int64_t)*fbcount;
+  for (int64_t q = threadIdx.x; q < nfb; q += blockDim.x) {
+    const int32_t i = fb[q];
+    if (rowinfo[i].w != 0.0f) {
+      zlist[atomicAdd(&cnt[4], 1ull)] = i;
+    } else if (!last) {
+      glist[atomicAdd(&cnt[0], 1ull)] = i;
+      atomicMax(&cnt[2], (unsigned long long)i);
+    } else {
+      xlist[atomicAdd(&cnt[1], 1ull)] = i;
+    }
+  }
+}
+
+// Rows without a defined residual correlation (r_i <= 1e-12 sigma1^2, an
+// inducing point on top of the point): |rho_ij| = 0 for every j, so the
+// neighbours are the min(i, m) smallest indices and the cut-off is a tie
+// whenever i > m.  One thread per row.
+__global__ void zero_corr_rows_kernel(KnnArgsV A, const int32_t* rows, const unsigned long long* count) {
+  const int64_t nz = (int64_t)*count;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nz; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = rows[q];
+    const int c = i < (int64_t)A.m ? (int)i : A.m;
+    for (int p = 0; p < A.m; ++p) A.nn[i * A.m + p] = p < c ? p : -1;
+    A.nn_cnt[i] = c;
+    if (i > (int64_t)A.m && A.m > 0) {
+      const unsigned long long slot = atomicAdd(&A.hdr->n_tie, 1ull);
+      if (A.tie_rows && (int64_t)slot < A.tie_cap) A.tie_rows[slot] = i;
+    }
+  }
+}
+
+// BF16 U rows of the listed rows [nrows][k64] (zero padded); candidate
+// counts of those rows reset
+__global__ void gather_bf16_kernel(const double* U, const int32_t* rows, int64_t nrows, int k, int k64,
+                                   __nv_bfloat16* Ug, int32_t* ccount) {
+  const int64_t total = nrows * (int64_t)k64;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t e = q / k64;
+    const int c = (int)(q - e * k64);
+    const int64_t i = rows[e];
+    Ug[q] = c < k ? __double2bfloat16(U[i * k + c]) : __float2bfloat16(0.0f);
+    if (c == 0) ccount[i] = 0;
+  }
 }
 
 // 1 if every time is an integer day with |t| < 2^24 (exact in FP32)
@@ -564,7 +685,9 @@ __global__ void __launch_bounds__(WARPS * 32) rerank_kernel(KnnArgsV A) {
   const int64_t total = (int64_t)gridDim.x * WARPS;
   const int K = A.m + 1;
   const double NEG = -1.0e300;
-  for (int64_t i = warp; i < A.n; i += total) {
+  const int64_t nrows = A.rlist ? A.rlist_n : A.n;
+  for (int64_t q = warp; q < nrows; q += total) {
+    const int64_t i = A.rlist ? (int64_t)A.rlist[q] : q;
     const float4 info = A.rowinfo[i];
     if (info.w != 0.0f) continue;  // listed in stage 1
     const int nc_all = A.ccount[i];
@@ -714,78 +837,187 @@ void launch_rows_per_warp(K kern, const KnnArgsV& A, cudaStream_t st, size_t byt
   kern<<<std::max(1, per) * sms, W * 32, smem, st>>>(A);
 }
 
-// stage 2 on the tensor cores (rfilter_tc_kernel) with its inputs: U in BF16
-// after the FP32 copy in the operand region, per-tile time ranges, the item
-// counts per group and the times flag in the (idle) residual-Gram region
-template <int NU>
-vst_status tc_filter(const KnnArgsV& A, char* vb, const VifLayout& V, const LagF* lagf, cudaStream_t st) {
-  const int64_t n = A.n;
-  const int k = A.k, k64 = (k + 63) / 64 * 64;
-  __nv_bfloat16* Ub = reinterpret_cast<__nv_bfloat16*>(vb + V.Ap + align256(sizeof(float) * (size_t)n * k));
-  const int T = (int)((n + kRfBM - 1) / kRfBM), T2 = (int)((n + kRfBN - 1) / kRfBN);
-  const int ngroups = (T + kRfGroup - 1) / kRfGroup;
-  char* sc = vb + V.gram;
-  int64_t* gcum = reinterpret_cast<int64_t*>(sc);
-  double2* tb128 = reinterpret_cast<double2*>(sc + align256(sizeof(int64_t) * (ngroups + 1)));
-  double2* tb256 = tb128 + T;
-  int* texact = reinterpret_cast<int*>(tb256 + T2);
+// Scratch of stage 2 (its own workspace region, knn_scratch_bytes): item
+// counts per group, per-tile time ranges, the times flag, the two row lists
+// of the second round and their counters.
+struct RfScratch {
+  int64_t* gcum;
+  double2 *tb128, *tb256, *tbg;
+  int* texact;
+  int32_t *glist, *xlist, *plist, *zlist;
+  // [0] gathered rows, [1] exhaustive rows, [2] largest gathered row,
+  // [3] rows of plist, [4] rows without a defined residual correlation
+  unsigned long long* cnt;
+  int T, T2, ngroups;
+};
+static RfScratch rf_scratch(char* vb, const VifLayout& V, int64_t n) {
+  RfScratch S{};
+  S.T = (int)((n + kRfBM - 1) / kRfBM);
+  S.T2 = (int)((n + kRfBN - 1) / kRfBN);
+  S.ngroups = (S.T + kRfGroup - 1) / kRfGroup;
+  size_t off = V.kscr;
+  auto take = [&](size_t bytes) {
+    char* p = vb + off;
+    off += align256(bytes);
+    return p;
+  };
+  S.gcum = reinterpret_cast<int64_t*>(take(sizeof(int64_t) * (S.ngroups + 1)));
+  S.tb128 = reinterpret_cast<double2*>(take(sizeof(double2) * S.T));
+  S.tb256 = reinterpret_cast<double2*>(take(sizeof(double2) * S.T2));
+  S.tbg = reinterpret_cast<double2*>(take(sizeof(double2) * (std::min<int64_t>(n, kVifGather) / kRfBM + 1)));
+  S.texact = reinterpret_cast<int*>(take(sizeof(int)));
+  S.cnt = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * 8));
+  S.glist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n));
+  S.xlist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n));
+  S.plist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n));
+  S.zlist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n));
+  return S;
+}
+
+static int sm_count() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  cudaError_t e = cudaMemsetAsync(texact, 0xff, sizeof(int), st);
-  if (e != cudaSuccess) return cuda_fail(e, "memset");
-  times_exact_kernel<<<sms * 4, 256, 0, st>>>(A.t, n, texact);
-  tile_times_kernel<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(A.t, n, kRfBM, T, tb128);
-  tile_times_kernel<<<(unsigned)((T2 * 32 + 255) / 256), 256, 0, st>>>(A.t, n, kRfBN, T2, tb256);
-  rf_groups_kernel<<<1, 1, 0, st>>>(T, ngroups, gcum);
-  u_bf16_kernel<<<sms * 8, 256, 0, st>>>(A.U, n, k, k64, Ub);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "filter set-up kernels");
+  return sms > 0 ? sms : 1;
+}
+
+template <int NU>
+vst_status rf_launch(const KnnArgsV& A, const RfArgs& R, const void* Aop, int64_t arows, const void* Bop, int k64,
+                     cudaStream_t st) {
   CUtensorMap ta, tb;
-  if (!tc_make_map_bf16(&ta, Ub, (uint64_t)n, (uint64_t)k64, kRfBM) ||
-      !tc_make_map_bf16(&tb, Ub, (uint64_t)n, (uint64_t)k64, kRfBN))
+  if (!tc_make_map_bf16(&ta, Aop, (uint64_t)arows, (uint64_t)k64, kRfBM) ||
+      !tc_make_map_bf16(&tb, Bop, (uint64_t)A.n, (uint64_t)k64, kRfBN))
     return fail(VST_ECUDA, "residual filter: tensor map encoding failed");
-  RfArgs R{};
-  R.n = n;
-  R.k = k;
-  R.kb = k64 / kRfBK;
-  R.T = T;
-  R.ngroups = ngroups;
-  R.gcum = gcum;
-  R.tb128 = tb128;
-  R.tb256 = tb256;
-  R.times_exact = texact;
-  R.lagf = lagf;
-  // BF16 rounding of both factors plus the FP32 accumulation, 5% margin
-  R.epsd = (float)(1.05 * (std::ldexp(1.0, -8) + std::ldexp(1.0, -18) + (double)k64 * std::ldexp(1.0, -22)));
   auto kern = rfilter_tc_kernel<NU>;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, RfShape::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, RfShape::SMEM);
   if (e != cudaSuccess) return cuda_fail(e, "residual filter attributes");
-  kern<<<sms, kRfThreads, RfShape::SMEM, st>>>(ta, tb, A, R);
+  kern<<<sm_count(), kRfThreads, RfShape::SMEM, st>>>(ta, tb, A, R);
   e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "residual filter kernel");
 }
 
+// stage 2 on the tensor cores over the lower triangle (rfilter_tc_kernel),
+// with its inputs: U in BF16 after the FP32 copy in the operand region,
+// per-tile time ranges and item counts in the scratch
 template <int NU>
-vst_status knn_stages(const KnnArgsV& A, char* vb, const VifLayout& V, const LagF* lagf, cudaStream_t st) {
+vst_status tc_filter(const KnnArgsV& A, char* vb, const VifLayout& V, const LagF* lagf, const RfScratch& S,
+                     RfArgs& R, __nv_bfloat16*& Ub, cudaStream_t st) {
+  const int64_t n = A.n;
+  const int k = A.k, k64 = (k + 63) / 64 * 64;
+  Ub = reinterpret_cast<__nv_bfloat16*>(vb + V.Ap + align256(sizeof(float) * (size_t)n * k));
+  const int sms = sm_count();
+  cudaError_t e = cudaMemsetAsync(S.texact, 0xff, sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  times_exact_kernel<<<sms * 4, 256, 0, st>>>(A.t, n, S.texact);
+  tile_times_kernel<<<(unsigned)((S.T * 32 + 255) / 256), 256, 0, st>>>(A.t, n, kRfBM, S.T, S.tb128);
+  tile_times_kernel<<<(unsigned)((S.T2 * 32 + 255) / 256), 256, 0, st>>>(A.t, n, kRfBN, S.T2, S.tb256);
+  rf_groups_kernel<<<1, 1, 0, st>>>(S.T, S.ngroups, S.gcum);
+  u_bf16_kernel<<<sms * 8, 256, 0, st>>>(A.U, n, k, k64, Ub);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "filter set-up kernels");
+  R = RfArgs{};
+  R.n = n;
+  R.k = k;
+  R.kb = k64 / kRfBK;
+  R.T = S.T;
+  R.ngroups = S.ngroups;
+  R.gcum = S.gcum;
+  R.tb128 = S.tb128;
+  R.tb256 = S.tb256;
+  R.times_exact = S.texact;
+  R.lagf = lagf;
+  // BF16 rounding of both factors plus the FP32 accumulation, 5% margin
+  R.epsd = (float)(1.05 * (std::ldexp(1.0, -8) + std::ldexp(1.0, -18) + (double)k64 * std::ldexp(1.0, -22)));
+  return rf_launch<NU>(A, R, Ub, n, Ub, k64, st);
+}
+
+template <int NU>
+vst_status knn_stages(KnnArgsV A, char* vb, const VifLayout& V, const LagF* lagf, cudaStream_t st) {
   constexpr int W = 4;
+  const int64_t n = A.n;
+  const int k64 = (A.k + 63) / 64 * 64;
   launch_rows_per_warp(tau_kernel<NU, W>, A, st);
-  if (A.n > 1) {
-    const vst_status s = tc_filter<NU>(A, vb, V, lagf, st);
-    if (s != VST_OK) return s;
-  }
+  if (n <= 1) return VST_OK;
+  const RfScratch S = rf_scratch(vb, V, n);
+  RfArgs R;
+  __nv_bfloat16* Ub = nullptr;
+  vst_status s = tc_filter<NU>(A, vb, V, lagf, S, R, Ub, st);
+  if (s != VST_OK) return s;
   launch_rows_per_warp(rerank_kernel<NU, W>, A, st);
+  // later rounds: rows whose candidates overflowed, with the tighter
+  // threshold rerank gave them (the m-th best of their stored candidates),
+  // screened again on the tensor cores against all predecessors, in batches
+  // of gathered rows; a round's overflow feeds the next (each raises the
+  // threshold to the m-th best of kVifCand candidates above the last one).
+  // Rows without a defined residual correlation take the first predecessors
+  // (every |rho| is 0); those still overflowing after the last round go to
+  // the exhaustive pass.
+  constexpr int kRounds = 4;
+  KnnArgsV A2 = A;
+  __nv_bfloat16* Ug = reinterpret_cast<__nv_bfloat16*>(vb + V.gath);
+  const int sms = sm_count();
+  int32_t* fb_in = A.fbrows;
+  unsigned long long* fbc_in = A.fbcount;
+  cudaError_t e = cudaMemsetAsync(S.cnt, 0, sizeof(unsigned long long) * 8, st);
+  if (e != cudaSuccess) return cuda_fail(e, "memset");
+  for (int round = 0; round <= kRounds; ++round) {
+    const int last = round == kRounds;
+    e = cudaMemsetAsync(S.cnt, 0, sizeof(unsigned long long), st);                // gathered rows
+    if (e == cudaSuccess) e = cudaMemsetAsync(S.cnt + 2, 0, sizeof(unsigned long long), st);  // largest row
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    fb_split_kernel<<<1, 1024, 0, st>>>(fb_in, fbc_in, A.rowinfo, last, S.glist, S.xlist, S.zlist, S.cnt);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    e = cudaMemcpyAsync(h, S.cnt, sizeof(h), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "second-round counts");
+    const int64_t ng = (int64_t)h[0];
+    if (ng == 0) break;
+    // this round's overflow goes to the other list
+    int32_t* fb_out = fb_in == A.fbrows ? S.plist : A.fbrows;
+    unsigned long long* fbc_out = fb_in == A.fbrows ? S.cnt + 3 : A.fbcount;
+    e = cudaMemsetAsync(fbc_out, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return cuda_fail(e, "memset");
+    A2.fbrows = fb_out;
+    A2.fbcount = fbc_out;
+    for (int64_t b0 = 0; b0 < ng; b0 += kVifGather) {
+      const int64_t nb = std::min<int64_t>(kVifGather, ng - b0);
+      const int32_t* rows = S.glist + b0;
+      gather_bf16_kernel<<<sms * 8, 256, 0, st>>>(A.U, rows, nb, A.k, k64, Ug, A.ccount);
+      const int nt = (int)((nb + kRfBM - 1) / kRfBM);
+      tile_times_list_kernel<<<(unsigned)((nt * 32 + 255) / 256), 256, 0, st>>>(A.t, rows, nb, nt, S.tbg);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return cuda_fail(e, "second-round set-up");
+      RfArgs R2 = R;
+      R2.rows = rows;
+      R2.nrows = nb;
+      R2.nt = nt;
+      R2.nj = (int)(((int64_t)h[2] + kRfBN - 1) / kRfBN);  // columns j < the largest listed row
+      R2.tbg = S.tbg;
+      if (R2.nj > 0) {
+        s = rf_launch<NU>(A, R2, Ug, nb, Ub, k64, st);
+        if (s != VST_OK) return s;
+      }
+      A2.rlist = rows;
+      A2.rlist_n = nb;
+      launch_rows_per_warp(rerank_kernel<NU, W>, A2, st);
+    }
+    fb_in = fb_out;
+    fbc_in = fbc_out;
+  }
+  zero_corr_rows_kernel<<<sms, 256, 0, st>>>(A, S.zlist, S.cnt + 4);
+  A2.fbrows = S.xlist;
+  A2.fbcount = S.cnt + 1;
   {
+    A2.rlist = nullptr;
+    A2.rlist_n = 0;
     const size_t smem = (sizeof(double) + sizeof(float)) * A.k;
-    int dev = 0, sms2 = 0, per2 = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms2, cudaDevAttrMultiProcessorCount, dev);
+    int per2 = 0;
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(pass2_kernel<NU>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per2, pass2_kernel<NU>, kPass2Warps * 32, smem);
-    pass2_kernel<NU><<<std::max(1, per2) * sms2, kPass2Warps * 32, smem, st>>>(A);
+    pass2_kernel<NU><<<std::max(1, per2) * sms, kPass2Warps * 32, smem, st>>>(A2);
   }
-  const cudaError_t e = cudaGetLastError();
+  e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "VIF neighbour kernels");
 }
 

@@ -3,6 +3,7 @@
 // the entry points agree.
 #pragma once
 
+#include <algorithm>
 #include <cstddef>
 #include <cstdint>
 
@@ -31,6 +32,8 @@ struct VifLayout {
   // residual-correlation neighbour search: per-row threshold, candidate
   // lists and counts, rows left to the brute-force search and their count
   size_t tau, cand, ccount, fbrows, fbcount;
+  size_t gath;  // BF16 U rows of the rows re-screened after a candidate overflow
+  size_t kscr;  // knn_scratch_bytes
   size_t total;
 };
 
@@ -38,6 +41,21 @@ struct VifLayout {
 inline int64_t vif_kp(int64_t k) { return (k + 255) / 256 * 256; }
 constexpr int kVifMaxParts = 3;  // BF16 parts per operand value
 constexpr int kVifCand = 2048;   // candidate slots per row of the filtered neighbour search
+constexpr int64_t kVifGather = 8192;  // rows per batch of the search's second (gathered) round
+// tensor-core candidate filter of the residual search: row and column tile
+// sizes, row tiles per group
+constexpr int kKnnTileRows = 128, kKnnTileCols = 256, kKnnGroup = 16;
+
+// scratch of that filter: item counts per group, per-tile time ranges, the
+// times flag, counters and the row lists of its later rounds
+inline size_t knn_scratch_bytes(int64_t n) {
+  auto a = [](size_t v) { return (v + 255) & ~size_t(255); };
+  const size_t nn = n > 0 ? (size_t)n : 1;
+  const size_t T = (nn + kKnnTileRows - 1) / kKnnTileRows, T2 = (nn + kKnnTileCols - 1) / kKnnTileCols;
+  const size_t ng = (T + kKnnGroup - 1) / kKnnGroup;
+  const size_t tg = (size_t)std::min<int64_t>((int64_t)nn, kVifGather) / kKnnTileRows + 1;
+  return a(8 * (ng + 1)) + a(16 * T) + a(16 * T2) + a(16 * tg) + a(4) + a(64) + 4 * a(4 * nn);
+}
 
 inline size_t align256(size_t v);
 
@@ -80,6 +98,8 @@ inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
   L.ccount = take(sizeof(int32_t) * nn);
   L.fbrows = take(sizeof(int32_t) * nn);
   L.fbcount = take(256);
+  L.gath = take(2 * (size_t)std::min<int64_t>((int64_t)nn, kVifGather) * (size_t)((kk + 63) / 64 * 64));
+  L.kscr = take(knn_scratch_bytes((int64_t)nn));
   L.total = off;
   return L;
 }
