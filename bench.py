@@ -284,10 +284,12 @@ def batched_leg(vst, torch, dev, steps):
 def vif_leg(vst, torch, dev, w, nv=30000, full=True):
     """VIF (Sect. 4.3).  (a) the first 30,000 rows of the bench workload with
     k = 1000 inducing points (seeded space-time kMeans++ with Lloyd steps on
-    coordinates scaled by the ranges): exact residual-correlation neighbour
-    search (FP64, all predecessors) and the Woodbury NLL in both forms;
+    coordinates scaled by the ranges): the exact residual-correlation
+    neighbour search and the Woodbury NLL and gradient in both forms;
     (b) the full 1.108M rows with k = 1000 (inducing points from a 50,000-row
-    subsample, plain correlation neighbours): the mixed-form NLL."""
+    subsample): the exact residual-correlation neighbour search, the NLL in
+    both mixed forms (and FP64 once, for the error per point) and the mixed
+    NLL + gradient with those neighbours."""
     import synthetic_inputs as si
     th = vst.vst_theta_from_ranges(*w.theta.astuple())
     out = {}
@@ -356,11 +358,10 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
     del wsg, nn, cnt
     if not full:
         return out
-    # full size, mixed
+    # full size: the exact residual-correlation neighbour search, then the
+    # NLL (mixed, and FP64 once for the accuracy record) and NLL + gradient
+    # with those neighbours
     xy, t, y = (torch.from_numpy(a).to(dev) for a in (w.xy, w.t, w.z))
-    ws0 = vst.Workspace(w.n, w.m, device=dev)
-    nn, cnt = vst.vif_build_neighbors(xy, t, th, w.m, ws=ws0)
-    del ws0
     r = np.random.default_rng(5).choice(w.n, 50000, replace=False)
     r.sort()
     sub = type(w)(name="sub", xy=w.xy[r], t=w.t[r], z=w.z[r], theta=w.theta, m=w.m, order=None)
@@ -368,6 +369,31 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
     ind = (torch.from_numpy(xyk).to(dev), torch.from_numpy(tk).to(dev))
     ws = vst.Workspace(w.n, w.m, k, device=dev, vif_grad=True)
     full = {"n": w.n, "k": k, "m": w.m}
+    nn = torch.empty((w.n, w.m), dtype=torch.int32, device=dev)
+    cnt = torch.empty(w.n, dtype=torch.int32, device=dev)
+    vst.vif_build_neighbors(xy, t, th, w.m, nn=nn, nn_cnt=cnt, ws=ws, inducing=ind)
+    torch.cuda.synchronize()
+    vst.vst_profile_enable(1)
+    t0 = time.perf_counter()
+    vst.vif_build_neighbors(xy, t, th, w.m, nn=nn, nn_cnt=cnt, ws=ws, inducing=ind)
+    kinfo = vst.vst_workspace_status(ws)
+    knn_ms = (time.perf_counter() - t0) * 1e3  # the call synchronises; wall time
+    fl, fms = vst.vst_profile_read(vst.PROF_VIF_FILTER)
+    vst.vst_profile_enable(0)
+    # the filter's algorithmic work: the lower triangle of U U^T, 2 k flops per
+    # pair j < i (the triangle pass; later rounds re-screen overflowing rows)
+    ffl = float(w.n) * (w.n - 1) / 2 * 2 * k
+    full["residual_knn"] = {"ms": knn_ms, "value": w.n / (knn_ms * 1e-3), "unit": "queries/s",
+                            "filter_ms": fms, "filter_launches": fl,
+                            "filter_roofline": {"bound": "tensor", "achieved": ffl / (fms * 1e-3) / 1e12,
+                                                "peak": BF16_PEAK, "unit": "TFLOP/s",
+                                                "frac": ffl / (fms * 1e-3) / 1e12 / BF16_PEAK,
+                                                "flops": ffl, "peak_note": "measured cuBLAS bf16 (burst)"},
+                            "exhaustive_rows": kinfo["n_fallback"], "tie_rows": kinfo["n_tie"],
+                            "what": "exact residual-correlation neighbours (FP64 low rank, tensor-core BF16 "
+                                    "candidate filter with a rigorous bound, FP64 re-rank)"}
+    v64 = vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=vst.FP64, ws=ws, inducing=ind).item()
+    vst.vst_workspace_status(ws)
     for name, prec, terms in (("mixed", vst.MIXED, 6), ("mixed_bf16x3", vst.MIXED_BF16X3, 3)):
         f = (lambda p=prec: vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=p, ws=ws, inducing=ind))
         tms = timed(f, 2)
@@ -386,6 +412,9 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
                                           "peak": BF16_PEAK, "unit": "TFLOP/s",
                                           "frac": flops / (gemm_ms * 1e-3) / 1e12 / BF16_PEAK,
                                           "flops_per_launch": flops, "peak_note": "measured cuBLAS bf16 (burst)"}}
+        vmix = vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=prec, ws=ws, inducing=ind).item()
+        full[name]["dnll_per_n_vs_fp64"] = abs(vmix - v64) / w.n
+    full["nll_fp64"] = v64
     # NLL + gradient, mixed (FP32 low rank and n x k products, FP64 reductions)
     fg = (lambda: vst.vecchia_nll_grad(xy, t, th, w.m, nn, cnt, y, precision=vst.MIXED, ws=ws, inducing=ind))
     full["nll_grad_mixed_ms"] = timed(fg, 2)

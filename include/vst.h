@@ -376,7 +376,8 @@ vst_status vecchia_sample_ex(const vst_points* pts, const vst_theta* theta, int 
  * its main kernels, by class: 0 = fused row kernel (NLL / gradient / factor),
  * 1 = FP64 fallback row kernel of the mixed form, 2 = neighbour query kernel,
  * 3 = Vecchia sampling kernel, 4 = VIF low-rank GEMM U = Sigma_nk L^{-T},
- * 5 = VIF per-row residual Gram, 6 = VIF [W e]^T [W e] product.
+ * 5 = VIF per-row residual Gram, 6 = VIF [W e]^T [W e] product, 7 = VIF
+ * residual-correlation candidate filter (tensor cores).
  * vst_profile_read() synchronises on the
  * recorded events and returns the number of launches of that class and their
  * summed device time (ms) since the last vst_profile_enable(1).  At most 4096

@@ -55,6 +55,57 @@ def lowrank(xy, t, xyk, tk, theta):
     return U, r
 
 
+def lowrank_rows(xy, t, xyk, tk, theta, chunk=32768, threads=None):
+    """The same U and r as lowrank() for large n: the rows of Sigma_nk are
+    formed and solved in independent chunks of points (rows of U do not
+    depend on one another), the chunks' covariance matrices in parallel
+    threads (the C++ covariance releases the interpreter)."""
+    from concurrent.futures import ThreadPoolExecutor
+    from . import default_threads
+    n, k = t.shape[0], tk.shape[0]
+    Skk = cov_matrix(xyk, tk, xyk, tk, theta)
+    L = np.linalg.cholesky(Skk)
+    U = np.empty((n, k))
+    starts = list(range(0, n, chunk))
+
+    def one(s):
+        e = min(n, s + chunk)
+        Snk = cov_matrix(xy[s:e], t[s:e], xyk, tk, theta)
+        U[s:e] = sla.solve_triangular(L, Snk.T, lower=True).T
+
+    with ThreadPoolExecutor(threads or default_threads()) as ex:
+        list(ex.map(one, starts))
+    r = theta[0] - (U * U).sum(1)
+    return U, r
+
+
+def knn_rows(xy, t, theta, U, r, m, rows):
+    """knn() for the listed rows only (brute force over all their
+    predecessors): (nn [len(rows), m], cnt, rho_m, rho_m1)."""
+    rows = np.asarray(rows, dtype=np.int64)
+    nn = np.full((rows.shape[0], m), -1, dtype=np.int32)
+    cnt = np.zeros(rows.shape[0], dtype=np.int32)
+    rm = np.full(rows.shape[0], np.nan)
+    rm1 = np.full(rows.shape[0], np.nan)
+    tiny = 1e-12 * theta[0]
+    for q, i in enumerate(rows):
+        if i == 0:
+            continue
+        j = np.arange(i)
+        R = cov_matrix(xy[i:i + 1], t[i:i + 1], xy[:i], t[:i], theta)[0] - U[:i] @ U[i]
+        ok = (r[j] > tiny) & (r[i] > tiny)
+        rho = np.where(ok, np.abs(R) / np.sqrt(np.where(ok, r[i] * r[j], 1.0)), 0.0)
+        order = np.lexsort((j, -rho))
+        c = min(int(i), m)
+        nn[q, :c] = j[order[:c]]
+        cnt[q] = c
+        if c == m and m > 0:
+            rm[q] = rho[order[m - 1]]
+        if i > m:
+            rm1[q] = rho[order[m]]
+    return nn, cnt, rm, rm1
+
+
 def residual_block(xy, t, theta, U, rows, cols):
     """Latent residual covariance R[rows, cols] = Sigma - U U^T (no nugget)."""
     C = cov_matrix(xy[rows], t[rows], xy[cols], t[cols], theta)

@@ -616,7 +616,7 @@ def vst_workspace_status(ws, stream=None, raise_on_error=True):
 
 
 PROF_ROWS, PROF_FALLBACK, PROF_KNN, PROF_SAMPLE = 0, 1, 2, 3
-PROF_VIF_GEMM, PROF_VIF_GRAM, PROF_VIF_SYRK = 4, 5, 6
+PROF_VIF_GEMM, PROF_VIF_GRAM, PROF_VIF_SYRK, PROF_VIF_FILTER = 4, 5, 6, 7
 
 
 def vst_profile_enable(on=True):

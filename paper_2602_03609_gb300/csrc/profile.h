@@ -13,7 +13,8 @@ enum ProfileClass {
   kProfVifGemm = 4,  // VIF low-rank U GEMM (tensor-core or FP64)
   kProfVifGram = 5,  // VIF per-row residual Gram
   kProfVifSyrk = 6,  // VIF [W e]^T [W e]
-  kProfClasses = 7
+  kProfVifFilter = 7,  // VIF residual-correlation candidate filter (tensor cores)
+  kProfClasses = 8
 };
 
 class ProfileScope {

@@ -221,6 +221,7 @@ __device__ __forceinline__ float cov32_err(const DevTheta& th, float dx, float d
 constexpr int kRfBM = kKnnTileRows, kRfBN = kKnnTileCols, kRfBK = 64, kRfStages = 4, kRfGroup = kKnnGroup;
 constexpr int kRfThreads = 320;
 constexpr uint64_t kRfWaitNs = 2000000000ull;  // 2 s per wait
+constexpr int kRfBins = 256;                    // |rho| histogram of the later rounds
 struct RfShape {
   static constexpr int A_BYTES = kRfBM * kRfBK * 2;
   static constexpr int B_BYTES = kRfBN * kRfBK * 2;
@@ -249,6 +250,8 @@ struct RfArgs {
   const int32_t* rows;
   int64_t nrows;
   int nt, nj;
+  int* hist;  // [nrows][kRfBins] counts of the approximate |rho| of each row's candidates
+  int* dmax;  // [nrows] largest approximation error (float bits)
   const double2* tbg;   // per gathered row tile: (t_min, t_max)
 };
 
@@ -293,22 +296,36 @@ __device__ __forceinline__ void rf_item(const RfArgs& R, int64_t w, int& I, int&
 // serves the 32 columns of a chunk.
 template <int NU>
 __device__ __noinline__ void rf_exact(CovF cf, float dot, float4 cm, float nuj, float xi, float yi, float ti,
-                                      float offi, float thr, float eu, int texact, int64_t i, int j, int32_t* ccount,
-                                      int32_t* cand) {
+                                      float offi, float thr, float si, float eu, int texact, int64_t i, int j,
+                                      int32_t* ccount, int32_t* cand, int* hist, int* dmax) {
   const float rhs = thr * cm.w;
   const float db = eu * nuj;
   bool keep = !texact;
+  float Rv = 0.f, bound = 0.f;
   if (!keep) {
     float rel;
     const float C = cov32_err<NU>(cf, xi - cm.x, yi - cm.y, ti - cm.z, rel);
-    const float Rv = fabsf(C - dot);
+    Rv = fabsf(C - dot);
     const float offs = offi + fabsf(cm.x) + fabsf(cm.y);
-    const float bound = 1.1f * fabsf(C) * (rel * kU + cf.c * 2.0f * kU * offs) + db + 1.0e-33f * cf.s1;
+    bound = 1.1f * fabsf(C) * (rel * kU + cf.c * 2.0f * kU * offs) + db + 1.0e-33f * cf.s1;
     keep = Rv + 1.5f * bound + 4.0f * kU * (Rv + fabsf(rhs)) >= rhs;
   }
   if (keep) {
     const int slot = atomicAdd(&ccount[i], 1);
     if (slot < kVifCand) cand[i * kVifCand + slot] = (int32_t)j;
+    if (hist && texact) {
+      // later rounds: the approximate |rho| of the candidate in one of
+      // kRfBins bins over [0, 1], and the largest error of such an
+      // approximation for the row (|rho - rho^| <= (1.5 bound + rounding) / (s_i s_j))
+      const float ss = si * cm.w;
+      if (ss > 0.f) {
+        const float rh = Rv / ss;
+        const float dl = (1.5f * bound + 8.0f * kU * (Rv + rhs)) / ss * 1.01f;
+        const int bin = min(kRfBins - 1, max(0, (int)(rh * (float)kRfBins)));
+        atomicAdd(&hist[bin], 1);
+        atomicMax(dmax, __float_as_int(dl));
+      }
+    }
   }
 }
 
@@ -474,6 +491,8 @@ __global__ void __launch_bounds__(kRfThreads, 1)
       const float offi = fabsf(xi) + fabsf(yi);
       const float eu = R.epsd * ri.z;
       const int climit = (int)(i - j0);  // columns c < climit have j < i
+      int* hrow = (R.rows && gi < R.nrows) ? R.hist + gi * kRfBins : nullptr;
+      int* drow = hrow ? R.dmax + gi : nullptr;
       // the eight warps pass the same barriers: a warp whose wait ran out
       // says so here, and all of them stop together after the barrier
       if (!ok && lane == 0) *epi_fail = 1u;
@@ -513,7 +532,7 @@ __global__ void __launch_bounds__(kRfThreads, 1)
           for (int q = 0; q < 32; ++q)
             if (mask & (1u << q))
               rf_exact<NU>(cf, __uint_as_float(v[q]), colX[b * kRfBN + cb0 + q], colS[b * kRfBN + cb0 + q].y, xi, yi,
-                           tiv, offi, ri.x, eu, texact, i, (int)j0 + cb0 + q, A.ccount, A.cand);
+                           tiv, offi, ri.x, ri.y, eu, texact, i, (int)j0 + cb0 + q, A.ccount, A.cand, hrow, drow);
         }
       }
     }
@@ -606,6 +625,53 @@ __global__ void zero_corr_rows_kernel(KnnArgsV A, const int32_t* rows, const uns
     if (i > (int64_t)A.m && A.m > 0) {
       const unsigned long long slot = atomicAdd(&A.hdr->n_tie, 1ull);
       if (A.tie_rows && (int64_t)slot < A.tie_cap) A.tie_rows[slot] = i;
+    }
+  }
+}
+
+// Rows of a gathered round whose candidates overflowed their slots: the
+// histogram of the approximate |rho| gives a threshold that m of them reach
+// (the lower edge of the bin holding the m-th largest, less the largest
+// approximation error), raised into the row's record if it is the larger.
+// One warp per row.
+__global__ void hist_threshold_kernel(const int32_t* rows, int64_t nrows, const int* hist, const int* dmax,
+                                      const int32_t* ccount, int m, float4* rowinfo) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (w >= nrows) return;
+  const int64_t i = rows[w];
+  if (ccount[i] <= kVifCand || m <= 0) return;
+  // bins 8 lane .. 8 lane + 7; the candidates in the bins of higher lanes
+  int c[8], tot = 0;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    c[u] = hist[w * kRfBins + lane * 8 + u];
+    tot += c[u];
+  }
+  int incl = tot;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_down_sync(kFull, incl, o);
+    if (lane + o < 32) incl += v;
+  }
+  const int above = incl - tot;
+  int bin = -1;
+  int acc = above;
+#pragma unroll
+  for (int u = 7; u >= 0; --u) {
+    acc += c[u];
+    if (bin < 0 && acc >= m) bin = lane * 8 + u;
+  }
+  // the highest bin over the lanes where the count reaches m
+  int best = bin;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = max(best, __shfl_xor_sync(kFull, best, o));
+  if (lane == 0 && best >= 0) {
+    const float4 info = rowinfo[i];
+    const float lo = (float)best / (float)kRfBins - __int_as_float(dmax[w]);
+    if (lo > 0.f) {
+      const float thr = __double2float_rd((double)lo * (1.0 - 2e-12) * (double)info.y * (1.0 - 1e-6));
+      if (thr > info.x) rowinfo[i] = make_float4(thr, info.y, info.z, info.w);
     }
   }
 }
@@ -720,7 +786,8 @@ __global__ void __launch_bounds__(WARPS * 32) rerank_kernel(KnnArgsV A) {
     } else {
       const double tm = __shfl_sync(kFull, lr, A.m - 1);  // m-th best of the stored candidates
       if (lane == 0) {
-        A.rowinfo[i] = make_float4(__double2float_rd(tm * (1.0 - 2e-12) * (double)info.y), info.y, info.z, 0.0f);
+        const float thr = __double2float_rd(tm * (1.0 - 2e-12) * (double)info.y);
+        A.rowinfo[i] = make_float4(fmaxf(thr, A.rowinfo[i].x), info.y, info.z, 0.0f);
         A.fbrows[atomicAdd(A.fbcount, 1ull)] = (int32_t)i;
       }
     }
@@ -845,6 +912,7 @@ struct RfScratch {
   double2 *tb128, *tb256, *tbg;
   int* texact;
   int32_t *glist, *xlist, *plist, *zlist;
+  int *hist, *dmax;  // per gathered row: |rho| histogram and largest error
   // [0] gathered rows, [1] exhaustive rows, [2] largest gathered row,
   // [3] rows of plist, [4] rows without a defined residual correlation
   unsigned long long* cnt;
@@ -871,6 +939,8 @@ static RfScratch rf_scratch(char* vb, const VifLayout& V, int64_t n) {
   S.xlist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n));
   S.plist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n));
   S.zlist = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * n));
+  S.hist = reinterpret_cast<int*>(take(sizeof(int) * std::min<int64_t>(n, kVifGather) * kRfBins));
+  S.dmax = reinterpret_cast<int*>(take(sizeof(int) * std::min<int64_t>(n, kVifGather)));
   return S;
 }
 
@@ -891,6 +961,7 @@ vst_status rf_launch(const KnnArgsV& A, const RfArgs& R, const void* Aop, int64_
   auto kern = rfilter_tc_kernel<NU>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, RfShape::SMEM);
   if (e != cudaSuccess) return cuda_fail(e, "residual filter attributes");
+  ProfileScope ps(kProfVifFilter, st);
   kern<<<sm_count(), kRfThreads, RfShape::SMEM, st>>>(ta, tb, A, R);
   e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "residual filter kernel");
@@ -947,12 +1018,13 @@ vst_status knn_stages(KnnArgsV A, char* vb, const VifLayout& V, const LagF* lagf
   // later rounds: rows whose candidates overflowed, with the tighter
   // threshold rerank gave them (the m-th best of their stored candidates),
   // screened again on the tensor cores against all predecessors, in batches
-  // of gathered rows; a round's overflow feeds the next (each raises the
-  // threshold to the m-th best of kVifCand candidates above the last one).
+  // of gathered rows; a round's overflow feeds the next, whose threshold is
+  // the larger of the m-th best stored candidate and the bound from the
+  // round's histogram of approximate |rho| (hist_threshold_kernel).
   // Rows without a defined residual correlation take the first predecessors
   // (every |rho| is 0); those still overflowing after the last round go to
   // the exhaustive pass.
-  constexpr int kRounds = 4;
+  constexpr int kRounds = 8;
   KnnArgsV A2 = A;
   __nv_bfloat16* Ug = reinterpret_cast<__nv_bfloat16*>(vb + V.gath);
   const int sms = sm_count();
@@ -983,6 +1055,9 @@ vst_status knn_stages(KnnArgsV A, char* vb, const VifLayout& V, const LagF* lagf
       const int64_t nb = std::min<int64_t>(kVifGather, ng - b0);
       const int32_t* rows = S.glist + b0;
       gather_bf16_kernel<<<sms * 8, 256, 0, st>>>(A.U, rows, nb, A.k, k64, Ug, A.ccount);
+      e = cudaMemsetAsync(S.hist, 0, sizeof(int) * nb * kRfBins, st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(S.dmax, 0, sizeof(int) * nb, st);
+      if (e != cudaSuccess) return cuda_fail(e, "memset");
       const int nt = (int)((nb + kRfBM - 1) / kRfBM);
       tile_times_list_kernel<<<(unsigned)((nt * 32 + 255) / 256), 256, 0, st>>>(A.t, rows, nb, nt, S.tbg);
       e = cudaGetLastError();
@@ -993,10 +1068,14 @@ vst_status knn_stages(KnnArgsV A, char* vb, const VifLayout& V, const LagF* lagf
       R2.nt = nt;
       R2.nj = (int)(((int64_t)h[2] + kRfBN - 1) / kRfBN);  // columns j < the largest listed row
       R2.tbg = S.tbg;
+      R2.hist = S.hist;
+      R2.dmax = S.dmax;
       if (R2.nj > 0) {
         s = rf_launch<NU>(A, R2, Ug, nb, Ub, k64, st);
         if (s != VST_OK) return s;
       }
+      hist_threshold_kernel<<<(unsigned)((nb * 32 + 255) / 256), 256, 0, st>>>(rows, nb, S.hist, S.dmax, A.ccount,
+                                                                               A.m, A.rowinfo);
       A2.rlist = rows;
       A2.rlist_n = nb;
       launch_rows_per_warp(rerank_kernel<NU, W>, A2, st);

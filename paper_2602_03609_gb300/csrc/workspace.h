@@ -47,14 +47,17 @@ constexpr int64_t kVifGather = 8192;  // rows per batch of the search's second (
 constexpr int kKnnTileRows = 128, kKnnTileCols = 256, kKnnGroup = 16;
 
 // scratch of that filter: item counts per group, per-tile time ranges, the
-// times flag, counters and the row lists of its later rounds
+// times flag, counters, the row lists of its later rounds and their |rho|
+// histograms (256 bins)
 inline size_t knn_scratch_bytes(int64_t n) {
   auto a = [](size_t v) { return (v + 255) & ~size_t(255); };
   const size_t nn = n > 0 ? (size_t)n : 1;
   const size_t T = (nn + kKnnTileRows - 1) / kKnnTileRows, T2 = (nn + kKnnTileCols - 1) / kKnnTileCols;
   const size_t ng = (T + kKnnGroup - 1) / kKnnGroup;
   const size_t tg = (size_t)std::min<int64_t>((int64_t)nn, kVifGather) / kKnnTileRows + 1;
-  return a(8 * (ng + 1)) + a(16 * T) + a(16 * T2) + a(16 * tg) + a(4) + a(64) + 4 * a(4 * nn);
+  const size_t ng2 = (size_t)std::min<int64_t>((int64_t)nn, kVifGather);
+  return a(8 * (ng + 1)) + a(16 * T) + a(16 * T2) + a(16 * tg) + a(4) + a(64) + 4 * a(4 * nn) + a(4 * ng2 * 256) +
+         a(4 * ng2);
 }
 
 inline size_t align256(size_t v);

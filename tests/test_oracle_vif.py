@@ -158,3 +158,24 @@ def test_gradient_variance_scaling_identity():
     S0 = vif.dense_sigma(xy, t, th, U, 0, nn0, cnt0)
     assert th[0] * g0[0] + th[4] * g0[4] == pytest.approx(0.5 * n - 0.5 * y @ np.linalg.solve(S0, y), rel=1e-9,
                                                           abs=1e-9 * n)
+
+
+def test_lowrank_rows_and_knn_rows_match_the_whole_matrix_versions():
+    # the chunked low rank and the per-row search are the same definitions
+    # evaluated piecewise: identical to lowrank() and knn() on a small case
+    rng = np.random.default_rng(3)
+    xy = rng.random((300, 2))
+    t = rng.integers(0, 6, 300).astype(float)
+    th = oracle.theta_from_ranges(1.0, 0.2, 2.0, 0.5, 0.05)
+    xyk = rng.random((12, 2))
+    tk = rng.integers(0, 6, 12).astype(float)
+    U, r = vif.lowrank(xy, t, xyk, tk, th)
+    U2, r2 = vif.lowrank_rows(xy, t, xyk, tk, th, chunk=64, threads=3)
+    np.testing.assert_allclose(U2, U, rtol=0, atol=1e-14)
+    np.testing.assert_allclose(r2, r, rtol=0, atol=1e-14)
+    nn, cnt, rm, rm1 = vif.knn(xy, t, th, U, r, 7)
+    rows = np.array([0, 1, 5, 8, 150, 299])
+    nn2, cnt2, rm2, rm12 = vif.knn_rows(xy, t, th, U, r, 7, rows)
+    assert np.array_equal(nn2, nn[rows]) and np.array_equal(cnt2, cnt[rows])
+    np.testing.assert_array_equal(rm2, rm[rows])
+    np.testing.assert_array_equal(rm12, rm1[rows])
