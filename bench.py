@@ -496,9 +496,21 @@ def cpu_baseline(w, th, seconds_hint=True):
     t0 = time.perf_counter()
     oracle.nll_grad_rows(w.xy, w.t, th, w.m, rows, nn, cnt, y, threads=threads)
     dt = time.perf_counter() - t0
+    # the neighbour search as the paper runs it (cover tree, Algorithms 1-2) on
+    # the first points of the workload: the tree over them, then every query
+    Sk = min(w.n, 10000)
+    t0 = time.perf_counter()
+    with oracle.CoverTree(w.xy[:Sk], w.t[:Sk], th) as T:
+        tb = time.perf_counter() - t0
+        T.knn(w.m, threads=threads)
+    tk = time.perf_counter() - t0
     return {"value": S / (w.n * dt), "unit": "evals/s", "cores": threads, "kind": "oracle",
             "sample": f"NLL+grad terms of the first {S} rows of the {w.n}-point workload "
-                      f"({dt:.2f} s on {threads} threads), scaled to one full evaluation"}
+                      f"({dt:.2f} s on {threads} threads), scaled to one full evaluation",
+            "neighbor_search": {"value": Sk / tk, "unit": "queries/s", "n": Sk, "build_s": tb, "total_s": tk,
+                                "sample": f"cover tree (Algorithms 1-2) over the first {Sk} points, built on one "
+                                          f"thread, then all {Sk} queries on {threads} threads; the per-query "
+                                          "cost grows with n"}}
 
 
 # ---------------------------------------------------------------------------

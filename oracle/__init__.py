@@ -49,6 +49,17 @@ def lib():
         L.orc_nll_grad_rows.restype = ctypes.c_double
         L.orc_nll_grad_rows.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int, ctypes.c_int64, _I64, _I32, _I32,
                                         _D, _D, ctypes.c_int]
+        L.orc_cover_tree_build.restype = ctypes.c_void_p
+        L.orc_cover_tree_build.argtypes = [ctypes.c_int64, _D, _D, _D]
+        L.orc_cover_tree_free.restype = None
+        L.orc_cover_tree_free.argtypes = [ctypes.c_void_p]
+        L.orc_cover_tree_depth.restype = ctypes.c_int
+        L.orc_cover_tree_depth.argtypes = [ctypes.c_void_p]
+        L.orc_cover_tree_structure.restype = None
+        L.orc_cover_tree_structure.argtypes = [ctypes.c_void_p, ctypes.c_int64, _I32, _I64]
+        L.orc_knn_cover_tree.restype = None
+        L.orc_knn_cover_tree.argtypes = [ctypes.c_void_p, ctypes.c_int64, _D, _D, _D, ctypes.c_int, ctypes.c_int64,
+                                         _I64, _I32, _I32, _D, _D, ctypes.c_int]
         L.orc_nll.restype = ctypes.c_double
         L.orc_nll.argtypes = [ctypes.c_int64, _D, _D, _D, ctypes.c_int, _I32, _I32, _D, _D, ctypes.c_int]
         L.orc_nll_grad.restype = ctypes.c_double
@@ -156,6 +167,58 @@ def knn(xy, t, theta, m, rows=None, threads=None):
                        nn.ctypes.data_as(_I32), cnt.ctypes.data_as(_I32), _d(rm), _d(rm1),
                        int(threads or default_threads()))
     return nn, cnt, rm, rm1
+
+
+class CoverTree:
+    """The cover tree of Algorithm 1 (Sect. 4.4.1) over the points in their
+    index order, under d_c = sqrt(1 - |rho|); the search of Algorithm 2 by
+    knn().  Use as a context manager or call close()."""
+
+    def __init__(self, xy, t, theta):
+        self.xy, self.t, self.th = _f64(xy), _f64(t), _f64(theta)
+        self.n = self.t.shape[0]
+        self.h = lib().orc_cover_tree_build(self.n, _d(self.xy), _d(self.t), _d(self.th))
+
+    @property
+    def depth(self) -> int:
+        return int(lib().orc_cover_tree_depth(self.h))
+
+    def structure(self):
+        """(level [n] int32, parent [n] int64, -1 for the root)."""
+        level = np.zeros(self.n, dtype=np.int32)
+        parent = np.zeros(self.n, dtype=np.int64)
+        lib().orc_cover_tree_structure(self.h, self.n, level.ctypes.data_as(_I32), parent.ctypes.data_as(_I64))
+        return level, parent
+
+    def knn(self, m, rows=None, threads=None):
+        """As knn() (same outputs, same tie order), by the cover-tree search."""
+        rows = np.arange(self.n, dtype=np.int64) if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+        R = rows.shape[0]
+        nn = np.full((R, m), -1, dtype=np.int32)
+        cnt = np.zeros(R, dtype=np.int32)
+        rm = np.zeros(R)
+        rm1 = np.zeros(R)
+        lib().orc_knn_cover_tree(self.h, self.n, _d(self.xy), _d(self.t), _d(self.th), int(m), R,
+                                 rows.ctypes.data_as(_I64), nn.ctypes.data_as(_I32), cnt.ctypes.data_as(_I32),
+                                 _d(rm), _d(rm1), int(threads or default_threads()))
+        return nn, cnt, rm, rm1
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().orc_cover_tree_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def tie_rows(rho_m, rho_m1, rel: float = 1e-12) -> np.ndarray:

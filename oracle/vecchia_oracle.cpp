@@ -256,6 +256,160 @@ void orc_knn_rows(int64_t n, const double* xy, const double* t, const double* th
 }
 
 // ---------------------------------------------------------------------------
+// Correlation neighbours by the cover tree of Sect. 4.4.1 (Algorithm 1:
+// construction in index order; Algorithm 2: the pruned search), under the
+// metric d_c(x, y) = sqrt(1 - |rho(x, y)|), rho the latent correlation.
+//
+// Construction: the root is point 0 and covers every other point.  For level
+// l = 1, 2, ... with radius R_l = 2^-l, each knot k of level l turns its
+// covered set into knots of level l + 1: repeatedly the point of smallest
+// index in the set becomes a new knot (a child of k), and the points of the
+// set within d_c <= R_l of it become its covered set.  Every covered point
+// has a larger index than its knot, so a knot's descendants all come after it.
+//
+// Search for row i (its m + 1 nearest predecessors, to list cut-off ties):
+// Q = {root}; for j = 1 .. depth: C = Q and the children of Q's knots with
+// index < i; D = the (m + 1)-th smallest d_c from i over C (1 if C is
+// smaller); Q = {x in C : d_c(x, i) <= D + 2^-(j - 1)}; finally the nearest
+// points of Q by brute force (the same order as orc_knn_rows: larger |rho|
+// first, then the smaller index).
+// Pinned by: orc_knn_rows (brute force) on small inputs, and the tree's
+// invariants (every point a knot once, children after their knot, covered
+// points within the level's radius).
+namespace {
+
+double corr_abs(const Theta& th, const double* xy, const double* t, int64_t i, int64_t j) {
+  const double cij = cov_latent(th, dist2(xy, i, j), t[i] - t[j]);
+  const double c0 = cov_latent(th, 0.0, 0.0);
+  return std::fabs(cij) / c0;
+}
+double d_c(double rho_abs) { return std::sqrt(std::max(0.0, 1.0 - rho_abs)); }
+
+struct CoverTree {
+  std::vector<std::vector<int64_t>> children;  // per point: its child knots
+  std::vector<int> level;                      // per point: the level it is a knot of
+  int depth = 0;
+};
+
+CoverTree build_cover_tree(const Theta& th, const double* xy, const double* t, int64_t n) {
+  CoverTree T;
+  T.children.assign((size_t)n, {});
+  T.level.assign((size_t)n, 0);
+  if (n == 0) return T;
+  std::vector<std::vector<int64_t>> cover((size_t)n);
+  cover[0].reserve((size_t)n);
+  for (int64_t p = 1; p < n; ++p) cover[0].push_back(p);
+  T.level[0] = 1;
+  std::vector<int64_t> current = {0};
+  int l = 1;
+  int64_t knots = 1;
+  while (knots < n) {
+    const double R = std::ldexp(1.0, -l);
+    std::vector<int64_t> next;
+    for (int64_t k : current) {
+      std::vector<int64_t> S = std::move(cover[k]);
+      cover[k].clear();
+      size_t head = 0;  // S[head..] is the set still to cover, in increasing index order
+      while (head < S.size()) {
+        const int64_t v = S[head++];
+        T.children[k].push_back(v);
+        T.level[v] = l + 1;
+        next.push_back(v);
+        ++knots;
+        std::vector<int64_t> rest, cv;
+        for (size_t q = head; q < S.size(); ++q) {
+          const int64_t p = S[q];
+          if (d_c(corr_abs(th, xy, t, p, v)) <= R) cv.push_back(p);
+          else rest.push_back(p);
+        }
+        cover[v] = std::move(cv);
+        S = std::move(rest);
+        head = 0;
+      }
+    }
+    current = std::move(next);
+    ++l;
+  }
+  T.depth = l;
+  return T;
+}
+
+}  // namespace
+
+void* orc_cover_tree_build(int64_t n, const double* xy, const double* t, const double* th8) {
+  return new CoverTree(build_cover_tree(mk(th8), xy, t, n));
+}
+void orc_cover_tree_free(void* tree) { delete static_cast<CoverTree*>(tree); }
+int orc_cover_tree_depth(const void* tree) { return static_cast<const CoverTree*>(tree)->depth; }
+// per point: its level and parent (-1 for the root), for the invariant checks
+void orc_cover_tree_structure(const void* tree, int64_t n, int32_t* level, int64_t* parent) {
+  const CoverTree& T = *static_cast<const CoverTree*>(tree);
+  for (int64_t p = 0; p < n; ++p) {
+    level[p] = T.level[p];
+    parent[p] = -1;
+  }
+  for (int64_t p = 0; p < n; ++p)
+    for (int64_t c : T.children[p]) parent[c] = p;
+}
+
+void orc_knn_cover_tree(const void* tree, int64_t n, const double* xy, const double* t, const double* th8, int m,
+                        int64_t n_rows, const int64_t* rows, int32_t* nn, int32_t* nn_cnt, double* rho_m,
+                        double* rho_m1, int threads) {
+  const CoverTree& T = *static_cast<const CoverTree*>(tree);
+  const Theta th = mk(th8);
+  (void)n;
+  parallel_rows(n_rows, threads, [&](int64_t r) {
+    const int64_t i = rows[r];
+    const int K = m + 1;
+    // Q: (d_c from i, point, whether its children are in C already); a
+    // knot's children enter C once, in the step after the knot itself
+    struct Ent {
+      double d;
+      int64_t p;
+      bool expanded;
+    };
+    std::vector<Ent> Q;
+    if (i > 0) Q.push_back({d_c(corr_abs(th, xy, t, 0, i)), 0, false});
+    for (int j = 1; j <= T.depth && i > 0; ++j) {
+      std::vector<Ent> C = Q;
+      const size_t nq = C.size();
+      for (size_t q = 0; q < nq; ++q) {
+        if (C[q].expanded) continue;
+        C[q].expanded = true;
+        for (int64_t c : T.children[C[q].p])
+          if (c < i) C.push_back({d_c(corr_abs(th, xy, t, c, i)), c, false});
+      }
+      double D = 1.0;
+      if ((int64_t)C.size() >= K) {
+        std::vector<double> ds;
+        ds.reserve(C.size());
+        for (const auto& c : C) ds.push_back(c.d);
+        std::nth_element(ds.begin(), ds.begin() + (K - 1), ds.end());
+        D = ds[K - 1];
+      }
+      const double lim = D + std::ldexp(1.0, -(j - 1));
+      Q.clear();
+      for (const auto& c : C)
+        if (c.d <= lim) Q.push_back(c);
+    }
+    // brute force over Q, ranked by |rho| (then the smaller index)
+    std::vector<std::pair<double, int64_t>> cand;
+    cand.reserve(Q.size());
+    for (const auto& q : Q) cand.emplace_back(corr_abs(th, xy, t, i, q.p), q.p);
+    const int64_t keep = std::min<int64_t>((int64_t)K, (int64_t)cand.size());
+    auto better = [](const std::pair<double, int64_t>& A, const std::pair<double, int64_t>& B) {
+      return A.first > B.first || (A.first == B.first && A.second < B.second);
+    };
+    std::partial_sort(cand.begin(), cand.begin() + keep, cand.end(), better);
+    const int cnt = (int)std::min<int64_t>(m, i);
+    for (int q = 0; q < m; ++q) nn[r * m + q] = q < cnt ? (int32_t)cand[q].second : -1;
+    nn_cnt[r] = cnt;
+    rho_m[r] = (cnt == m && cnt > 0) ? cand[m - 1].first : NAN;
+    rho_m1[r] = (i > m) ? cand[m].first : NAN;
+  });
+}
+
+// ---------------------------------------------------------------------------
 // Vecchia factor on the response covariance (Sect. 4.1 with Sigma~ of Sect. 3.1):
 // A[i, q] = (A_i)_q for neighbour nn[i, q]  (B_{i, nn[i,q]} = -A[i, q]), D[i] = D_i.
 // Returns the first row whose Sigma~_N is not SPD, or -1.
