@@ -642,18 +642,22 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
 #pragma unroll
     for (int u = 0; u < VEC; ++u) a[q + u] = tmp[u];
   }
-  bool ok = true;
-  T dinv = T(1);
+  // Each lane keeps its own pivot (checked once after the loop) and 1/L_jj.
+  // Entries above the diagonal (a[k] of lanes j < k) are updated like the
+  // others but never read: the solves read the lower triangle only, and a
+  // step reads the broadcast column only below its pivot.
+  T dinv = T(1), mypiv = T(1);
 #pragma unroll
   for (int k = 0; k < PM; ++k) {
     if (!MIXED && k >= m && k < LAST) continue;  // FP64: skip padding positions (identity rows and columns)
     const T piv = __shfl_sync(kFull, a[k], k);
-    ok = ok && (piv > T(0));
-    const T rs = drsqrt<T>(piv > T(0) ? piv : T(1));
-    if (lane == k) dinv = rs;
-    const bool act = (lane >= k) && (lane < PM);
-    const T v = act ? a[k] * rs : T(0);
-    if (act) a[k] = v;
+    const T rs = drsqrt<T>(piv);  // NaN or inf for a pivot <= 0: the row fails the check below
+    if (lane == k) {
+      dinv = rs;
+      mypiv = piv;
+    }
+    const T v = a[k] * rs;
+    a[k] = v;
     if (lane < PM) s.col[lane] = v;
     __syncwarp();
 #pragma unroll
@@ -681,6 +685,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
     }
     __syncwarp();
   }
+  const bool ok = __all_sync(kFull, mypiv > T(0));
 
   if constexpr (MIXED) {
     // condition estimate from the pivots of the used positions
@@ -732,7 +737,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       if (!MIXED && k >= m && k < LAST) continue;  // FP64: skip padding positions (identity rows and columns)
       const T zk = __shfl_sync(kFull, accz * dinv, k);
       if (lane == k) zj = zk;
-      if (lane > k) accz = fma(-a[k], zk, accz);
+      accz = fma(-a[k], zk, accz);  // lanes <= k: their z is taken already
     }
   }
 
@@ -749,8 +754,10 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       T bk = T(0);
       if (need_b) bk = __shfl_sync(kFull, acc_b * dinv, k);
       if (lane == k) { aj = ak; bj = bk; }
-      if (lane < k) {
-        const T lkj = Lsm[k][lane];
+      {
+        // lanes >= k read entries on or above the diagonal and update sums
+        // whose values are taken already
+        const T lkj = Lsm[k][lane < PM ? lane : 0];
         if constexpr (MIXED) {
           if (need_b) {
             const float2 r = __ffma2_rn(make_float2(-lkj, -lkj), make_float2(ak, bk), make_float2(acc_a, acc_b));
