@@ -40,7 +40,7 @@ struct VifLayout {
 // inducing-point dimension padded for the tensor-core GEMM (N tiles of 256)
 inline int64_t vif_kp(int64_t k) { return (k + 255) / 256 * 256; }
 constexpr int kVifMaxParts = 3;  // BF16 parts per operand value
-constexpr int kVifCand = 2048;   // candidate slots per row of the filtered neighbour search
+constexpr int kVifCand = 1024;   // candidate slots per row of the filtered neighbour search
 constexpr int64_t kVifGather = 8192;  // rows per batch of the search's second (gathered) round
 // tensor-core candidate filter of the residual search: row and column tile
 // sizes, row tiles per group
