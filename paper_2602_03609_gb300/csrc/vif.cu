@@ -505,11 +505,18 @@ __global__ void __launch_bounds__(128) gram_delta_kernel(const int32_t* nn, cons
         for (int z = 0; z < 32; ++z) {
           const float4 a = *reinterpret_cast<const float4*>(col + z * PM + jr[q]);
           const float4 b = *reinterpret_cast<const float4*>(col + z * PM + jc[q]);
-          const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+          const float av[4] = {a.x, a.y, a.z, a.w};
+          const float2 b01 = make_float2(b.x, b.y), b23 = make_float2(b.z, b.w);
 #pragma unroll
-          for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y) part[4 * x + y] = fmaf(av[x], bv[y], part[4 * x + y]);
+          for (int x = 0; x < 4; ++x) {  // packed FP32 pairs: the same fmaf per product
+            const float2 ax = make_float2(av[x], av[x]);
+            const float2 p01 = __ffma2_rn(ax, b01, make_float2(part[4 * x], part[4 * x + 1]));
+            const float2 p23 = __ffma2_rn(ax, b23, make_float2(part[4 * x + 2], part[4 * x + 3]));
+            part[4 * x] = p01.x;
+            part[4 * x + 1] = p01.y;
+            part[4 * x + 2] = p23.x;
+            part[4 * x + 3] = p23.y;
+          }
         }
 #pragma unroll
         for (int z = 0; z < 16; ++z) {
