@@ -292,6 +292,26 @@ vst_status vif_lowrank_u(const vst_points* pts, const vst_theta* theta, const vs
                          int precision, double* U, double* r, void* workspace, size_t ws_bytes,
                          void* stream);
 
+/* The VIF's contraction over the points on the tensor cores (the products
+ * W^T W, W^T e and e^T e of the Woodbury form in the complexity remark of
+ * Sect. 4.3, and the gradient's k x k contractions): C = A^T B, or C = A^T A
+ * when B is NULL (both triangles written).
+ * A, B: [n][kc] FP32 device matrices, row strides lda, ldb >= kc (elements).
+ * C: [kc][kc] row-major FP64 device output.  Column c of an operand gets,
+ * in each block of 128 rows, the exponent E with max |A[i][c]| < 2^E over
+ * the block, and each value is cut into three BF16 fixed-point parts of 9
+ * bits (remainder at most 2^(E - 27)); six part products are kept, the
+ * leading one summed exactly over each block, the corrections in FP32, the
+ * blocks in double-float and FP64.  Values the parts hold exactly (integer
+ * multiples of 2^(E - 8)) give C exactly while every partial sum stays below
+ * 2^48 units of the product's leading power of two.
+ * 1 <= kc <= 16384, 0 <= n < 2^31.  Workspace: vst_workspace_size_gram_tc(n,
+ * kc) bytes, 256-byte aligned, caller-owned; a device wait that runs out is
+ * reported as VST_ETIMEOUT by vst_workspace_status. */
+size_t vst_workspace_size_gram_tc(int64_t n, int kc);
+vst_status vif_gram_tc(int64_t n, int kc, const float* A, int64_t lda, const float* B, int64_t ldb, double* C,
+                       void* workspace, size_t ws_bytes, void* stream);
+
 /* Batched NLL and gradient of nsets independent datasets (one Vecchia model
  * each, Sect. 4.1 and 3.1) in one persistent launch.  Dataset d owns rows
  * offsets[d] .. offsets[d+1]-1 of the concatenated arrays xy, t, y, nn,

@@ -30,7 +30,8 @@ __all__ = [
     "vecchia_sample", "vst_workspace_status", "VecchiaNLL", "theta_tuple", "vst_profile_enable",
     "vst_profile_read", "vecchia_nll_grad_noalloc", "vst_noalloc_status", "NOALLOC_MAX_N",
     "BatchedWorkspace", "vecchia_nll_grad_batched", "BatchedGraph", "vst_autotune_nll_grad",
-    "vst_autotune_nll_grad_batched", "vst_autotune_clear", "MIXED_BF16X3", "vif_lowrank_u",
+    "vst_autotune_nll_grad_batched", "vst_autotune_clear", "MIXED_BF16X3", "vif_lowrank_u", "vif_gram_tc",
+    "vst_workspace_size_gram_tc",
     "vecchia_predict", "vst_workspace_size_predict", "PredictWorkspace", "sts_kmeanspp",
     "vecchia_nll_grad_ex", "vecchia_nll_grad_batched_ex", "vecchia_sample_ex", "vst_noalloc_scratch_bytes",
 ]
@@ -133,6 +134,11 @@ def lib():
                                       ctypes.c_size_t, _P]
         L.vif_lowrank_u.restype = ctypes.c_int
         L.vif_lowrank_u.argtypes = [PT, TH, IN, ctypes.c_int, _P, _P, _P, ctypes.c_size_t, _P]
+        L.vst_workspace_size_gram_tc.restype = ctypes.c_size_t
+        L.vst_workspace_size_gram_tc.argtypes = [ctypes.c_int64, ctypes.c_int]
+        L.vif_gram_tc.restype = ctypes.c_int
+        L.vif_gram_tc.argtypes = [ctypes.c_int64, ctypes.c_int, _P, ctypes.c_int64, _P, ctypes.c_int64, _P, _P,
+                                  ctypes.c_size_t, _P]
         L.vecchia_sample.restype = ctypes.c_int
         L.vecchia_sample.argtypes = [PT, TH, ctypes.c_int, _P, _P, _P, _P, _P, ctypes.c_size_t, _P]
         L.vst_profile_enable.restype = None
@@ -372,6 +378,50 @@ def vif_lowrank_u(xy, t, theta, inducing, precision=FP64, U=None, r=None, ws=Non
                                _ptr(U, torch.float64, "U"), _ptr(r, torch.float64, "r"), ws.ptr, ws.nbytes,
                                _stream(stream)))
     return U, r
+
+
+def vst_workspace_size_gram_tc(n, kc) -> int:
+    return int(lib().vst_workspace_size_gram_tc(int(n), int(kc)))
+
+
+def _rows_f32(x, name, kc):
+    if not (isinstance(x, torch.Tensor) and x.is_cuda and x.dtype == torch.float32 and x.dim() == 2):
+        raise TypeError(f"{name} must be a 2-D CUDA float32 tensor")
+    if x.shape[1] != kc or x.stride(1) != 1 or (x.shape[0] > 1 and x.stride(0) < kc):
+        raise ValueError(f"{name} must be [n, kc] with unit column stride")
+    return x.data_ptr(), max(int(x.stride(0)), kc)
+
+
+def vif_gram_tc(A, B=None, C=None, ws=None, stream=None):
+    """C = A^T B (A^T A when B is None), [kc, kc] float64, on the tensor cores
+    with the fixed-point BF16 split, exponents per column and 128-row block
+    (the contraction over the points of the VIF's Woodbury form, Sect. 4.3).  A, B: [n, kc] CUDA float32 tensors whose
+    rows may be strided.  ws: a CUDA uint8 tensor of at least
+    vst_workspace_size_gram_tc(n, kc) bytes (allocated when None); its status
+    header is read by vst_workspace_status(ws)."""
+    n, kc = A.shape
+    pa, lda = _rows_f32(A, "A", kc)
+    pb, ldb = (None, 0) if B is None else _rows_f32(B, "B", kc)
+    if B is not None and B.shape[0] != n:
+        raise ValueError("A and B need the same number of rows")
+    C = C if C is not None else torch.empty((kc, kc), dtype=torch.float64, device=A.device)
+    need = vst_workspace_size_gram_tc(n, kc)
+    if ws is None:
+        ws = _RawWorkspace(need, A.device)
+    if ws.nbytes < need:
+        raise ValueError("workspace too small")
+    _check(lib().vif_gram_tc(int(n), int(kc), pa, lda, pb, ldb, _ptr(C, torch.float64, "C"), ws.ptr, ws.nbytes,
+                             _stream(stream)))
+    return C
+
+
+class _RawWorkspace(Workspace):
+    """A workspace of a given byte count (vif_gram_tc)."""
+
+    def __init__(self, nbytes, device=None):
+        self.nbytes = int(nbytes)
+        self.buf = torch.empty(self.nbytes + 256, dtype=torch.uint8, device=device or "cuda")
+        self.ptr = (self.buf.data_ptr() + 255) // 256 * 256
 
 
 def vst_workspace_size_predict(n_train, n_pred, m) -> int:

@@ -21,7 +21,8 @@
 //   gram64_kernel        FP64: per-row U_p . U_q over the local block (fed to the row kernel)
 //   gram_delta_kernel    mixed: per-row U_p . U_q, accumulated without cancellation
 //   wvec_kernel<T>       rows of [W e] and sum log D_i
-//   syrk_kernel<T>       partial [W e]^T [W e] over row chunks, then a fixed-order sum
+//   syrk_kernel<double>  partial [W e]^T [W e] over row chunks, then a fixed-order sum
+//                        (FP64 form; the mixed form's is tc_syrk on the tensor cores)
 //   final_kernel         M = I + G, FP64 Cholesky, z = L_M^{-1} W^T e, the NLL
 #include <algorithm>
 #include <cfloat>
@@ -1014,21 +1015,27 @@ static vst_status vif_nll_T(const vst_points* pts, const vst_theta* theta, int m
     nparts = (int64_t)wblocks * 8;
   }
   const int kk = k + 1;
-  const int64_t chunk = std::max<int64_t>((n + kVifSyrkChunks - 1) / kVifSyrkChunks, 1);
-  const int nchunk = (int)std::min<int64_t>(kVifSyrkChunks, (n + chunk - 1) / chunk);
-  const int nb = (kk + 63) / 64;
-  // [W e]^T [W e] stays on the FP32/FP64 SIMT kernel in both forms: the
-  // Woodbury quadratic form e^T e - v^T M^{-1} v cancels two O(n) terms, and
-  // the tensor cores' internal FP32 summation (not round-to-nearest) left
-  // |dNLL|/n above 1e-6 at n = 30,000, k = 1000 even with double-float
-  // drains every 128 rows
-  if (n > 0) {
-    ProfileScope ps(kProfVifSyrk, st);
-    syrk_kernel<T><<<dim3(nb, nb, nchunk), 256, 0, st>>>(WE, n, kk, chunk, part);
-  }
   const int64_t kk2 = (int64_t)kk * kk;
-  if (nchunk > 0) syrk_sum_kernel<<<(int)((kk2 + 255) / 256), 256, 0, st>>>(part, nchunk, kk, G);
-  else cudaMemsetAsync(G, 0, sizeof(double) * kk2, st);
+  if constexpr (std::is_same<T, float>::value) {
+    // [W e]^T [W e] on the tensor cores with the fixed-point split (six
+    // products in both mixed forms): the Woodbury quadratic form
+    // e^T e - v^T M^{-1} v cancels two O(n) terms, so the summation must be
+    // free of bias (a floating split's leading accumulator, not
+    // round-to-nearest, left |dNLL|/n above 1e-6 at n = 30,000, k = 1000)
+    ProfileScope ps(kProfVifSyrk, st);
+    s = tc_syrk(WE, kk, n, kk, G, vbase + V.Ap, part, hdr, st);
+    if (s != VST_OK) return s;
+  } else {
+    const int64_t chunk = std::max<int64_t>((n + kVifSyrkChunks - 1) / kVifSyrkChunks, 1);
+    const int nchunk = (int)std::min<int64_t>(kVifSyrkChunks, (n + chunk - 1) / chunk);
+    const int nb = (kk + 63) / 64;
+    if (n > 0) {
+      ProfileScope ps(kProfVifSyrk, st);
+      syrk_kernel<T><<<dim3(nb, nb, nchunk), 256, 0, st>>>(WE, n, kk, chunk, part);
+    }
+    if (nchunk > 0) syrk_sum_kernel<<<(int)((kk2 + 255) / 256), 256, 0, st>>>(part, nchunk, kk, G);
+    else cudaMemsetAsync(G, 0, sizeof(double) * kk2, st);
+  }
   make_m_kernel<<<(int)(((int64_t)k * k + 255) / 256 + 1), 256, 0, st>>>(G, k, M, v, z + k);
   s = chol64(M, k, hdr, VST_ENOTSPD, st);
   if (s != VST_OK) return s;

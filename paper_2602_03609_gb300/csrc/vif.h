@@ -48,14 +48,18 @@ vst_status tc_product(const float* A, int64_t lda, int64_t n, const double* M, i
                       int split_terms, char* vbase, const VifLayout& V, WsHeader* hdr, cudaStream_t st);
 
 // C = A^T B (FP64 kc x kc) for FP32 A, B [n][kc] (row strides lda, ldb) on
-// the tensor cores (vif_tc.cu): split K over the n rows, double-float drains
-// of the tensor-memory accumulators, segments summed in FP64 in a fixed order.
-// tmp: the first tc_gram_part_offset(n, kc) bytes of a tc_gram_bytes(n, kc)
-// region, part: the rest (16 kc^2 doubles).
-size_t tc_gram_bytes(int64_t n, int64_t kc);
-size_t tc_gram_part_offset(int64_t n, int64_t kc);
+// the tensor cores (vif_tc.cu): fixed-point BF16 parts (three) with an
+// exponent per column and 128-row block, split K over the n rows,
+// double-float drains of the tensor-memory accumulators, segments summed in
+// FP64 in a fixed order.  opa, opb: tc_operand_bytes(n, kc) bytes each
+// (workspace.h); part: tc_gram_part_bytes(kc) bytes.
+size_t tc_gram_part_bytes(int64_t kc);
 vst_status tc_gram(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t n, int kc, double* C,
-                   int split_terms, void* tmp, double* part, WsHeader* hdr, cudaStream_t st);
+                   void* opa, void* opb, double* part, WsHeader* hdr, cudaStream_t st);
+// C = A^T A (FP64 kc x kc, both triangles) on the same kernel, lower triangle
+// of tiles only; opa: tc_operand_bytes(n, kc) bytes.
+vst_status tc_syrk(const float* A, int64_t lda, int64_t n, int kc, double* C, void* opa, double* part,
+                   WsHeader* hdr, cudaStream_t st);
 
 // 2-D TMA map of a row-major BF16 matrix rows x cols (cols contiguous, a
 // multiple of 8), box 64 columns x box_rows rows, 128-byte swizzle (vif_tc.cu)

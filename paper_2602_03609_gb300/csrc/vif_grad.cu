@@ -58,7 +58,7 @@ constexpr int kChunks = kDgemmChunks;
 
 struct GradLayout {
   size_t LinvM, Minv, Y, GU, H, abar, dbar, eps, beta, qd, wv, svec, spart, btil, roff, rcur, rent, bsum,
-      t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, ltab, ltabf, xyf, xykf, svf, tcg, total;
+      t1part, Jpart, J, Kp, Psi, T1, Omega, t2part, grows, ltab, ltabf, xyf, xykf, svf, tcg, tcpart, total;
 };
 
 GradLayout grad_layout(int64_t n, int m, int64_t k) {
@@ -103,7 +103,8 @@ GradLayout grad_layout(int64_t n, int m, int64_t k) {
   G.xyf = take(8 * nn);
   G.xykf = take(8 * kk);
   G.svf = take(8 * kk);
-  G.tcg = take(tc_gram_bytes(n, k));
+  G.tcg = take(tc_operand_bytes(n, k));  // H^T U's second operand (the first in the NLL's Ap)
+  G.tcpart = take(tc_gram_part_bytes(k));
   G.total = off;
   return G;
 }
@@ -713,8 +714,10 @@ vst_status vif_nll_grad_T(const vst_points* pts, const vst_theta* theta, int m, 
     else t1(term1_kernel<2, T>);
   }
   if constexpr (F32) {
-    s = tc_gram(reinterpret_cast<const float*>(PT(G.H)), k, reinterpret_cast<const float*>(U), k, n, k, P(G.J), terms,
-                gb + G.tcg, P(G.tcg + tc_gram_part_offset(n, k)), hdr, st);
+    // (the NLL's operand-part buffers, free once the products above are
+    // formed, take H's parts)
+    s = tc_gram(reinterpret_cast<const float*>(PT(G.H)), k, reinterpret_cast<const float*>(U), k, n, k, P(G.J),
+                vb + V.Ap, gb + G.tcg, P(G.tcpart), hdr, st);
     if (s != VST_OK) return s;
   } else {
     gemm_tn(PT(G.H), k, U, k, n, k, k, false, P(G.Jpart), P(G.J), st);

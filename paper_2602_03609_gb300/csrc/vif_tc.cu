@@ -13,6 +13,25 @@
 // 16 significand bits (relative error ~1e-5 per product), three parts carry
 // 24 (the FP32 level).
 //
+// The contractions over the points (tc_gram, tc_syrk) use a fixed-point
+// split instead, in 128-row blocks: column c of an operand gets, in each
+// block, the exponent E with max |S[i][c]| < 2^E over the block's rows, and
+// x = S[i][c] becomes
+//   x 2^(8 - E) = s_0 + 2^-9 s_1 + 2^-18 s_2 + (a remainder below 2^-19)
+// with integers |s_j| <= 256, each exact in BF16 (part j holds s_j 2^(-9 j)).
+// The leading products s_0 s_0' are integers below 2^16 and the sum of one
+// block's 128 of them an integer below 2^23, so the leading accumulator of
+// one drain (one block) is exact whatever the tensor core's rounding: the
+// rounding bias of the floating split (one sign for the positive sums on a
+// Gram's diagonal) does not build up over n rows.  The other kept products,
+// 2^-9 smaller and below, go to the correction accumulator.  The drain scales
+// both by the block's power of two relative to the columns' largest exponents
+// (exact) before adding them to its double-float sums, and the segment sum
+// applies 2^(E_a + E_b - 16) of those largest exponents in FP64.  These
+// contractions always take three parts (six products), which leave a
+// remainder of at most 2^(E - 27) per value: the Woodbury form cancels two
+// O(n) terms, and two parts (2^(E - 18)) moved the VIF NLL by ~1e-4 per point.
+//
 // Operands in HBM, K-major BF16 (K = inducing point index p, padded to kp):
 //   A parts [P][n][kp]   A[i][p] = Sigma(x_i, z_p), FP32 evaluation
 //   B parts [P][kp][kp]  B[c][p] = (L^{-1})[c][p]  (lower triangular)
@@ -48,6 +67,7 @@ namespace vst {
 
 vst_status fail(vst_status s, const char* fmt, ...);
 vst_status cuda_fail(cudaError_t e, const char* where);
+void launch_init_header(WsHeader* h, cudaStream_t st);
 
 namespace {
 
@@ -144,33 +164,73 @@ __global__ void split_b_kernel(const double* M, int k, int kp, int mode, __nv_bf
   }
 }
 
-// Transposed parts of an FP32 matrix S [n][k] (row stride lds):
-// T[j][c][i] = part j of S[i][c], [P][kp][np], zero for i >= n or c >= k.
-// One block of 256 threads per 64 x 64 tile, staged through shared memory so
-// that both the reads (along c) and the writes (along i) are contiguous.
+// exponent E with |x| < 2^E for every x whose largest magnitude has the
+// FP32 bit pattern bits (zero and subnormal maxima give E = -126)
+__device__ __forceinline__ int fx_exp(unsigned bits) { return (int)((bits >> 23) & 0xffu) - 126; }
+
+// fixed-point parts of x given the shift sh = 8 - E
 template <int P>
-__global__ void split_t_kernel(const float* S, int64_t lds, int64_t n, int k, int kp, int64_t np, __nv_bfloat16* T) {
-  __shared__ float tile[64][65];
-  const int64_t i0 = (int64_t)blockIdx.x * 64;
+__device__ __forceinline__ void split_fixed(float x, int sh, __nv_bfloat16 (&o)[P]) {
+  float r = ldexpf(x, sh);  // |r| < 256
+#pragma unroll
+  for (int j = 0; j < P; ++j) {
+    const float sj = rintf(r);  // an integer, |sj| <= 256
+    o[j] = __float2bfloat16_rn(j == 0 ? sj : j == 1 ? sj * 0x1p-9f : sj * 0x1p-18f);
+    r = (r - sj) * 512.0f;  // exact: |r - sj| <= 1/2 is a multiple of r's last place
+  }
+}
+
+// column exponents are kept biased by kFxBias (positive, for atomicMax)
+constexpr int kFxBias = 1024;
+
+// Transposed fixed-point parts of an FP32 matrix S [n][k] (row stride lds):
+// T[j][c][i] = part j of S[i][c], [P][kp][np], zero for i >= n or c >= k,
+// with the exponent of column c over the 128-row block of row i, stored in
+// eblk[i / 128][c]; eg[c] (zeroed beforehand) collects the largest block
+// exponent of column c < k plus kFxBias.  One block of 256 threads per
+// 128 x 64 tile, staged through shared memory so that both the reads (along
+// c) and the writes (along i) are contiguous.  NaNs are passed over by the
+// maxima and reach the products through the parts.
+template <int P>
+__global__ void __launch_bounds__(256) split_fx_t_kernel(const float* S, int64_t lds, int64_t n, int k, int kp,
+                                                         int64_t np, __nv_bfloat16* T, int16_t* eblk, int* eg) {
+  __shared__ float tile[128][65];
+  __shared__ unsigned cmax[4][64];
+  __shared__ int esh[64];
+  const int64_t i0 = (int64_t)blockIdx.x * 128;
   const int c0 = blockIdx.y * 64;
   const int tc = threadIdx.x & 63, tr = threadIdx.x >> 6;
-#pragma unroll 4
-  for (int q = 0; q < 16; ++q) {
+  float mx = 0.0f;
+#pragma unroll 8
+  for (int q = 0; q < 32; ++q) {
     const int r = tr + 4 * q;
     const int64_t i = i0 + r;
     const int c = c0 + tc;
-    tile[r][tc] = (i < n && c < k) ? S[i * lds + c] : 0.0f;
+    const float v = (i < n && c < k) ? S[i * lds + c] : 0.0f;
+    tile[r][tc] = v;
+    mx = fmaxf(mx, fabsf(v));
+  }
+  cmax[tr][tc] = __float_as_uint(mx);  // non-negative floats order as their bit patterns
+  __syncthreads();
+  if (threadIdx.x < 64) {
+    const int t = threadIdx.x;
+    const unsigned m = max(max(cmax[0][t], cmax[1][t]), max(cmax[2][t], cmax[3][t]));
+    const int E = fx_exp(m);
+    esh[t] = E;
+    eblk[(int64_t)blockIdx.x * kp + c0 + t] = (int16_t)E;
+    if (c0 + t < k) atomicMax(eg + c0 + t, E + kFxBias);
   }
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 2; ++q) {
+  for (int q = 0; q < 4; ++q) {  // 64 columns x 16 groups of 8 rows
     const int item = threadIdx.x + 256 * q;
-    const int cr = item >> 3, g = item & 7;
+    const int cr = item >> 4, g = item & 15;
+    const int sh = 8 - esh[cr];
     __align__(16) __nv_bfloat16 o[P][8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       __nv_bfloat16 sp[P];
-      split_parts<P>(tile[g * 8 + e][cr], sp);
+      split_fixed<P>(tile[g * 8 + e][cr], sh, sp);
 #pragma unroll
       for (int j = 0; j < P; ++j) o[j][e] = sp[j];
     }
@@ -179,6 +239,22 @@ __global__ void split_t_kernel(const float* S, int64_t lds, int64_t n, int k, in
       *reinterpret_cast<uint4*>(T + ((int64_t)j * kp + c0 + cr) * np + i0 + g * 8) =
           *reinterpret_cast<const uint4*>(o[j]);
   }
+}
+
+// the pieces of one operand in its tc_operand_bytes region
+struct FxOperand {
+  __nv_bfloat16* parts;
+  int16_t* eblk;
+  int* eg;
+};
+FxOperand fx_operand(char* p, int64_t n, int kc) {
+  const size_t kp = (size_t)vif_kp(kc > 0 ? kc : 1);
+  const size_t np = (size_t)((n > 0 ? n : 1) + 127) / 128 * 128;
+  FxOperand o;
+  o.parts = reinterpret_cast<__nv_bfloat16*>(p);
+  o.eblk = reinterpret_cast<int16_t*>(p + align256(2 * (size_t)kVifMaxParts * kp * np));
+  o.eg = reinterpret_cast<int*>(reinterpret_cast<char*>(o.eblk) + align256(2 * (np / 128) * kp));
+  return o;
 }
 
 // double-float coordinates of the inducing points
@@ -406,10 +482,11 @@ __global__ void __launch_bounds__(128, 1)
 
 // ---- C = A^T B over the rows of A and B (split K, warp-specialised) ----
 //
-// The operands come as transposed BF16 parts [P][kp][np] (split_t_kernel):
+// The operands come as transposed BF16 parts [P][kp][np] (split_fx_t_kernel):
 // row c of part j holds part j of column c over the np rows (zero padded), so
 // C[a][b] = sum_i At[a][i] Bt[b][i] is a K-major product with K = the row
-// index.  A CTA computes one 128 x 128 output tile over one K segment.
+// index.  A CTA computes one 128 x 128 output tile (of all T x T tiles, or of
+// the lower triangle when tri) over one K segment of whole 128-row blocks.
 // Warp 0 issues the TMA loads; warp 1 issues the MMAs into two TMEM buffers,
 // each a main accumulator (a0 b0) and a correction accumulator (the other
 // kept part products) of 128 columns; warps 4-11 drain a buffer every
@@ -418,14 +495,18 @@ __global__ void __launch_bounds__(128, 1)
 // 64 ((w - 4) / 4) .. + 63) while the MMAs fill the other buffer.  Warps 2-3
 // only fill out the first warpgroup, which gives registers to the two
 // draining warpgroups (384 threads launch with 168 registers each, 64,512 in
-// all; 128 x 64 + 256 x 216 = 63,488).  The
-// tensor core's FP32 accumulation is not round-to-nearest, so its error
-// grows with the number of accumulation steps; a drain every 128 rows keeps
-// each run to 8 steps, and the double-float sums carry ~48 bits over the
-// whole segment.  Each CTA writes its tile (rows and columns < kc) in FP64
-// to out[segment]; gram_sum_kernel adds the segments in a fixed order.
+// all; 128 x 64 + 256 x 216 = 63,488).  One drain per 128-row block keeps
+// the leading accumulator's fixed-point sum below 2^23, hence exact, and each
+// correction run to 8 accumulation steps; the drain scales both by
+// 2^(E_a - Eg_a + E_b - Eg_b) (the block's exponents against the columns'
+// largest, at most 1, exact; below 2^-126 the block's terms are dropped) and
+// the double-float sums carry ~48 bits over the whole segment.  Each CTA
+// writes its tile (rows and columns < kc) in FP64 to out[segment];
+// gram_sum_kernel adds the segments in a fixed order.
 constexpr int kGramDrainKb = 2;
 constexpr int kGramMaxSeg = 16;
+static_assert(kGramDrainKb == 2, "one drain per 128-row exponent block");
+static_assert(kGramDrainKb * 64 * 256 * 256 <= (1 << 23), "leading fixed-point sum of one drain exact in FP32");
 
 template <int P, int STAGES>
 struct GramTcShape {
@@ -433,7 +514,7 @@ struct GramTcShape {
   static constexpr int A_BYTES = BM * BK * 2;
   static constexpr int B_BYTES = BN * BK * 2;
   static constexpr int STAGE_BYTES = P * (A_BYTES + B_BYTES);
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 256 + 1024;  // + barriers, alignment slack
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 256 + 1024 + 1024;  // + barriers, column exponents, slack
   static constexpr int THREADS = 384;
   static constexpr int REGS_LOW = 64, REGS_HIGH = 216;
   static_assert(128 * REGS_LOW + 256 * REGS_HIGH <= THREADS * 168, "register split");
@@ -445,7 +526,8 @@ struct GramTcShape {
 template <int P, int STAGES>
 __global__ void __launch_bounds__(384, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int64_t np,
-                   int kc, int kp, int nseg, double* out, WsHeader* hdr) {
+                   int kc, int kp, int nseg, int tri, const int16_t* ea_blk, const int* ea_g,
+                   const int16_t* eb_blk, const int* eb_g, double* out, WsHeader* hdr) {
   using S = GramTcShape<P, STAGES>;
   extern __shared__ unsigned char tc_smem[];
   const uint32_t raw = umma::smem_u32(tc_smem);
@@ -458,18 +540,26 @@ __global__ void __launch_bounds__(384, 1)
   uint64_t* done = acce + 2;        // every MMA finished
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   volatile uint32_t* drain_fail = tslot + 1;  // a drain warp's wait ran out
+  int* egs = reinterpret_cast<int*>(gbase + STAGES * S::STAGE_BYTES + 256);  // [128 rows | 128 columns]
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int T = kp / S::BM;
-  const int ntiles = T * T;
+  const int ntiles = tri ? T * (T + 1) / 2 : T * T;
   const int tile = (int)(blockIdx.x % ntiles), seg = (int)(blockIdx.x / ntiles);
-  const int tm = tile / T, tn = tile % T;
-  // this segment's K blocks: the first (kbt % nseg) segments take one more
-  const int64_t kbt = np / S::BK;
-  const int64_t per = kbt / nseg, rem = kbt % nseg;
-  const int64_t kb0 = seg * per + (seg < rem ? seg : rem);
-  const int nkb = (int)(per + (seg < rem ? 1 : 0));
-  const int ndr = (nkb + kGramDrainKb - 1) / kGramDrainKb;
+  int tm = tile / T, tn = tile % T;
+  if (tri) {  // the lower triangle of tiles, tn <= tm
+    tm = 0;
+    while ((tm + 1) * (tm + 2) / 2 <= tile) ++tm;
+    tn = tile - tm * (tm + 1) / 2;
+  }
+  // this segment's 128-row blocks (two K blocks each): the first (nb % nseg)
+  // segments take one more
+  const int64_t nb = np / 128;
+  const int64_t per = nb / nseg, rem = nb % nseg;
+  const int64_t b0 = seg * per + (seg < rem ? seg : rem);
+  const int ndr = (int)(per + (seg < rem ? 1 : 0));
+  const int64_t kb0 = 2 * b0;
+  const int nkb = 2 * ndr;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -484,6 +574,8 @@ __global__ void __launch_bounds__(384, 1)
     *drain_fail = 0u;
     umma::fence_mbar_init();
   }
+  for (int q = threadIdx.x; q < 256; q += S::THREADS)
+    egs[q] = q < 128 ? ea_g[tm * S::BM + q] - kFxBias : eb_g[tn * S::BN + q - 128] - kFxBias;
   if (warp == 0) {
     umma::tmem_alloc(umma::smem_u32(tslot), 512);
     umma::tmem_relinquish();
@@ -589,8 +681,13 @@ __global__ void __launch_bounds__(384, 1)
     float hi[64], lo[64];
 #pragma unroll
     for (int c = 0; c < 64; ++c) hi[c] = lo[c] = 0.f;
+    const int arow = q4 * 32 + lane;
+    const int16_t* ea_row = ea_blk + tm * S::BM + arow;
+    const int16_t* eb_col = eb_blk + tn * S::BN + half * 64;
     for (int d = 0; d < ndr; ++d) {
       const int b = d & 1;
+      const int64_t blk = b0 + d;
+      const int da = (int)ea_row[blk * kp] - egs[arow];
       if (!warp_wait(&accf[b], (uint32_t)(d >> 1) & 1u)) {
         ok = false;
         break;
@@ -602,6 +699,7 @@ __global__ void __launch_bounds__(384, 1)
         uint32_t v[8], w[8];
         umma::tmem_ld_32x32b_x8(ta + c * 8, v);
         umma::tmem_ld_32x32b_x8(ta + S::BN + c * 8, w);
+        const uint4 e8 = __ldg(reinterpret_cast<const uint4*>(eb_col + blk * kp + c * 8));
         umma::tmem_wait_ld();
         if (c == 7) {
           // the buffer is free for the next MMAs once its last columns are read
@@ -609,11 +707,16 @@ __global__ void __launch_bounds__(384, 1)
           __syncwarp();
           if (lane == 0) umma::mbar_arrive(&acce[b]);
         }
+        const uint32_t ew[4] = {e8.x, e8.y, e8.z, e8.w};
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-          const df t = df_two_sum(hi[c * 8 + e], __uint_as_float(v[e]));
+          const int eb = (int)(int16_t)(ew[e >> 1] >> (16 * (e & 1)));
+          // 2^x for x = min(da + db, 0) (padding columns: zero products), 0 below 2^-126
+          const int x = min(da + eb - egs[128 + half * 64 + c * 8 + e], 0);
+          const float sc = x < -126 ? 0.0f : __int_as_float((127 + x) << 23);
+          const df t = df_two_sum(hi[c * 8 + e], __uint_as_float(v[e]) * sc);
           hi[c * 8 + e] = t.hi;
-          lo[c * 8 + e] += t.lo + __uint_as_float(w[e]);
+          lo[c * 8 + e] += t.lo + __uint_as_float(w[e]) * sc;
         }
       }
     }
@@ -643,13 +746,20 @@ __global__ void __launch_bounds__(384, 1)
   if (warp == 0) umma::tmem_dealloc(tmem, 512);
 }
 
-// C = the sum of the nseg FP64 partials (fixed order)
-__global__ void gram_sum_kernel(const double* part, int nseg, int kc, double* C) {
+// C[a][b] = 2^(Eg_a + Eg_b - 16) times the sum of the nseg FP64 partials
+// (fixed order), Eg the columns' largest exponents (biased); sym: only
+// b <= a was computed, mirrored into both triangles
+__global__ void gram_sum_kernel(const double* part, int nseg, int kc, const int* ea, const int* eb, int sym,
+                                double* C) {
   const int64_t kk = (int64_t)kc * kc;
   for (int64_t id = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; id < kk; id += (int64_t)gridDim.x * blockDim.x) {
+    const int a = (int)(id / kc), b = (int)(id % kc);
+    if (sym && b > a) continue;
     double s = 0.0;
     for (int q = 0; q < nseg; ++q) s += part[q * kk + id];
+    s = ldexp(s, ea[a] + eb[b] - 2 * kFxBias - 16);
     C[id] = s;
+    if (sym) C[(int64_t)b * kc + a] = s;
   }
 }
 
@@ -742,7 +852,7 @@ vst_status tc_product_P(const float* A, int64_t lda, int64_t n, const double* M,
 }
 
 // segments of K for a grid of ntiles tiles: the count in 1..kGramMaxSeg
-// (at most one per K block) whose CTAs fill the SMs' waves best, the
+// (at most one per 128-row block) whose CTAs fill the SMs' waves best, the
 // smallest such count on ties
 int gram_nseg(int ntiles, int64_t kbt, int sms) {
   int best = 1;
@@ -759,23 +869,30 @@ int gram_nseg(int ntiles, int64_t kbt, int sms) {
   return best;
 }
 
+// B == nullptr: the symmetric C = A^T A (one operand, the lower triangle of
+// tiles, mirrored by the sum).  opa, opb: the operands' regions
+// (tc_operand_bytes each; opb unused when symmetric).
 template <int P, int STAGES>
 vst_status tc_gram_P(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t n, int kc, double* C,
-                     char* tmp, double* part, WsHeader* hdr, cudaStream_t st) {
+                     char* opa, char* opb, double* part, WsHeader* hdr, cudaStream_t st) {
   using S = GramTcShape<P, STAGES>;
+  const bool sym = B == nullptr;
   const int kp = vif_kp(kc);
-  const int64_t np = (n + 63) / 64 * 64;
-  __nv_bfloat16* At = reinterpret_cast<__nv_bfloat16*>(tmp);
-  __nv_bfloat16* Bt = At + (size_t)P * kp * np;
-  const dim3 tgrid((unsigned)(np / 64), (unsigned)(kp / 64));
-  if (np / 64 > 0x7fffffff) return fail(VST_EINVAL, "too many rows");
-  split_t_kernel<P><<<tgrid, 256, 0, st>>>(A, lda, n, kc, kp, np, At);
-  split_t_kernel<P><<<tgrid, 256, 0, st>>>(B, ldb, n, kc, kp, np, Bt);
-  cudaError_t e = cudaGetLastError();
+  const int64_t np = (n + 127) / 128 * 128;
+  const FxOperand oa = fx_operand(opa, n, kc);
+  const FxOperand ob = sym ? oa : fx_operand(opb, n, kc);
+  const dim3 tgrid((unsigned)(np / 128), (unsigned)(kp / 64));
+  if (np / 128 > 0x7fffffff) return fail(VST_EINVAL, "too many rows");
+  cudaError_t e = cudaMemsetAsync(oa.eg, 0, sizeof(int) * kp, st);
+  if (e == cudaSuccess && !sym) e = cudaMemsetAsync(ob.eg, 0, sizeof(int) * kp, st);
+  if (e != cudaSuccess) return cuda_fail(e, "column exponents");
+  split_fx_t_kernel<P><<<tgrid, 256, 0, st>>>(A, lda, n, kc, kp, np, oa.parts, oa.eblk, oa.eg);
+  if (!sym) split_fx_t_kernel<P><<<tgrid, 256, 0, st>>>(B, ldb, n, kc, kp, np, ob.parts, ob.eblk, ob.eg);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "transposed split kernels");
   CUtensorMap ta, tb;
-  if (!make_map(&ta, At, (uint64_t)P * kp, (uint64_t)np, S::BM) ||
-      !make_map(&tb, Bt, (uint64_t)P * kp, (uint64_t)np, S::BN))
+  if (!make_map(&ta, oa.parts, (uint64_t)P * kp, (uint64_t)np, S::BM) ||
+      !make_map(&tb, ob.parts, (uint64_t)P * kp, (uint64_t)np, S::BN))
     return fail(VST_ECUDA, "cuTensorMapEncodeTiled unavailable or rejected the operand layout");
   auto kern = gram_tc_kernel<P, STAGES>;
   e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
@@ -792,11 +909,13 @@ vst_status tc_gram_P(const float* A, int64_t lda, const float* B, int64_t ldb, i
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int T = kp / S::BM;
-  const int ntiles = T * T;
-  const int nseg = gram_nseg(ntiles, np / S::BK, std::max(1, sms));
-  kern<<<(unsigned)(ntiles * nseg), S::THREADS, S::SMEM, st>>>(ta, tb, np, kc, kp, nseg, part, hdr);
+  const int ntiles = sym ? T * (T + 1) / 2 : T * T;
+  const int nseg = gram_nseg(ntiles, np / 128, std::max(1, sms));
+  kern<<<(unsigned)(ntiles * nseg), S::THREADS, S::SMEM, st>>>(ta, tb, np, kc, kp, nseg, sym ? 1 : 0, oa.eblk, oa.eg,
+                                                               ob.eblk, ob.eg, part, hdr);
   const int64_t kk = (int64_t)kc * kc;
-  gram_sum_kernel<<<(unsigned)std::min<int64_t>((kk + 255) / 256, 8192), 256, 0, st>>>(part, nseg, kc, C);
+  gram_sum_kernel<<<(unsigned)std::min<int64_t>((kk + 255) / 256, 8192), 256, 0, st>>>(part, nseg, kc, oa.eg, ob.eg,
+                                                                                       sym ? 1 : 0, C);
   e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "tensor-core Gram");
 }
@@ -861,29 +980,29 @@ vst_status tc_product(const float* A, int64_t lda, int64_t n, const double* M, i
                     : tc_product_P<3, 128, 2>(A, lda, n, M, k, C, vbase, V, hdr, st);
 }
 
-// scratch of tc_gram: the two transposed operands (three parts each) and the
-// FP64 partials of up to kGramMaxSeg segments
-size_t tc_gram_bytes(int64_t n, int64_t kc) {
-  return tc_gram_part_offset(n, kc) + (size_t)8 * kGramMaxSeg * kc * kc;
-}
-size_t tc_gram_part_offset(int64_t n, int64_t kc) {
-  const int64_t kp = vif_kp(std::max<int64_t>(kc, 1));
-  const int64_t np = (std::max<int64_t>(n, 1) + 63) / 64 * 64;
-  return align256((size_t)2 * 3 * kp * np * 2);
-}
+// FP64 partials of tc_gram / tc_syrk: up to kGramMaxSeg kc x kc segments
+size_t tc_gram_part_bytes(int64_t kc) { return (size_t)8 * kGramMaxSeg * kc * kc; }
 
 // C = A^T B (FP64 kc x kc) for FP32 A, B [n][kc] (row strides lda, ldb) on
-// the tensor cores: transposed split parts, split-K tiles over the rows with
-// double-float drains of the tensor-memory accumulators, segments summed in
-// FP64 in a fixed order.  split_terms = 3 or 6; tmp: the transposed parts
-// (tc_gram_part_offset bytes), part: kGramMaxSeg kc x kc doubles.
+// the tensor cores: transposed fixed-point parts, split-K tiles over the
+// 128-row blocks with double-float drains of the tensor-memory accumulators,
+// segments summed in FP64 in a fixed order.  opa, opb: tc_operand_bytes(n,
+// kc) bytes each; part: tc_gram_part_bytes(kc) bytes.
 vst_status tc_gram(const float* A, int64_t lda, const float* B, int64_t ldb, int64_t n, int kc, double* C,
-                   int split_terms, void* tmp, double* part, WsHeader* hdr, cudaStream_t st) {
+                   void* opa, void* opb, double* part, WsHeader* hdr, cudaStream_t st) {
   if (kc <= 0) return VST_OK;
   if (n <= 0) return cudaMemsetAsync(C, 0, sizeof(double) * kc * kc, st) == cudaSuccess ? VST_OK : VST_ECUDA;
-  char* t = static_cast<char*>(tmp);
-  return split_terms == 3 ? tc_gram_P<2, 3>(A, lda, B, ldb, n, kc, C, t, part, hdr, st)
-                          : tc_gram_P<3, 2>(A, lda, B, ldb, n, kc, C, t, part, hdr, st);
+  return tc_gram_P<3, 2>(A, lda, B, ldb, n, kc, C, static_cast<char*>(opa), static_cast<char*>(opb), part, hdr, st);
+}
+
+// C = A^T A (FP64 kc x kc, both triangles) for FP32 A [n][kc] (row stride
+// lda): tc_gram's product on the lower triangle of tiles.  opa:
+// tc_operand_bytes(n, kc) bytes; part: tc_gram_part_bytes(kc) bytes.
+vst_status tc_syrk(const float* A, int64_t lda, int64_t n, int kc, double* C, void* opa, double* part,
+                   WsHeader* hdr, cudaStream_t st) {
+  if (kc <= 0) return VST_OK;
+  if (n <= 0) return cudaMemsetAsync(C, 0, sizeof(double) * kc * kc, st) == cudaSuccess ? VST_OK : VST_ECUDA;
+  return tc_gram_P<3, 2>(A, lda, nullptr, 0, n, kc, C, static_cast<char*>(opa), nullptr, part, hdr, st);
 }
 
 // U (FP32, [n][k]) of the mixed form on the tensor cores; split_terms = 3 or 6.
@@ -896,3 +1015,30 @@ vst_status lowrank_tc(const vst_points* pts, const vst_theta* theta, const vst_i
 }
 
 }  // namespace vst
+
+using namespace vst;
+
+// workspace: the status header, the two operands' regions, the partials
+extern "C" size_t vst_workspace_size_gram_tc(int64_t n, int kc) {
+  if (n < 0 || kc <= 0) return 0;
+  return 256 + 2 * tc_operand_bytes(n, kc) + align256(tc_gram_part_bytes(kc));
+}
+
+extern "C" vst_status vif_gram_tc(int64_t n, int kc, const float* A, int64_t lda, const float* B, int64_t ldb,
+                                  double* C, void* ws, size_t ws_bytes, void* stream) {
+  if (n < 0 || n >= (int64_t(1) << 31)) return fail(VST_EINVAL, "n=%lld out of range", (long long)n);
+  if (kc <= 0 || kc > 16384) return fail(VST_EINVAL, "kc=%d out of range (1..16384)", kc);
+  if (!C || (n > 0 && !A)) return fail(VST_EINVAL, "NULL array");
+  if (lda < kc || (B && ldb < kc)) return fail(VST_EINVAL, "row strides below kc");
+  if (!ws || reinterpret_cast<uintptr_t>(ws) % 256) return fail(VST_EINVAL, "workspace NULL or not 256-byte aligned");
+  const size_t need = vst_workspace_size_gram_tc(n, kc);
+  if (ws_bytes < need) return fail(VST_ENOMEM, "workspace has %zu bytes, %zu needed", ws_bytes, need);
+  cudaStream_t st = (cudaStream_t)stream;
+  char* base = static_cast<char*>(ws);
+  WsHeader* hdr = reinterpret_cast<WsHeader*>(base);
+  launch_init_header(hdr, st);
+  char* opa = base + 256;
+  char* opb = opa + tc_operand_bytes(n, kc);
+  double* part = reinterpret_cast<double*>(opb + tc_operand_bytes(n, kc));
+  return B ? tc_gram(A, lda, B, ldb, n, kc, C, opa, opb, part, hdr, st) : tc_syrk(A, lda, n, kc, C, opa, part, hdr, st);
+}

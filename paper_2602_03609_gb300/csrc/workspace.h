@@ -62,6 +62,18 @@ inline size_t knn_scratch_bytes(int64_t n) {
 
 inline size_t align256(size_t v);
 
+// one operand of the tensor-core contractions over the points: its
+// transposed BF16 parts [kVifMaxParts][kp][np] (np = n rounded up to 128),
+// the exponent of each column over each 128-row block [np / 128][kp] (int16)
+// and over all rows [kp] (int32)
+inline size_t tc_operand_bytes(int64_t n, int64_t kc) {
+  const size_t kp = (size_t)vif_kp(kc > 0 ? kc : 1);
+  const size_t np = (size_t)((n > 0 ? n : 1) + 127) / 128 * 128;
+  return align256(2 * (size_t)kVifMaxParts * kp * np) + align256(2 * (np / 128) * kp) + align256(4 * kp);
+}
+// scratch of the symmetric product A^T A: one operand
+inline size_t tc_syrk_tmp_bytes(int64_t n, int64_t kc) { return tc_operand_bytes(n, kc); }
+
 inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
   VifLayout L{};
   size_t off = 0;
@@ -90,7 +102,8 @@ inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
   const size_t kp = (size_t)vif_kp((int64_t)kk);
   // (the residual neighbour search keeps U in FP32 and then in BF16 [n][k
   // rounded up to 64] here; the 1 KiB covers the alignment between the two)
-  L.Ap = take(2 * (size_t)kVifMaxParts * nn * kp + 1024);
+  // (also the scratch of the tensor-core [W e]^T [W e], kk + 1 columns)
+  L.Ap = take(std::max(2 * (size_t)kVifMaxParts * nn * kp + 1024, tc_syrk_tmp_bytes((int64_t)nn, (int64_t)kk + 1)));
   L.Bp = take(2 * (size_t)kVifMaxParts * kp * kp);
   L.zf = take(16 * kk);
   L.rpart = take(sizeof(double) * nn * (kp / 128));

@@ -116,3 +116,25 @@ def test_host_validation_without_gpu(vst):
     rc = L.vif_build_neighbors(ctypes.byref(pts), ctypes.byref(th), 5, ctypes.byref(big), 1024, 2048, None, 0,
                                256, 1 << 40, None)
     assert rc == 1 and b"inducing" in L.vst_last_error()
+
+
+def test_gram_tc_workspace_size_and_argument_checks(vst):
+    # header 256 B; two operands, each its transposed parts (3 parts x kp x
+    # np BF16, kp = kc rounded up to 256, np = n rounded up to 128), an int16
+    # exponent per column and 128-row block and an int32 one per column; then
+    # 16 segments of kc x kc doubles
+    n, kc = 1000, 300
+    kp, np_ = 512, 1024
+    opb = 2 * 3 * kp * np_ + 2 * (np_ // 128) * kp + 4 * kp
+    expect = 256 + 2 * opb + 8 * 16 * kc * kc
+    assert vst.vst_workspace_size_gram_tc(n, kc) == expect
+    assert vst.vst_workspace_size_gram_tc(n, 0) == 0
+    L = vst.lib()
+    fake = ctypes.c_void_p(256)
+    for nn_, kc_ in [(n, 0), (-1, kc), (n, 20000)]:
+        rc = L.vif_gram_tc(nn_, kc_, fake, max(kc_, 1), None, 0, fake, fake, 1 << 40, None)
+        assert rc == 1, (nn_, kc_)  # VST_EINVAL, before any device work
+    rc = L.vif_gram_tc(n, kc, fake, kc - 1, None, 0, fake, fake, 1 << 40, None)
+    assert rc == 1
+    rc = L.vif_gram_tc(n, kc, fake, kc, None, 0, fake, fake, expect - 1, None)
+    assert rc == 2  # VST_ENOMEM
