@@ -304,6 +304,32 @@ __device__ __forceinline__ void pair_cov(T dx, T dy, T P, T G, T& v, T& q) {
   }
 }
 
+// covariance and P x M'(x) of two pairs at once on packed FP32 pairs (mixed
+// form, per-pair lag factors and distances as float2); Pm is P already
+// multiplied by the pairs' validity (0 or 1)
+template <int NU>
+__device__ __forceinline__ void pair_cov2(float2 dx, float2 dy, float2 Pm, float2 G, float2& v, float2& q) {
+  const float2 d2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
+  const float2 hh = __fmul2_rn(d2, make_float2(rsqrtf(d2.x), rsqrtf(d2.y)));
+  const float2 h = make_float2(d2.x > 0.f ? hh.x : 0.f, d2.y > 0.f ? hh.y : 0.f);
+  const float2 x = __fmul2_rn(G, h);
+  const float2 E = make_float2(__expf(-x.x), __expf(-x.y));
+  float2 M, xdM;
+  if constexpr (NU == 0) {
+    M = E;
+    xdM = __fmul2_rn(x, make_float2(-E.x, -E.y));
+  } else if constexpr (NU == 1) {
+    M = __ffma2_rn(x, E, E);  // (1 + x) e^-x
+    xdM = __fmul2_rn(__fmul2_rn(x, x), make_float2(-E.x, -E.y));
+  } else {
+    const float2 x23 = __fmul2_rn(__fmul2_rn(x, x), make_float2(1.0f / 3.0f, 1.0f / 3.0f));
+    M = __fmul2_rn(__fadd2_rn(__fadd2_rn(make_float2(1.0f, 1.0f), x), x23), E);
+    xdM = __fmul2_rn(__fmul2_rn(x23, __fadd2_rn(make_float2(1.0f, 1.0f), x)), make_float2(-E.x, -E.y));
+  }
+  v = __fmul2_rn(Pm, M);
+  q = __fmul2_rn(Pm, xdM);
+}
+
 // lag factors of a pair: from the row's table when FAST (all times integer
 // days and every lag of the block inside the table), else the general lookup
 template <typename T, bool FAST, typename LagS>
@@ -325,7 +351,57 @@ __device__ __forceinline__ void cov_tiled(const DevTheta& th, const LagD* lagd, 
   constexpr int TS = TileShape<PM>::TS;
   constexpr bool MIXED = std::is_same<T, float>::value;
   T* qt = MIXED ? reinterpret_cast<T*>(&s.q1[0]) : reinterpret_cast<T*>(&s.xe[0][0]);
-  if (lane < 28) {
+  if constexpr (MIXED && TS % 2 == 0) {
+    // the tile's column pairs (b, b + 1) on packed FP32 pairs; invalid
+    // positions enter as a zero factor on P.  The lag factors come from the
+    // row's table or the general lookup; the arithmetic is the same either
+    // way, so a dataset gives the same bits in single and batched calls.
+    constexpr int TH = TS / 2;
+    if (lane < 28) {
+      float2 ncx[TH], ncy[TH], cmask[TH];
+      int ctd[TS];
+#pragma unroll
+      for (int u = 0; u < TH; ++u) {
+        const Pos<T> p0 = s.pos[tC * TS + 2 * u], p1 = s.pos[tC * TS + 2 * u + 1];
+        ncx[u] = make_float2(-p0.ox, -p1.ox);
+        ncy[u] = make_float2(-p0.oy, -p1.oy);
+        cmask[u] = make_float2(p0.valid ? 1.0f : 0.0f, p1.valid ? 1.0f : 0.0f);
+        ctd[2 * u] = p0.td;
+        ctd[2 * u + 1] = p1.td;
+      }
+      T kv[TS][TS];
+#pragma unroll
+      for (int a = 0; a < TS; ++a) {
+        const Pos<T> pr = s.pos[tR * TS + a];
+        const float rm = pr.valid ? 1.0f : 0.0f;
+        const float2 rx = make_float2(pr.ox, pr.ox), ry = make_float2(pr.oy, pr.oy), rmm = make_float2(rm, rm);
+#pragma unroll
+        for (int u = 0; u < TH; ++u) {
+          T P0, G0, Qa0, L0, P1, G1, Qa1, L1;
+          pair_lag<T, FAST>(th, lagd, lagf, tab, allint, pr.td, ctd[2 * u], s.tt[tR * TS + a], s.tt[tC * TS + 2 * u], P0,
+                            G0, Qa0, L0);
+          pair_lag<T, FAST>(th, lagd, lagf, tab, allint, pr.td, ctd[2 * u + 1], s.tt[tR * TS + a],
+                            s.tt[tC * TS + 2 * u + 1], P1, G1, Qa1, L1);
+          const float2 Pm = __fmul2_rn(make_float2(P0, P1), __fmul2_rn(rmm, cmask[u]));
+          float2 v, q;
+          pair_cov2<NU>(__fadd2_rn(rx, ncx[u]), __fadd2_rn(ry, ncy[u]), Pm, make_float2(G0, G1), v, q);
+          kv[a][2 * u] = v.x;
+          kv[a][2 * u + 1] = v.y;
+          qt[(a * TS + 2 * u) * 32 + lane] = q.x;
+          qt[(a * TS + 2 * u + 1) * 32 + lane] = q.y;
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < TS; ++a) st_row<T, TS>(&s.K[tR * TS + a][tC * TS], kv[a]);
+#pragma unroll
+      for (int b = 0; b < TS; ++b) {
+        T col[TS];
+#pragma unroll
+        for (int a = 0; a < TS; ++a) col[a] = kv[a][b];
+        st_row<T, TS>(&s.K[tC * TS + b][tR * TS], col);
+      }
+    }
+  } else if (lane < 28) {
     Pos<T> pc[TS];
 #pragma unroll
     for (int u = 0; u < TS; ++u) pc[u] = s.pos[tC * TS + u];
@@ -355,19 +431,41 @@ __device__ __forceinline__ void cov_tiled(const DevTheta& th, const LagD* lagd, 
       st_row<T, TS>(&s.K[tC * TS + b][tR * TS], col);
     }
   }
-  for (int q = lane; q < bs->ndpairs; q += 32) {
-    const uint32_t rc = bs->dpairs[q];
-    const int r = rc & 0xff, c = (rc >> 8) & 0xff;
-    const Pos<T> pr = s.pos[r], pc = s.pos[c];
-    T P, G, Qa, L, v, qq;
-    pair_lag<T, FAST>(th, lagd, lagf, tab, allint, pr.td, pc.td, s.tt[r], s.tt[c], P, G, Qa, L);
-    pair_cov<T, NU>(pr.ox - pc.ox, pr.oy - pc.oy, P, G, v, qq);
-    const bool ok = (pr.valid & pc.valid) != 0;
-    v = ok ? v : T(0);
-    s.K[r][c] = v;
-    s.K[c][r] = v;
-    s.qd[q] = ok ? qq : T(0);
-    if constexpr (!MIXED) s.qd[2 * PM + q] = v;
+  if constexpr (MIXED && TS % 2 == 0) {
+    // the diagonal-block pairs two per lane (their count 8 TS (TS - 1) / 2 is even)
+    const int q0 = 2 * lane;
+    if (q0 < bs->ndpairs) {
+      const uint32_t rc0 = bs->dpairs[q0], rc1 = bs->dpairs[q0 + 1];
+      const int pr_0 = rc0 & 0xff, pc_0 = (rc0 >> 8) & 0xff, pr_1 = rc1 & 0xff, pc_1 = (rc1 >> 8) & 0xff;
+      const Pos<T> pr0 = s.pos[pr_0], pc0 = s.pos[pc_0], pr1 = s.pos[pr_1], pc1 = s.pos[pc_1];
+      T P0, G0, Qa0, L0, P1, G1, Qa1, L1;
+      pair_lag<T, FAST>(th, lagd, lagf, tab, allint, pr0.td, pc0.td, s.tt[pr_0], s.tt[pc_0], P0, G0, Qa0, L0);
+      pair_lag<T, FAST>(th, lagd, lagf, tab, allint, pr1.td, pc1.td, s.tt[pr_1], s.tt[pc_1], P1, G1, Qa1, L1);
+      const float2 Pm = make_float2((pr0.valid & pc0.valid) ? P0 : 0.0f, (pr1.valid & pc1.valid) ? P1 : 0.0f);
+      float2 v, q;
+      pair_cov2<NU>(make_float2(pr0.ox - pc0.ox, pr1.ox - pc1.ox), make_float2(pr0.oy - pc0.oy, pr1.oy - pc1.oy), Pm,
+                    make_float2(G0, G1), v, q);
+      s.K[pr_0][pc_0] = v.x;
+      s.K[pc_0][pr_0] = v.x;
+      s.K[pr_1][pc_1] = v.y;
+      s.K[pc_1][pr_1] = v.y;
+      *reinterpret_cast<float2*>(&s.qd[q0]) = q;
+    }
+  } else {
+    for (int q = lane; q < bs->ndpairs; q += 32) {
+      const uint32_t rc = bs->dpairs[q];
+      const int r = rc & 0xff, c = (rc >> 8) & 0xff;
+      const Pos<T> pr = s.pos[r], pc = s.pos[c];
+      T P, G, Qa, L, v, qq;
+      pair_lag<T, FAST>(th, lagd, lagf, tab, allint, pr.td, pc.td, s.tt[r], s.tt[c], P, G, Qa, L);
+      pair_cov<T, NU>(pr.ox - pc.ox, pr.oy - pc.oy, P, G, v, qq);
+      const bool ok = (pr.valid & pc.valid) != 0;
+      v = ok ? v : T(0);
+      s.K[r][c] = v;
+      s.K[c][r] = v;
+      s.qd[q] = ok ? qq : T(0);
+      if constexpr (!MIXED) s.qd[2 * PM + q] = v;
+    }
   }
 }
 
@@ -380,7 +478,53 @@ __device__ __forceinline__ void adj_tiled(const DevTheta& th, const LagD* lagd, 
   constexpr int TS = TileShape<PM>::TS;
   constexpr bool MIXED = std::is_same<T, float>::value;
   const T* qt = MIXED ? reinterpret_cast<const T*>(&s.q1[0]) : reinterpret_cast<const T*>(&s.xe[0][0]);
-  if (lane < 28) {
+  if constexpr (MIXED && TS % 2 == 0) {
+    // column pairs (b, b + 1) on packed FP32 pairs, even and odd columns in
+    // separate partial sums; g2 and g3 accumulate with the sign taken out
+    constexpr int TH = TS / 2;
+    if (lane < 28) {
+      float2 ac2[TH], bc2[TH];
+      int tc[TS];
+#pragma unroll
+      for (int u = 0; u < TH; ++u) {
+        ac2[u] = make_float2(s.ab[tC * TS + 2 * u][0], s.ab[tC * TS + 2 * u + 1][0]);
+        bc2[u] = make_float2(s.ab[tC * TS + 2 * u][1], s.ab[tC * TS + 2 * u + 1][1]);
+        tc[2 * u] = s.pos[tC * TS + 2 * u].td;
+        tc[2 * u + 1] = s.pos[tC * TS + 2 * u + 1].td;
+      }
+      const float2 pe2 = make_float2(pexp, pexp), hg2 = make_float2(hg, hg), half2 = make_float2(0.5f, 0.5f);
+      float2 G0 = make_float2(0.f, 0.f), G1 = G0, G2 = G0, G3 = G0;
+#pragma unroll
+      for (int a = 0; a < TS; ++a) {
+        const T ara = s.ab[tR * TS + a][0], bra = s.ab[tR * TS + a][1];
+        const int tra = s.pos[tR * TS + a].td;
+        T kv[TS];
+        ld_row<T, TS>(kv, &s.K[tR * TS + a][tC * TS]);
+        const T ra = c1 * ara - hc2 * bra, rb = -hc2 * ara;
+        const float2 ra2 = make_float2(ra, ra), rb2 = make_float2(rb, rb);
+#pragma unroll
+        for (int u = 0; u < TH; ++u) {
+          T P0, G0_, Qa0, L0, P1, G1_, Qa1, L1;
+          pair_lag<T, FAST>(th, lagd, lagf, tab, allint, tra, tc[2 * u], s.tt[tR * TS + a], s.tt[tC * TS + 2 * u], P0,
+                            G0_, Qa0, L0);
+          pair_lag<T, FAST>(th, lagd, lagf, tab, allint, tra, tc[2 * u + 1], s.tt[tR * TS + a],
+                            s.tt[tC * TS + 2 * u + 1], P1, G1_, Qa1, L1);
+          const float2 Kv = make_float2(kv[2 * u], kv[2 * u + 1]);
+          const float2 Xv = make_float2(qt[(a * TS + 2 * u) * 32 + lane], qt[(a * TS + 2 * u + 1) * 32 + lane]);
+          const float2 w = __ffma2_rn(ra2, ac2[u], __fmul2_rn(rb2, bc2[u]));
+          const float2 w2 = __fadd2_rn(w, w);  // both (r, c) and (c, r)
+          G0 = __ffma2_rn(w2, Kv, G0);
+          G1 = __ffma2_rn(w2, Xv, G1);
+          G2 = __ffma2_rn(__fmul2_rn(w2, make_float2(Qa0, Qa1)), __ffma2_rn(pe2, Kv, __fmul2_rn(hg2, Xv)), G2);
+          G3 = __ffma2_rn(__fmul2_rn(w2, make_float2(L0, L1)), __ffma2_rn(half2, Xv, Kv), G3);
+        }
+      }
+      g0 += G0.x + G0.y;
+      g1 += G1.x + G1.y;
+      g2 -= G2.x + G2.y;
+      g3 -= G3.x + G3.y;
+    }
+  } else if (lane < 28) {
     T ac[TS], bc[TS];
     int tc[TS];
 #pragma unroll
@@ -416,18 +560,48 @@ __device__ __forceinline__ void adj_tiled(const DevTheta& th, const LagD* lagd, 
       }
     }
   }
-  for (int q = lane; q < bs->ndpairs; q += 32) {
-    const uint32_t rc = bs->dpairs[q];
-    const int r = rc & 0xff, c = (rc >> 8) & 0xff;
-    T P, G, Qa, L;
-    pair_lag<T, FAST>(th, lagd, lagf, tab, allint, s.pos[r].td, s.pos[c].td, s.tt[r], s.tt[c], P, G, Qa, L);
-    const T ar = s.ab[r][0], br = s.ab[r][1], ac = s.ab[c][0], bc = s.ab[c][1];
-    const T Kv = MIXED ? s.K[r][c] : s.qd[2 * PM + q], Xv = s.qd[q];
-    const T w2 = T(2) * (ar * (c1 * ac - hc2 * bc) - hc2 * br * ac);
-    g0 = fma(w2, Kv, g0);
-    g1 = fma(w2, Xv, g1);
-    g2 = fma(w2 * Qa, -pexp * Kv - hg * Xv, g2);
-    g3 = fma(-w2 * L, Kv + T(0.5) * Xv, g3);
+  if constexpr (MIXED && TS % 2 == 0) {
+    // the diagonal-block pairs two per lane, as in cov_tiled
+    const int q0 = 2 * lane;
+    if (q0 < bs->ndpairs) {
+      const uint32_t rc0 = bs->dpairs[q0], rc1 = bs->dpairs[q0 + 1];
+      const int pr_0 = rc0 & 0xff, pc_0 = (rc0 >> 8) & 0xff, pr_1 = rc1 & 0xff, pc_1 = (rc1 >> 8) & 0xff;
+      T P0, G0_, Qa0, L0, P1, G1_, Qa1, L1;
+      pair_lag<T, FAST>(th, lagd, lagf, tab, allint, s.pos[pr_0].td, s.pos[pc_0].td, s.tt[pr_0], s.tt[pc_0], P0, G0_,
+                        Qa0, L0);
+      pair_lag<T, FAST>(th, lagd, lagf, tab, allint, s.pos[pr_1].td, s.pos[pc_1].td, s.tt[pr_1], s.tt[pc_1], P1, G1_,
+                        Qa1, L1);
+      const float2 ar = make_float2(s.ab[pr_0][0], s.ab[pr_1][0]), br = make_float2(s.ab[pr_0][1], s.ab[pr_1][1]);
+      const float2 ac = make_float2(s.ab[pc_0][0], s.ab[pc_1][0]), bc = make_float2(s.ab[pc_0][1], s.ab[pc_1][1]);
+      const float2 Kv = make_float2(s.K[pr_0][pc_0], s.K[pr_1][pc_1]);
+      const float2 Xv = *reinterpret_cast<const float2*>(&s.qd[q0]);
+      // w = ar (c1 ac - hc2 bc) - hc2 br ac, doubled
+      const float2 t = __ffma2_rn(make_float2(c1, c1), ac, __fmul2_rn(make_float2(-hc2, -hc2), bc));
+      const float2 w = __ffma2_rn(ar, t, __fmul2_rn(__fmul2_rn(make_float2(-hc2, -hc2), br), ac));
+      const float2 w2 = __fadd2_rn(w, w);
+      const float2 G0 = __fmul2_rn(w2, Kv), G1 = __fmul2_rn(w2, Xv);
+      const float2 G2 = __fmul2_rn(__fmul2_rn(w2, make_float2(Qa0, Qa1)),
+                                   __ffma2_rn(make_float2(pexp, pexp), Kv, __fmul2_rn(make_float2(hg, hg), Xv)));
+      const float2 G3 = __fmul2_rn(__fmul2_rn(w2, make_float2(L0, L1)), __ffma2_rn(make_float2(0.5f, 0.5f), Xv, Kv));
+      g0 += G0.x + G0.y;
+      g1 += G1.x + G1.y;
+      g2 -= G2.x + G2.y;
+      g3 -= G3.x + G3.y;
+    }
+  } else {
+    for (int q = lane; q < bs->ndpairs; q += 32) {
+      const uint32_t rc = bs->dpairs[q];
+      const int r = rc & 0xff, c = (rc >> 8) & 0xff;
+      T P, G, Qa, L;
+      pair_lag<T, FAST>(th, lagd, lagf, tab, allint, s.pos[r].td, s.pos[c].td, s.tt[r], s.tt[c], P, G, Qa, L);
+      const T ar = s.ab[r][0], br = s.ab[r][1], ac = s.ab[c][0], bc = s.ab[c][1];
+      const T Kv = MIXED ? s.K[r][c] : s.qd[2 * PM + q], Xv = s.qd[q];
+      const T w2 = T(2) * (ar * (c1 * ac - hc2 * bc) - hc2 * br * ac);
+      g0 = fma(w2, Kv, g0);
+      g1 = fma(w2, Xv, g1);
+      g2 = fma(w2 * Qa, -pexp * Kv - hg * Xv, g2);
+      g3 = fma(-w2 * L, Kv + T(0.5) * Xv, g3);
+    }
   }
 }
 
