@@ -917,8 +917,18 @@ static vst_status vif_factor_T(const vst_points* pts, const vst_theta* theta, in
   T* gram = reinterpret_cast<T*>(vbase + V.gram);
   if (n > 0) {
     ProfileScope ps(kProfVifGram, st);
-    launch_gram(m + 1, nn, nn_cnt, n, m, k, U, reinterpret_cast<const double*>(vbase + V.r), theta->sigma1sq, gram,
-                st);
+    const double* rr = reinterpret_cast<const double*>(vbase + V.r);
+    if constexpr (std::is_same<T, float>::value) {
+      // blocks of 32 positions: the tensor-core kernel (vif_gram_tc.cu)
+      if (padded_pm(m + 1) == 32) {
+        s = gram_tc_rows(nn, nn_cnt, n, m, k, U, rr, theta->sigma1sq, gram, hdr, st);
+        if (s != VST_OK) return s;
+      } else {
+        launch_gram(m + 1, nn, nn_cnt, n, m, k, U, rr, theta->sigma1sq, gram, st);
+      }
+    } else {
+      launch_gram(m + 1, nn, nn_cnt, n, m, k, U, rr, theta->sigma1sq, gram, st);
+    }
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "gram kernel");

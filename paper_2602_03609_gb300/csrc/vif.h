@@ -61,6 +61,11 @@ vst_status tc_gram(const float* A, int64_t lda, const float* B, int64_t ldb, int
 vst_status tc_syrk(const float* A, int64_t lda, int64_t n, int kc, double* C, void* opa, double* part,
                    WsHeader* hdr, cudaStream_t st);
 
+// mixed VIF: the per-row residual Gram gram[i][pair] (FP32 [n][528]) for
+// local blocks of 32 positions on the tensor cores (vif_gram_tc.cu)
+vst_status gram_tc_rows(const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, const float* U,
+                        const double* r, double s1, float* gram, WsHeader* hdr, cudaStream_t st);
+
 // 2-D TMA map of a row-major BF16 matrix rows x cols (cols contiguous, a
 // multiple of 8), box 64 columns x box_rows rows, 128-byte swizzle (vif_tc.cu)
 bool tc_make_map_bf16(CUtensorMap* map, const void* ptr, uint64_t rows, uint64_t cols, uint32_t box_rows);

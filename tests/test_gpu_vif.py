@@ -192,3 +192,30 @@ def test_vif_grad_tensor_core_gram_many_drains(env):
     g64, gm = g64.cpu().numpy(), gm.cpu().numpy()
     print("grad mixed - fp64 per n", (gm - g64) / n)
     assert np.all(np.abs(gm - g64) <= 1e-4 * np.abs(g64) + 1e-6 * n), (gm, g64)
+
+
+@pytest.mark.parametrize("k,m", [(60, 30), (130, 26)])
+def test_vif_mixed_32_position_blocks(env, k, m):
+    """Local blocks of 32 positions (m = 24..31), whose per-row residual Gram
+    runs on the tensor cores (groups of four rows, 64-column chunks; here
+    410 rows: the last group ragged, and for k = 130 a ragged last chunk):
+    the mixed NLL and NLL + gradient against the oracle's Woodbury NLL and
+    forward-mode gradient, |dNLL|/n <= 1e-6, |dg_j| <= 1e-4 |g_j| + 1e-6 n."""
+    torch, vst = env
+    xy, t, th, xyk, tk, y = problem(41, 10, k, seed=k + m, order="time")
+    n = t.shape[0]
+    U, r = ovif.lowrank(xy, t, xyk, tk, th)
+    nn_o, cnt_o, _, _ = ovif.knn(xy, t, th, U, r, m)
+    v_o, g_o = ovif.nll_grad(xy, t, th, xyk, tk, m, nn_o, cnt_o, y)
+    xy_d, t_d, y_d, xyk_d, tk_d, nn_d, cnt_d = dev(torch, xy, t, y, xyk, tk, nn_o, cnt_o)
+    ind = (xyk_d, tk_d)
+    ws = vst.Workspace(n, m, k, vif_grad=True)
+    for prec in (vst.MIXED, vst.MIXED_BF16X3):
+        v = vst.vecchia_nll(xy_d, t_d, th, m, nn_d, cnt_d, y_d, precision=prec, ws=ws, inducing=ind)
+        vst.vst_workspace_status(ws)
+        assert abs(v.item() - v_o) / n <= 1e-6, (prec, abs(v.item() - v_o) / n)
+        v2, g = vst.vecchia_nll_grad(xy_d, t_d, th, m, nn_d, cnt_d, y_d, precision=prec, ws=ws, inducing=ind)
+        vst.vst_workspace_status(ws)
+        assert v2.item() == v.item()
+        err = np.abs(g.cpu().numpy() - g_o)
+        assert np.all(err <= 1e-4 * np.abs(g_o) + 1e-6 * n), (prec, g.cpu().numpy(), g_o)
