@@ -921,7 +921,9 @@ static vst_status vif_factor_T(const vst_points* pts, const vst_theta* theta, in
     if constexpr (std::is_same<T, float>::value) {
       // blocks of 32 positions: the tensor-core kernel (vif_gram_tc.cu)
       if (padded_pm(m + 1) == 32) {
-        s = gram_tc_rows(nn, nn_cnt, n, m, k, U, rr, theta->sigma1sq, gram, hdr, st);
+        // (the operand-part buffers of the low rank are free once U is formed)
+        s = gram_tc_rows(nn, nn_cnt, n, m, k, U, reinterpret_cast<__nv_bfloat16*>(vbase + V.Ap),
+                         reinterpret_cast<float*>(vbase + V.uscale), gram, hdr, st);
         if (s != VST_OK) return s;
       } else {
         launch_gram(m + 1, nn, nn_cnt, n, m, k, U, rr, theta->sigma1sq, gram, st);

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -62,9 +63,10 @@ vst_status tc_syrk(const float* A, int64_t lda, int64_t n, int kc, double* C, vo
                    WsHeader* hdr, cudaStream_t st);
 
 // mixed VIF: the per-row residual Gram gram[i][pair] (FP32 [n][528]) for
-// local blocks of 32 positions on the tensor cores (vif_gram_tc.cu)
+// local blocks of 32 positions on the tensor cores (vif_gram_tc.cu); parts:
+// scratch of 3 n vif_kp(k) BF16 values, uscale: n ceil(k / 64) floats
 vst_status gram_tc_rows(const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, const float* U,
-                        const double* r, double s1, float* gram, WsHeader* hdr, cudaStream_t st);
+                        __nv_bfloat16* parts, float* uscale, float* gram, WsHeader* hdr, cudaStream_t st);
 
 // 2-D TMA map of a row-major BF16 matrix rows x cols (cols contiguous, a
 // multiple of 8), box 64 columns x box_rows rows, 128-byte swizzle (vif_tc.cu)

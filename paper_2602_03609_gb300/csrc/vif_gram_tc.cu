@@ -1,36 +1,38 @@
 // The mixed VIF's per-row residual Gram on the tensor cores (Sect. 4.3: the
-// residual covariance C - U U^T of each local block).  For row i with
-// positions p (its neighbours, unused positions, and i itself at the last
-// position L), V_p = U_p - U_i for the neighbours and V_L = U_i; the block
-// S = V V^T (32 x 32) gives
-//   U_p . U_q = |U_i|^2 + w_p + w_q + S_pq,  w_p = S_Lp,  |U_i|^2 = sigma1^2 - r_i,
-// formed in double-float and rounded once, as in the SIMT kernel
-// (gram_delta_kernel, vif.cu), whose accumulation this replaces for PM = 32.
+// residual covariance C - U U^T of each local block): for row i and the
+// positions p, q of its block (its neighbours, unused positions, and i
+// itself at the last position L), gram[i][pair(p, q)] = U_p . U_q, for local
+// blocks of 32 positions.
 //
-// Four rows make one 128-row MMA operand (row 32 b + p = position p of row
-// b); S of the four rows are the diagonal 32 x 32 blocks of the 128 x 128
-// product, the rest is computed and not read.  The columns (the k inducing
-// points) go in chunks of 64.  Per chunk each position gets the exponent E
-// of its largest |V| there and its 64 values become three 9-bit fixed-point
-// BF16 parts of 2^(E - 8) (as the contractions over the points in
-// vif_tc.cu): the leading part products are integers below 2^16, a chunk's
-// sum of 64 an integer below 2^22, exact in the FP32 accumulator whatever
-// its rounding.  The correction products go to a second accumulator.  Each
-// chunk is drained on its own: the diagonal blocks are scaled by
+// usplit_kernel cuts every row of U once into three 9-bit fixed-point BF16
+// parts per 64-column chunk: with E the exponent of the chunk's largest
+// |U|, x = U 2^(8 - E) = s_0 + 2^-9 s_1 + 2^-18 s_2 + (below 2^-19), integers
+// |s_j| <= 256 exact in BF16 (as the contractions over the points in
+// vif_tc.cu); the parts go to [3][n][kp] and 2^(E - 8) to uscale[row][chunk].
+//
+// gram_tc_rows_kernel: four rows make one 128-row MMA operand (row 32 b + p =
+// position p of row b); their blocks S = V V^T are the diagonal 32 x 32
+// blocks of the 128 x 128 product, the rest is computed and not read.  Per
+// chunk the leading part products are integers below 2^16 and the chunk's
+// sum of 64 an integer below 2^22, exact in the FP32 accumulator whatever its
+// rounding; the correction products go to a second accumulator.  Each chunk
+// is drained on its own: the diagonal blocks are scaled by
 // 2^(E_p + E_q - 16) (exact) and added to double-float sums in registers.
+// (The SIMT kernel for other block sizes, gram_delta_kernel in vif.cu, works
+// around the row's own vector, U_p - U_i; on the tensor cores the exponent
+// per row and chunk keeps the direct form's error at |dNLL|/n ~1e-8 on the
+// bench workload, with no bias.)
 //
 // CTA of 13 warps, persistent over groups of four rows:
-//   warps 0-7  convert: warp w takes row w % 4 of every other chunk (w / 4
-//              the chunk parity); each load instruction reads two of the 32
-//              U rows 256 bytes at a time (coalesced), a position's maximum
-//              is reduced over the 16 lanes holding it, and the parts go to
-//              a shared-memory stage in the 128-byte-swizzled K-major
-//              layout the MMA reads
+//   warps 0-7  copy: warp w takes every other chunk (w / 4 the chunk parity);
+//              eight lanes copy one position's 128-byte row of a part, 16
+//              rows a pass, into a shared-memory stage in the 128-byte-
+//              swizzled K-major layout the MMA reads, with the rows' scales
 //   warps 8-11 drain TMEM lanes 32 b.. (row b = warp % 4) after each chunk;
-//              at the end of a group the E-step above, writing gram[i][pair]
+//              at the end of a group they write gram[i][pair]
 //   warp 12    TMEM allocation, tcgen05.mma issue (one lane), commits
-// Stages are handed over with mbarriers (converters -> MMA: full, count 4;
-// MMA -> converters: empty, by commit; MMA -> drains: accf, by commit;
+// Stages are handed over with mbarriers (copiers -> MMA: full, count 4;
+// MMA -> copiers: empty, by commit; MMA -> drains: accf, by commit;
 // drains -> MMA: acce, count 4).  Every wait is limited in time; a wait that
 // runs out reports VST_ETIMEOUT and the CTA still frees its tensor memory.
 #include <cuda_bf16.h>
@@ -94,13 +96,45 @@ __device__ __forceinline__ void gsplit2(float2 x, uint32_t& w0, uint32_t& w1, ui
   w2 = *reinterpret_cast<const uint32_t*>(&b2);
 }
 
+// parts [3][n][kp] (BF16) and scales uscale[n][nchunk] of U [n][k]: one warp
+// per row, lane l holds columns 2 l, 2 l + 1 of each 64-column chunk
+__global__ void __launch_bounds__(256) usplit_kernel(const float* U, int64_t n, int k, int kp, int nchunk,
+                                                     __nv_bfloat16* parts, float* uscale) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool vec = (k & 1) == 0;
+  const int64_t pstride = n * (int64_t)kp;
+  for (int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; i < n; i += nw) {
+    const float* u = U + i * (int64_t)k;
+    for (int c = 0; c < nchunk; ++c) {
+      const int col = c * kGKc + 2 * lane;
+      float2 v = make_float2(0.f, 0.f);
+      if (vec && col + 2 <= k) v = __ldg(reinterpret_cast<const float2*>(u + col));
+      else {
+        if (col < k) v.x = __ldg(u + col);
+        if (col + 1 < k) v.y = __ldg(u + col + 1);
+      }
+      const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(fmaxf(fabsf(v.x), fabsf(v.y))));
+      const int E = gexp_b(mb >> 23);
+      const float scale = __int_as_float((127 + 8 - E) << 23);
+      uint32_t w0, w1, w2;
+      gsplit2(__fmul2_rn(v, make_float2(scale, scale)), w0, w1, w2);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(parts + i * (int64_t)kp + col);
+      dst[0] = w0;
+      dst[pstride / 2] = w1;
+      dst[pstride] = w2;
+      if (lane == 0) uscale[i * nchunk + c] = __int_as_float((127 + E - 8) << 23);
+    }
+  }
+}
+
 // the six kept part products (a, b): (0,0) leading; (0,1) (1,0) (0,2) (1,1) (2,0)
 __device__ __forceinline__ int gpa(int t) { return t == 2 ? 1 : t == 4 ? 1 : t == 5 ? 2 : 0; }
 __device__ __forceinline__ int gpb(int t) { return t == 1 ? 1 : t == 3 ? 2 : t == 4 ? 1 : 0; }
 
 __global__ void __launch_bounds__(kGThreads, 1)
-    gram_tc_rows_kernel(const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, const float* U,
-                        const double* r, double s1, float* gram, WsHeader* hdr) {
+    gram_tc_rows_kernel(const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, int kp,
+                        const __nv_bfloat16* parts, const float* uscale, float* gram, WsHeader* hdr) {
   extern __shared__ unsigned char g_smem[];
   const uint32_t raw = umma::smem_u32(g_smem);
   const uint32_t sbase = (raw + 1023u) & ~1023u;
@@ -148,28 +182,36 @@ __global__ void __launch_bounds__(kGThreads, 1)
   };
 
   if (warp < 8) {
-    // ---- converters: row b = warp % 4, chunks t with t % 2 = warp / 4.
-    // Load instruction j reads positions 2 j (lanes 0-15) and 2 j + 1 (lanes
-    // 16-31), four columns per lane; position p's maximum is reduced over its
-    // 16 lanes.
-    const int b = warp & 3, par = warp >> 2;
-    const int half = lane >> 4, cl = lane & 15;  // position parity, column quad
-    const bool vec = (k & 3) == 0;
+    // ---- copiers: chunks t with t % 2 = warp / 4; set lane L = 32 (warp % 4)
+    // + lane copies 16 bytes (unit L % 8) of rows 16 pass + L / 8, pass 0..7:
+    // positions L / 8 and 16 + L / 8 of the four rows of the group
+    const int par = warp >> 2;
+    const int L = 32 * (warp & 3) + lane;
+    const int unit = L & 7, rsub = L >> 3;
+    const int64_t pstride = n * (int64_t)kp;
     int64_t cur_g = -1;
-    int myidx = -1;  // U row of position `lane` (-1: unused)
-    int64_t i = 0;
+    int ridx[8];  // U row of tile row 16 pass + rsub (-1: zeros)
     for (int64_t t = par; t < nt; t += 2) {
       const int64_t gi = t / nchunk;
       const int c = (int)(t % nchunk);
       if (gi != cur_g) {
         cur_g = gi;
-        i = (blockIdx.x + gi * gridDim.x) * kGRows + b;
-        myidx = -1;
-        if (i < n) {
-          const int cnt = min(max(nn_cnt[i], 0), min(m, kGL));
-          if (lane < cnt) myidx = nn[i * m + lane];
-          if (lane == kGL) myidx = (int)i;
-          if (myidx < 0 || myidx > i) myidx = -1;
+#pragma unroll
+        for (int ps = 0; ps < 8; ++ps) {
+          const int row = 16 * ps + rsub;
+          const int b = row >> 5, pos = row & 31;
+          const int64_t i = (blockIdx.x + gi * gridDim.x) * kGRows + b;
+          int v = -1;
+          if (i < n) {
+            if (pos == kGL) {
+              v = (int)i;
+            } else {
+              const int cnt = min(max(nn_cnt[i], 0), min(m, kGL));
+              if (pos < cnt) v = nn[i * m + pos];
+              if (v < 0 || v > i) v = -1;
+            }
+          }
+          ridx[ps] = v;
         }
       }
       const int s = (int)(t % kGStages);
@@ -178,79 +220,34 @@ __global__ void __launch_bounds__(kGThreads, 1)
         ok = false;
         break;
       }
-      const int col = c * kGKc + 4 * cl;
-      // U_i at this lane's four columns (unused positions and the row's own
-      // position subtract nothing)
-      float4 ui = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (i < n) {
-        const float* pu = U + i * (int64_t)k + col;
-        if (vec && col + 4 <= k) ui = __ldg(reinterpret_cast<const float4*>(pu));
-        else if (col < k) {
-          ui.x = __ldg(pu);
-          if (col + 1 < k) ui.y = __ldg(pu + 1);
-          if (col + 2 < k) ui.z = __ldg(pu + 2);
-          if (col + 3 < k) ui.w = __ldg(pu + 3);
-        }
-      }
       unsigned char* st = gb + s * kGStageBytes;
-      // all 16 loads of the chunk in flight before any is used
-      float4 av[16];
-      unsigned sub = 0u;  // bit j: position 2 j + half is a neighbour (V = U_p - U_i)
-      const bool fast = vec && c * kGKc + kGKc <= k;  // the whole chunk inside the k columns
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int ridx = __shfl_sync(0xffffffffu, myidx, 2 * j + half);
-        av[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ridx >= 0 && 2 * j + half != kGL) sub |= 1u << j;
-        if (ridx >= 0) {
-          const float* pa = U + (int64_t)ridx * k + col;
-          if (fast) {
-            av[j] = __ldg(reinterpret_cast<const float4*>(pa));
-          } else if (col < k) {
-            av[j].x = __ldg(pa);
-            if (col + 1 < k) av[j].y = __ldg(pa + 1);
-            if (col + 2 < k) av[j].z = __ldg(pa + 2);
-            if (col + 3 < k) av[j].w = __ldg(pa + 3);
-          }
-        }
-      }
-      // V, and each position's largest magnitude as its biased exponent:
-      // four positions per word (one byte each), reduced over the 16 lanes
-      // of a position with per-byte maxima
-      unsigned ebw[4] = {0u, 0u, 0u, 0u};
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        float4 a = av[j];
-        if (sub & (1u << j)) {  // (unused positions stay zero, the row's own is U_i)
-          const float2 d0 = fsub2(make_float2(a.x, a.y), make_float2(ui.x, ui.y));
-          const float2 d1 = fsub2(make_float2(a.z, a.w), make_float2(ui.z, ui.w));
-          a = make_float4(d0.x, d0.y, d1.x, d1.y);
-          av[j] = a;
-        }
-        const float lm = fmaxf(fmaxf(fabsf(a.x), fabsf(a.y)), fmaxf(fabsf(a.z), fabsf(a.w)));
-        ebw[j >> 2] |= (__float_as_uint(lm) >> 23) << (8 * (j & 3));
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) ebw[q] = __vmaxu4(ebw[q], __shfl_xor_sync(0xffffffffu, ebw[q], o));
       const int slot = (int)(t % kGExpSlots);
+      const int col = c * kGKc + 8 * unit;
+      // all 24 loads of the lane (and the rows' scales) in flight before the stores
+      uint4 d[3][8];
+      float sc[8];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int pos = 2 * j + half;
-        const int E = gexp_b((ebw[j >> 2] >> (8 * (j & 3))) & 0xffu);
-        const float scale = __int_as_float((127 + 8 - E) << 23);
-        const float2 sc2 = make_float2(scale, scale);
-        uint2 o0, o1, o2;
-        gsplit2(__fmul2_rn(make_float2(av[j].x, av[j].y), sc2), o0.x, o1.x, o2.x);
-        gsplit2(__fmul2_rn(make_float2(av[j].z, av[j].w), sc2), o0.y, o1.y, o2.y);
-        const int row = 32 * b + pos;
-        // this lane's 8 bytes: 16-byte chunk cl / 2 of the row, half cl % 2
-        const int off = (row >> 3) * 1024 + (row & 7) * 128 + (((cl >> 1) ^ (row & 7)) << 4) + ((cl & 1) << 3);
-        *reinterpret_cast<uint2*>(st + off) = o0;
-        *reinterpret_cast<uint2*>(st + kGPartBytes + off) = o1;
-        *reinterpret_cast<uint2*>(st + 2 * kGPartBytes + off) = o2;
-        if (cl == 0) sfac[slot * 128 + row] = __int_as_float((127 + E - 8) << 23);
+      for (int ps = 0; ps < 8; ++ps)
+        sc[ps] = (unit == 0 && ridx[ps] >= 0) ? __ldg(uscale + (int64_t)ridx[ps] * nchunk + c) : 0.0f;
+#pragma unroll
+      for (int ps = 0; ps < 8; ++ps) {
+        const __nv_bfloat16* src = parts + (int64_t)(ridx[ps] >= 0 ? ridx[ps] : 0) * kp + col;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          d[j][ps] = make_uint4(0u, 0u, 0u, 0u);
+          if (ridx[ps] >= 0) d[j][ps] = __ldg(reinterpret_cast<const uint4*>(src + j * pstride));
+        }
+      }
+#pragma unroll
+      for (int ps = 0; ps < 8; ++ps) {
+        const int row = 16 * ps + rsub;
+        unsigned char* dst = st + (row >> 3) * 1024 + (row & 7) * 128 + ((unit ^ (row & 7)) << 4);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) *reinterpret_cast<uint4*>(dst + j * kGPartBytes) = d[j][ps];
+      }
+      if (unit == 0) {
+#pragma unroll
+        for (int ps = 0; ps < 8; ++ps) sfac[slot * 128 + 16 * ps + rsub] = sc[ps];
       }
       fence_proxy_async_smem();
       __syncwarp();
@@ -322,20 +319,10 @@ __global__ void __launch_bounds__(kGThreads, 1)
       __syncwarp();
       if (i < n) {
         constexpr int NPAIR = kGP * (kGP + 1) / 2;
-        const df s1m = df_split(s1 - r[i]);  // |U_i|^2 = sigma1^2 - r_i
         for (int e = lane; e < NPAIR; e += 32) {
           int pa, pb;
           pair_of<kGP>(e, pa, pb);  // pa >= pb
-          df v = {0.f, 0.f};
-          if (pa != kGL) {
-            v = df_two_sum(S[kGL * kGSStride + pa], S[kGL * kGSStride + pb]);
-            const df tt = df_two_sum(v.hi, S[pa * kGSStride + pb]);
-            v = df{tt.hi, v.lo + tt.lo};
-          } else if (pb != kGL) {
-            v = df{S[kGL * kGSStride + pb], 0.f};
-          }
-          const df tt = df_two_sum(v.hi, s1m.hi);
-          gram[i * NPAIR + e] = tt.hi + (tt.lo + (v.lo + s1m.lo));
+          gram[i * NPAIR + e] = S[pa * kGSStride + pb];
         }
       }
       __syncwarp();
@@ -390,18 +377,25 @@ __global__ void __launch_bounds__(kGThreads, 1)
 }  // namespace
 
 // gram[i][e] (FP32, [n][32 * 33 / 2]) of the mixed VIF for local blocks of 32
-// positions (m + 1 <= 32 rounded up to 32), on the tensor cores.
+// positions (m + 1 <= 32 rounded up to 32), on the tensor cores.  parts:
+// 3 n kp BF16 values (kp = k rounded up to 256); uscale: n ceil(k / 64) floats.
 vst_status gram_tc_rows(const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, const float* U,
-                        const double* r, double s1, float* gram, WsHeader* hdr, cudaStream_t st) {
+                        __nv_bfloat16* parts, float* uscale, float* gram, WsHeader* hdr, cudaStream_t st) {
   if (n <= 0 || k <= 0) return VST_OK;
-  cudaError_t e = cudaFuncSetAttribute(gram_tc_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
-  if (e != cudaSuccess) return cuda_fail(e, "tensor-core row Gram attributes");
+  const int kp = vif_kp(k);
+  const int nchunk = (k + kGKc - 1) / kGKc;
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  usplit_kernel<<<(unsigned)std::min<int64_t>((n + 7) / 8, (int64_t)std::max(1, sms) * 32), 256, 0, st>>>(
+      U, n, k, kp, nchunk, parts, uscale);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "fixed-point split of U");
+  e = cudaFuncSetAttribute(gram_tc_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGSmem);
+  if (e != cudaSuccess) return cuda_fail(e, "tensor-core row Gram attributes");
   const int64_t ngroups = (n + kGRows - 1) / kGRows;
   const int grid = (int)std::min<int64_t>(ngroups, std::max(1, sms));
-  gram_tc_rows_kernel<<<grid, kGThreads, kGSmem, st>>>(nn, nn_cnt, n, m, k, U, r, s1, gram, hdr);
+  gram_tc_rows_kernel<<<grid, kGThreads, kGSmem, st>>>(nn, nn_cnt, n, m, k, kp, parts, uscale, gram, hdr);
   e = cudaGetLastError();
   return e == cudaSuccess ? VST_OK : cuda_fail(e, "tensor-core row Gram");
 }

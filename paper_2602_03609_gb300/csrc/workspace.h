@@ -25,6 +25,7 @@ constexpr int kVifDayBlocks = 256;     // day-range reduction blocks
 
 struct VifLayout {
   size_t S, X, U, r, gram, WE, logd, syrk, G, M, v, z, dinfo, dtab;
+  size_t uscale;  // mixed: per (U row, 64-column chunk) scale of its fixed-point parts
   size_t Ap, Bp, zf;  // tensor-core low rank: BF16 operand parts, inducing coordinates
   size_t rpart;       // per (row, column tile) sums of U_ic^2 from the GEMM epilogue
   size_t dpart;       // day-range partials
@@ -99,6 +100,7 @@ inline VifLayout vif_layout(int64_t n, int m, int64_t k) {
   L.z = take(sizeof(double) * (kk + 2));
   L.dinfo = take(sizeof(int64_t) * 4);
   L.dtab = take(sizeof(float) * 2 * kk * (size_t)kVifMaxDays);
+  L.uscale = take(sizeof(float) * nn * ((kk + 63) / 64));
   const size_t kp = (size_t)vif_kp((int64_t)kk);
   // (the residual neighbour search keeps U in FP32 and then in BF16 [n][k
   // rounded up to 64] here; the 1 KiB covers the alignment between the two)
