@@ -20,6 +20,8 @@
 //   rdiag_kernel<T>      r_i = sigma1^2 - ||U_i||^2
 //   gram64_kernel        FP64: per-row U_p . U_q over the local block (fed to the row kernel)
 //   gram_delta_kernel    mixed: per-row U_p . U_q, accumulated without cancellation
+//                        (blocks of 8, 16, 24 positions; 32-position blocks go to the
+//                        tensor-core kernel of vif_gram_tc.cu)
 //   wvec_kernel<T>       rows of [W e] and sum log D_i
 //   syrk_kernel<double>  partial [W e]^T [W e] over row chunks, then a fixed-order sum
 //                        (FP64 form; the mixed form's is tc_syrk on the tensor cores)
