@@ -872,7 +872,8 @@ vst_status vif_lowrank(const vst_points* pts, const vst_theta* theta, const vst_
   return lowrank_T<float>(pts, theta, ind, nu, precision == VST_MIXED_BF16X3 ? 3 : 6, vbase, V, hdr, st);
 }
 
-// FP64: gram = U_p . U_q;  mixed: gram = U_p . U_q - sigma1^2 (see gram_delta_kernel)
+// gram = U_p . U_q for the pairs of each local block (FP64; mixed: accumulated without
+// cancellation and rounded once to FP32, see gram_delta_kernel)
 static void launch_gram(int pm, const int32_t* nn, const int32_t* nn_cnt, int64_t n, int m, int k, const double* U,
                         const double* r, double s1, double* gram, cudaStream_t st) {
   (void)r;
