@@ -426,6 +426,26 @@ def vif_leg(vst, torch, dev, w, nv=30000, full=True):
                                           "flops_per_launch": flops, "split_products": terms,
                                           "issued_frac": terms * flops / (gemm_ms * 1e-3) / 1e12 / BF16_PEAK,
                                           "peak_note": "measured cuBLAS bf16 (burst)"}}
+        # the per-row residual Gram (32-position blocks, tensor cores, with the
+        # split of U): algorithmic 2 k flops per entry of the 32 x 33 / 2 lower
+        # triangle; issued: six part products on 128 x 128 tiles per four rows
+        # (the diagonal blocks read are a quarter of each tile)
+        gram_ms, syrk_ms = parts["gram"][1], parts["syrk"][1]
+        pm = 32
+        gfl = float(w.n) * pm * (pm + 1) / 2 * 2 * k
+        gissued = 6.0 * 128 * 128 * (-(-k // 256) * 256) * 2 * (-(-w.n // 4))
+        # [W e]^T [W e]: algorithmic n kc (kc + 1) flops (symmetric, kc = k + 1);
+        # issued: six products on the lower triangle of 128 x 128 tiles
+        kc = k + 1
+        sfl = float(w.n) * kc * (kc + 1)
+        tt = -(-kc // 256) * 256 // 128
+        sissued = 6.0 * tt * (tt + 1) / 2 * 128 * 128 * (-(-w.n // 128) * 128) * 2
+        for key, fl, iss, ms_ in (("gram_roofline", gfl, gissued, gram_ms), ("syrk_roofline", sfl, sissued, syrk_ms)):
+            full[name][key] = {"bound": "tensor", "achieved": fl / (ms_ * 1e-3) / 1e12, "peak": BF16_PEAK,
+                               "unit": "TFLOP/s", "frac": fl / (ms_ * 1e-3) / 1e12 / BF16_PEAK,
+                               "flops_per_launch": fl, "issued_flops": iss,
+                               "issued_frac": iss / (ms_ * 1e-3) / 1e12 / BF16_PEAK,
+                               "peak_note": "measured cuBLAS bf16 (burst)"}
         vmix = vst.vecchia_nll(xy, t, th, w.m, nn, cnt, y, precision=prec, ws=ws, inducing=ind).item()
         full[name]["dnll_per_n_vs_fp64"] = abs(vmix - v64) / w.n
     full["nll_fp64"] = v64
