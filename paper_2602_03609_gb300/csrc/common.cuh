@@ -103,7 +103,18 @@ template <typename T> __device__ __forceinline__ T dexp(T x);
 template <> __device__ __forceinline__ float dexp<float>(float x) { return expf(x); }
 template <> __device__ __forceinline__ double dexp<double>(double x) { return exp(x); }
 template <typename T> __device__ __forceinline__ T drsqrt(T x);
-template <> __device__ __forceinline__ float drsqrt<float>(float x) { return rsqrtf(x); }
+// 1/sqrt(x) by the hardware approximation, denormal inputs and outputs
+// flushed to zero (rsqrtf also handles denormal inputs, at the cost of a few
+// instructions per call; the arguments here are variances and squared
+// distances, and a zero or flushed one is handled where it occurs)
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+template <> __device__ __forceinline__ float drsqrt<float>(float x) { return rsqrt_ftz(x); }
+// the smallest normal FP32 value: squared distances below it count as 0
+constexpr float kFltMinNormal = 1.17549435e-38f;
 template <> __device__ __forceinline__ double drsqrt<double>(double x) { return rsqrt(x); }
 template <typename T> __device__ __forceinline__ T dsqrt(T x);
 template <> __device__ __forceinline__ float dsqrt<float>(float x) { return sqrtf(x); }

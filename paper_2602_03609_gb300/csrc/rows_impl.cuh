@@ -291,7 +291,7 @@ template <typename T, int NU>
 __device__ __forceinline__ void pair_cov(T dx, T dy, T P, T G, T& v, T& q) {
   const T d2 = dx * dx + dy * dy;
   if constexpr (std::is_same<T, float>::value) {
-    const float h = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
+    const float h = d2 >= kFltMinNormal ? d2 * rsqrt_ftz(d2) : 0.f;
     const float x = G * h;
     const float E = __expf(-x);
     v = P * matern_M<NU, float>(x, E);
@@ -310,8 +310,8 @@ __device__ __forceinline__ void pair_cov(T dx, T dy, T P, T G, T& v, T& q) {
 template <int NU>
 __device__ __forceinline__ void pair_cov2(float2 dx, float2 dy, float2 Pm, float2 G, float2& v, float2& q) {
   const float2 d2 = __ffma2_rn(dx, dx, __fmul2_rn(dy, dy));
-  const float2 hh = __fmul2_rn(d2, make_float2(rsqrtf(d2.x), rsqrtf(d2.y)));
-  const float2 h = make_float2(d2.x > 0.f ? hh.x : 0.f, d2.y > 0.f ? hh.y : 0.f);
+  const float2 hh = __fmul2_rn(d2, make_float2(rsqrt_ftz(d2.x), rsqrt_ftz(d2.y)));
+  const float2 h = make_float2(d2.x >= kFltMinNormal ? hh.x : 0.f, d2.y >= kFltMinNormal ? hh.y : 0.f);
   const float2 x = __fmul2_rn(G, h);
   const float2 E = make_float2(__expf(-x.x), __expf(-x.y));
   float2 M, xdM;
@@ -731,7 +731,7 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       if constexpr (MIXED) {
         // FP32: h = d2 * rsqrt(d2), e^-x via the exp2 unit (relative errors
         // of a few 1e-7, inside the mixed form's covariance error budget)
-        const float h = d2 > 0.f ? d2 * rsqrtf(d2) : 0.f;
+        const float h = d2 >= kFltMinNormal ? d2 * rsqrt_ftz(d2) : 0.f;
         if (CAN_VIF && vif) {
           // VIF: the residual C - U U^T is a small difference, which
           // amplifies any systematic FP32 error in C (a rounded lag factor,

@@ -31,7 +31,7 @@ __device__ __forceinline__ float cov32(const DevTheta& th, float dx, float dy, f
   const float P = (float)th.sigma1sq * exp2f(-(float)th.p * lp);
   const float G = (float)th.c * exp2f(-0.5f * (float)th.gamma * lp);
   const float d2 = dx * dx + dy * dy;
-  const float x = G * (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f);
+  const float x = G * (d2 >= kFltMinNormal ? d2 * rsqrt_ftz(d2) : 0.f);
   return P * matern_M<NU, float>(x, expf(-x));
 }
 

@@ -165,8 +165,9 @@ __device__ __forceinline__ CovF cov_f(const DevTheta& th) {
 
 // covariance of Eq. (2) in FP32 (the same steps as the mixed form's cov32)
 // and a bound on its relative error in units of u = 2^-24, from the error
-// bounds of the FP32 functions (log2f 2 ulp, exp2f / expf / rsqrtf 3 ulp,
-// 1 ulp <= 2u) carried through each step: the lag powers (relative error of
+// bounds of the FP32 functions (log2f 2 ulp, exp2f / expf / the approximate
+// reciprocal square root 3 ulp, 1 ulp <= 2u; a subnormal squared distance is
+// taken as 0, which changes C by a relative O(1e-38)) carried through each step: the lag powers (relative error of
 // psi^-p grows with p |log2 psi| and the |2 alpha log2|u|| of the inner
 // power), the Matern argument x = G h (its relative error enters C times x)
 template <int NU>
@@ -179,7 +180,7 @@ __device__ __forceinline__ float cov32_err(const CovF& th, float dx, float dy, f
   const float P = th.s1 * exp2f(-th.p * lp);
   const float G = th.c * exp2f(-0.5f * th.gamma * lp);
   const float d2 = dx * dx + dy * dy;
-  const float x = G * (d2 > 0.f ? d2 * rsqrtf(d2) : 0.f);
+  const float x = G * (d2 >= kFltMinNormal ? d2 * rsqrt_ftz(d2) : 0.f);
   const float C = P * matern_M<NU, float>(x, expf(-x));
   const float core = 4.3f * fabsf(arg) + 8.1f + 4.2f * fabsf(lp);
   const float relP = fabsf(th.p) * core + 8.0f;
