@@ -70,12 +70,19 @@ typedef enum {
                      exceeds the threshold, or whose FP32 Cholesky fails, are
                      redone in FP64.  VIF: U = Sigma_nk L^{-T} on the tensor
                      cores, each FP32 operand split into three BF16 parts,
-                     six products accumulated in FP32 (about FP32 accuracy) */
-  VST_MIXED_BF16X3 = 2  /* as VST_MIXED, but the VIF low-rank product splits
-                           each operand into two BF16 parts and keeps three
-                           products (16 significand bits, relative error
-                           ~1e-5 per entry of U); plain Vecchia: = VST_MIXED.
-                           Single-dataset entry points only. */
+                     six products accumulated in FP32 (about FP32 accuracy);
+                     the per-row residual Gram (blocks of 32 positions) and
+                     the contractions over the points (W^T W, W^T e, e^T e,
+                     the gradient's H^T U) on the tensor cores with three
+                     fixed-point BF16 parts, leading sums exact per block */
+  VST_MIXED_BF16X3 = 2  /* as VST_MIXED, but the VIF low-rank product (and the
+                           gradient's n x k products) split each operand into
+                           two BF16 parts and keep three products (16
+                           significand bits, relative error ~1e-5 per entry
+                           of U); the per-row Gram and the contractions over
+                           the points keep three fixed-point parts.  Plain
+                           Vecchia: = VST_MIXED.  Single-dataset entry points
+                           only. */
 } vst_precision;
 
 /* Native parameters of Eq. (2) plus the nugget of Eq. (1):

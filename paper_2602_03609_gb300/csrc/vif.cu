@@ -898,11 +898,11 @@ static void launch_gram(int pm, const int32_t* nn, const int32_t* nn_cnt, int64_
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)std::max(per, 1) * sms));
     kern<<<blocks, 128, smem, st>>>(nn, nn_cnt, n, m, k, U, r, s1, gram);
   };
+  // (blocks of 32 positions go to the tensor-core kernel, gram_tc_rows)
   switch (padded_pm(pm)) {
     case 8: go(gram_delta_kernel<8>, gram_delta_smem<8>(4)); break;
     case 16: go(gram_delta_kernel<16>, gram_delta_smem<16>(4)); break;
-    case 24: go(gram_delta_kernel<24>, gram_delta_smem<24>(4)); break;
-    default: go(gram_delta_kernel<32>, gram_delta_smem<32>(4));
+    default: go(gram_delta_kernel<24>, gram_delta_smem<24>(4));
   }
 }
 
