@@ -924,9 +924,19 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
 #pragma unroll
     for (int k = LAST - 1; k >= 0; --k) {
       if (!MIXED && k >= m && k < LAST) continue;  // FP64: skip padding positions (identity rows and columns)
-      const T ak = __shfl_sync(kFull, acc_a * dinv, k);
-      T bk = T(0);
-      if (need_b) bk = __shfl_sync(kFull, acc_b * dinv, k);
+      T ak, bk = T(0);
+      if constexpr (MIXED) {
+        if (need_b) {
+          const float2 sab = __fmul2_rn(make_float2(acc_a, acc_b), make_float2(dinv, dinv));
+          ak = __shfl_sync(kFull, sab.x, k);
+          bk = __shfl_sync(kFull, sab.y, k);
+        } else {
+          ak = __shfl_sync(kFull, acc_a * dinv, k);
+        }
+      } else {
+        ak = __shfl_sync(kFull, acc_a * dinv, k);
+        if (need_b) bk = __shfl_sync(kFull, acc_b * dinv, k);
+      }
       if (lane == k) { aj = ak; bj = bk; }
       {
         // lanes >= k read entries on or above the diagonal and update sums
@@ -1021,8 +1031,23 @@ __device__ __forceinline__ void row_body(const RowArgs& g, const DevTheta& th, c
       df_fma_acc(rs, -yl.hi, df{aj, 0.0f});
       rs.lo = fmaf(-yl.lo, aj, fmaf(-bj, rf, rs.lo));
     }
-    Ds = df_warp_sum(Ds);
-    rs = df_warp_sum(rs);
+    {
+      // both double-float warp sums on packed FP32 pairs (the steps of df_warp_sum)
+      const float2 m1 = make_float2(-1.0f, -1.0f);
+      float2 hi = make_float2(Ds.hi, rs.hi), lo = make_float2(Ds.lo, rs.lo);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float2 oh = make_float2(__shfl_xor_sync(kFull, hi.x, o), __shfl_xor_sync(kFull, hi.y, o));
+        const float2 ol = make_float2(__shfl_xor_sync(kFull, lo.x, o), __shfl_xor_sync(kFull, lo.y, o));
+        const float2 sm = __fadd2_rn(hi, oh);
+        const float2 bb = __ffma2_rn(hi, m1, sm);
+        const float2 er = __fadd2_rn(__ffma2_rn(__ffma2_rn(bb, m1, sm), m1, hi), __ffma2_rn(bb, m1, oh));
+        hi = sm;
+        lo = __fadd2_rn(__fadd2_rn(lo, ol), er);
+      }
+      Ds = df{hi.x, lo.x};
+      rs = df{hi.y, lo.y};
+    }
     Dt = Ds.hi + Ds.lo;
     rt = rs.hi + rs.lo;
     if (!(Dt > 0.0f) || !(rt == rt)) {  // lost to FP32 rounding: redo in FP64
