@@ -54,7 +54,7 @@ def _measured_peak(key, fallback):
 # DRAM bytes (read + write) of one launch of the mixed row kernel on the
 # continental workload, from one ncu capture of the current kernel
 # (dram__bytes_read.sum + dram__bytes_write.sum): the inputs, read once
-ROWS_TRAFFIC_BYTES = 173206784 + 4233216
+ROWS_TRAFFIC_BYTES = 173642496 + 4249856
 
 # dense BF16 tensor peak (a cuBLAS GEMM timed alone on this part), for the
 # VIF low-rank GEMM
