@@ -194,11 +194,12 @@ def test_vif_grad_tensor_core_gram_many_drains(env):
     assert np.all(np.abs(gm - g64) <= 1e-4 * np.abs(g64) + 1e-6 * n), (gm, g64)
 
 
-@pytest.mark.parametrize("k,m", [(60, 30), (130, 26)])
+@pytest.mark.parametrize("k,m", [(60, 30), (130, 26), (61, 31)])
 def test_vif_mixed_32_position_blocks(env, k, m):
     """Local blocks of 32 positions (m = 24..31), whose per-row residual Gram
     runs on the tensor cores (groups of four rows, 64-column chunks; here
-    410 rows: the last group ragged, and for k = 130 a ragged last chunk):
+    410 rows: the last group ragged, for k = 130 a ragged last chunk, for
+    k = 61 an odd column count, and m = 31 a block without padding):
     the mixed NLL and NLL + gradient against the oracle's Woodbury NLL and
     forward-mode gradient, |dNLL|/n <= 1e-6, |dg_j| <= 1e-4 |g_j| + 1e-6 n."""
     torch, vst = env
